@@ -1,0 +1,426 @@
+"""Benchmark: base64 encode + strict decode of large single buffers on GB300.
+
+One step = the whole hot path over one batch of input: encode 1 GiB of
+uniform random bytes with the standard table, strict-decode the result, then
+the same with the base64url table (padded) swapped in at run time. The metric
+is input GB/s (bytes consumed by encode plus characters consumed by decode,
+per second), next to an on-device D2D memcpy of the same bytes.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torch.distributed.run, one replica of the workload per GPU
+(the buffers are independent; no data-path collective): weak scaling.
+`--impl reference` times the oracle (the plain scalar C codec) on the host's
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encode/decode input GB/s vs on-device D2D memcpy GB/s; batched p99 latency"
+N_BYTES = 1 << 30
+SEED = 1
+WORKLOAD = ("large single buffer: 1 GiB uniform random bytes (seed 1); encode then strict "
+            "decode, standard table then base64url table (padded) swapped at run time")
+
+
+def peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def csrc_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1910_05109_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str) -> dict | None:
+    """DRAM traffic per input byte of `kernel` from the committed ncu summary,
+    if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    digest = csrc_digest()
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        kv = dict(x.split("=", 1) for x in line.split())
+        if kv.get("kernel") == kernel and kv.get("csrc") == digest:
+            return {"bytes_per_input_byte": float(kv["dram_bytes_per_input_byte"])}
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.reader.join(timeout=2)
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU baseline (oracle)
+
+def oracle_pass(data: np.ndarray, threads: int) -> tuple[int, float]:
+    """The oracle over one step's work (encode + decode, both tables), with the
+    buffer split into `threads` slices at multiples of 3 bytes (each slice's
+    encoding is then a whole number of 4-character groups). Returns (input
+    bytes consumed, seconds)."""
+    import oracle
+    tables = (oracle.standard_alphabet(), oracle.url_alphabet())
+    n = data.size
+    per = max(3, (n // threads) // 3 * 3)
+    cuts = list(range(0, n, per)) + [n]
+    slices = [data[cuts[i]:cuts[i + 1]] for i in range(len(cuts) - 1)]
+    consumed = 0
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        for alph in tables:
+            enc = list(ex.map(lambda s: oracle.encode(s, alph, True), slices))
+            dec = list(ex.map(lambda e: oracle.decode(e, alph, True), enc))
+            assert sum(r for r, _ in dec) == n
+            consumed += n + sum(e.size for e in enc)
+    return consumed, time.perf_counter() - t0
+
+
+def cpu_baseline(data: np.ndarray) -> dict:
+    cores = len(os.sched_getaffinity(0))
+    consumed, sec = 0, 0.0
+    for _ in range(3):
+        c, s = oracle_pass(data, cores)
+        consumed, sec = consumed + c, sec + s
+    one = data[: 64 << 20]
+    c1, s1 = oracle_pass(one, 1)
+    return {"value": consumed / sec / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": (f"three full steps (1 GiB each; encode+decode, standard and url tables) "
+                       f"split over {cores} threads at 3-byte boundaries; {sec:.2f} s wall"),
+            "value_1core": c1 / s1 / 1e9,
+            "sample_1core": "first 64 MiB of the same buffer, one thread, both tables"}
+
+
+# ---------------------------------------------------------------- helpers
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def emit(obj: dict):
+    print(json.dumps(obj), flush=True)
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1910_05109_gb300 import workloads as wl
+    data = wl.random_bytes(N_BYTES, SEED)
+    cores = len(os.sched_getaffinity(0))
+    # Each step: a bounded sample (the first 128 MiB) of the step's workload.
+    sample = data[: 128 << 20]
+    for _ in range(args.warmup):
+        oracle_pass(sample, cores)
+    total, sec = 0, 0.0
+    for _ in range(args.steps):
+        c, s = oracle_pass(sample, cores)
+        total += c
+        sec += s
+    value = total / sec / 1e9
+    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+          "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True,
+          "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+          "config": {"workload": WORKLOAD, "bytes": N_BYTES, "sample_bytes": sample.size},
+          "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                           "sample": "first 128 MiB of the 1 GiB buffer per step, both tables, "
+                                     f"split over {cores} threads"},
+          "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                  "d2h_bytes_per_step": 0}})
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1910_05109_gb300 import build as gpu_build
+    if rank == 0 or ws == 1:
+        gpu_build.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_1910_05109_gb300 import binding as b64
+    from paper_1910_05109_gb300 import workloads as wl
+
+    n = args.bytes
+    data = wl.random_bytes(n, SEED)
+    src = torch.from_numpy(data).to(dev)
+    std = b64.Alphabet.standard()
+    url = b64.Alphabet.create(std.chars()[0][:62] + b"-_", True)
+    m = b64.encoded_length(n, True)
+    enc = {k: torch.empty(m, dtype=torch.uint8, device=dev) for k in ("std", "url")}
+    dec = {k: torch.empty(b64.decoded_max_length(m), dtype=torch.uint8, device=dev)
+           for k in ("std", "url")}
+    res = torch.zeros(2, dtype=torch.int64, device=dev)
+    tables = (("std", std), ("url", url))
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        for i, (k, a) in enumerate(tables):
+            if ev is not None:
+                ev[4 * i].record(stream)
+            b64.encode(src, a, enc[k], stream)
+            if ev is not None:
+                ev[4 * i + 1].record(stream)
+                ev[4 * i + 2].record(stream)
+            b64.decode_async(enc[k], dec[k], res[i:i + 1], a, stream)
+            if ev is not None:
+                ev[4 * i + 3].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    # Round trip and alphabet swap checked once (not timed).
+    assert int(res[0]) == n and int(res[1]) == n
+    assert torch.equal(dec["std"][:n], src) and torch.equal(dec["url"][:n], src)
+    assert not torch.equal(enc["std"], enc["url"])
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(K)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+    gpu_id = gpu_id if gpu_id.startswith("GPU-") else f"GPU-{gpu_id}"
+    with ClockSampler(gpu_id) as clocks:
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        start.record(stream)
+        for k in range(K):
+            step(evs[k])
+        stop.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+    ms = start.elapsed_time(stop)
+    t_enc = [e[4 * i].elapsed_time(e[4 * i + 1]) for e in evs for i in range(2)]
+    t_dec = [e[4 * i + 2].elapsed_time(e[4 * i + 3]) for e in evs for i in range(2)]
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    assert int(res[0]) == n and int(res[1]) == n
+
+    # D2D memcpy of the same bytes (torch copy_ issues cudaMemcpyAsync D2D).
+    def memcpy_ms(nbytes: int, reps: int = 20) -> float:
+        a = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        bb = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        for _ in range(3):
+            bb.copy_(a)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        times = []
+        for _ in range(reps):
+            e0.record(stream)
+            bb.copy_(a)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        del a, bb
+        return statistics.median(times)
+
+    mc_n, mc_m = memcpy_ms(n), memcpy_ms(m)
+    enc_ms, dec_ms = statistics.median(t_enc), statistics.median(t_dec)
+    enc_avg, dec_avg = sum(t_enc) / len(t_enc), sum(t_dec) / len(t_dec)
+
+    # End to end through the public API with host buffers: pinned host input
+    # -> device, encode, encoded text -> host; host text -> device, decode,
+    # decoded bytes and result -> host; both tables.
+    if args.no_e2e:
+        return finish(args, locals())
+    h_src = torch.from_numpy(data).pin_memory()
+    h_txt = torch.empty(m, dtype=torch.uint8).pin_memory()
+    h_out = torch.empty(n, dtype=torch.uint8).pin_memory()
+    h_res = torch.empty(2, dtype=torch.int64).pin_memory()
+    d_in = torch.empty(n, dtype=torch.uint8, device=dev)
+    d_txt = torch.empty(m, dtype=torch.uint8, device=dev)
+
+    def e2e_step():
+        for i, (k, a) in enumerate(tables):
+            d_in.copy_(h_src, non_blocking=True)
+            b64.encode(d_in, a, enc[k], stream)
+            h_txt.copy_(enc[k], non_blocking=True)
+            d_txt.copy_(h_txt, non_blocking=True)
+            b64.decode_async(d_txt, dec[k], res[i:i + 1], a, stream)
+            h_out.copy_(dec[k][:n], non_blocking=True)
+            h_res[i:i + 1].copy_(res[i:i + 1], non_blocking=True)
+
+    e2e_steps = max(3, min(10, K // 50))
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    assert int(h_res[0]) == n and torch.equal(h_out, h_src)
+    del h_src, h_txt, h_out, d_in, d_txt
+    return finish(args, locals())
+
+
+def finish(args, v):
+    import torch.distributed as dist
+    ws, rank, K, n, m, ms = v["ws"], v["rank"], v["K"], v["n"], v["m"], v["ms"]
+    enc_ms, dec_ms, enc_avg, dec_avg = v["enc_ms"], v["dec_ms"], v["enc_avg"], v["dec_avg"]
+    mc_n, mc_m, data, clocks = v["mc_n"], v["mc_m"], v["data"], v["clocks"]
+    e2e_ms = v.get("e2e_ms")
+
+    step_in = 2 * (n + m)                       # input bytes per step (both tables)
+    value = step_in * ws / (ms / K / 1e3) / 1e9
+    pk = peaks()
+    enc_alg = n + m                             # algorithmic bytes per encode launch
+    dec_alg = m + n                             # per decode call (reads m, writes n)
+    dominant = "decode" if dec_avg >= enc_avg else "encode"
+    dom_ms = dec_avg if dominant == "decode" else enc_avg
+    achieved = (dec_alg if dominant == "decode" else enc_alg) / (dom_ms / 1e3) / 1e9
+    kname = "decode_tma_kernel" if dominant == "decode" else "encode_tma_kernel"
+    tr = profiled_traffic(kname)
+    traffic = None
+    if tr is not None:
+        traffic = tr["bytes_per_input_byte"] * (m if dominant == "decode" else n)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD if n == N_BYTES else f"{n} bytes (profiling case)",
+                   "bytes": n, "encoded_bytes": m,
+                   "tables": ["standard (Table 1)", "base64url, padded"],
+                   "l2": "inputs (1 GiB / 1.43 GB) larger than L2; no flush",
+                   "parallelism": f"replicas x{ws}"},
+        "encode_gbps": n / (enc_ms / 1e3) / 1e9,
+        "decode_gbps": m / (dec_ms / 1e3) / 1e9,
+        "memcpy_gbps": {"encode_input": n / (mc_n / 1e3) / 1e9,
+                        "decode_input": m / (mc_m / 1e3) / 1e9},
+        "frac_of_memcpy": {"encode": mc_n / enc_ms, "decode": mc_m / dec_ms},
+        "base64_gbps": {"encode": m / (enc_ms / 1e3) / 1e9, "decode": m / (dec_ms / 1e3) / 1e9},
+        "dram_gbps": {"encode": enc_alg / (enc_ms / 1e3) / 1e9,
+                      "decode": dec_alg / (dec_ms / 1e3) / 1e9,
+                      "memcpy": 2 * n / (mc_n / 1e3) / 1e9},
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved,
+                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                     "peak_source": pk["source"], "traffic": traffic},
+        "e2e": None if e2e_ms is None else {
+            "value": step_in / (e2e_ms / 1e3) / 1e9, "unit": "GB/s",
+            "h2d_bytes_per_step": 2 * (n + m), "d2h_bytes_per_step": 2 * (m + n + 8)},
+        "gpu_launches": 6 * K,
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(data)
+    if rank == 0:
+        emit(out)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--bytes", type=int, default=N_BYTES,
+                    help="input size (default 1 GiB; smaller sizes are for profiling)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

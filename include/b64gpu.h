@@ -1,0 +1,143 @@
+/*
+ * b64gpu: base64 encode and strict decode on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * The operations are those of Mula & Lemire, "Base64 encoding and decoding at
+ * almost the speed of a memory copy" (arXiv:1910.05109):
+ *   - encode (Sec. 2 and Sec. 3.1): every 3 input bytes s1,s2,s3 become the
+ *     characters of the 6-bit values s1 div 4, (s2 div 16) + (s1*16) mod 64,
+ *     (s2*4) mod 64 + (s3 div 64), s3 mod 64, looked up in a 64-entry
+ *     alphabet (Table 1, or any other table given at run time, Sec. 3.1);
+ *     '=' pads the output to a multiple of 4 characters (Sec. 2);
+ *   - strict decode (Sec. 2 and Sec. 3.2): every 4 characters a,b,c,d become
+ *     a*4 + b div 16, (b*16) mod 256 + c div 4, (c*64) mod 256 + d; any byte
+ *     outside the alphabet is an error (Sec. 3.2, Fig. 2).
+ *
+ * Decoding rules where the paper is silent (the library's contract):
+ *   - the error reported is the smallest offset among all errors;
+ *   - a byte >= 0x80, or any byte not in the alphabet, is an error at its index;
+ *   - padded alphabets: '=' is allowed only as the last character, or as the
+ *     second-to-last when the last is '='; any other '=' is an error at its
+ *     index; a length that is not a multiple of 4 is an error at offset len;
+ *   - unpadded alphabets: every '=' is an error; a length of 1 mod 4 is an
+ *     error at offset len;
+ *   - bits of the last character that reach no output byte are ignored;
+ *   - MIME mode (b64_mime_decode*): CR, LF and space are skipped first, the
+ *     rules above apply to the rest, and offsets are in the original input.
+ *
+ * Conventions for every call below:
+ *   - Data pointers (src, dst, offsets, results) are DEVICE pointers on the
+ *     current CUDA device, owned by the caller. The library keeps no pointer
+ *     after a call returns and never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Calls enqueue work on it and return without waiting, except
+ *     where a call says it synchronises.
+ *   - The library writes nothing past the output length it returns; on a
+ *     decode error the content of dst is unspecified but nothing past
+ *     b64_decoded_max_length(len) is written.
+ *   - src and dst must not overlap.
+ *   - Any alignment is accepted; 16-byte aligned src and dst take the fast
+ *     path.
+ *   - Errors in arguments or CUDA calls are reported through the return value;
+ *     b64_last_error() then gives a message for the calling thread.
+ */
+#ifndef B64GPU_H
+#define B64GPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Codes returned by calls that return int (0 = success). */
+#define B64_SUCCESS 0
+#define B64_ERR_INVALID_ARGUMENT (-1)
+#define B64_ERR_CUDA (-2)
+
+/* Codes returned by calls that return int64_t in place of a length. They are
+ * far below -(len+1) for any possible len, so they cannot be mistaken for a
+ * decode error offset. */
+#define B64_E_INVAL (INT64_MIN + 1)
+#define B64_E_CUDA (INT64_MIN + 2)
+
+/* ---------------------------------------------------------------- alphabets
+ * A 64-character table (Table 1 and its base64url variant, Sec. 2; any other
+ * table at run time, Sec. 3.1) plus a padding mode. Handles are host objects,
+ * immutable after creation and safe to share between threads. */
+typedef struct b64_alphabet b64_alphabet;
+
+/* chars: 64 distinct bytes, each < 0x80 and none of '=', CR, LF or space
+ * (those have fixed meanings). padded: 1 = encode appends '=' and decode
+ * requires it; 0 = no padding. Returns NULL (and sets b64_last_error) if chars
+ * is invalid. Free with b64_alphabet_destroy. */
+b64_alphabet* b64_alphabet_create(const uint8_t chars[64], int padded);
+
+/* Table 1 (A-Z a-z 0-9 + /), padded. Static; never destroy. */
+const b64_alphabet* b64_alphabet_standard(void);
+
+/* base64url (Sec. 2: '+' and '/' replaced by '-' and '_'), unpadded. Static. */
+const b64_alphabet* b64_alphabet_url(void);
+
+/* Destroys a handle made by b64_alphabet_create (NULL and the static tables
+ * are ignored). The caller must make sure no enqueued call still needs it:
+ * calls copy the table into their launch parameters, so it may be destroyed
+ * as soon as the call has returned. */
+void b64_alphabet_destroy(b64_alphabet* a);
+
+/* Copies the 64 characters into out and returns the padding mode. */
+int b64_alphabet_chars(const b64_alphabet* a, uint8_t out[64]);
+
+/* ---------------------------------------------------------------- lengths */
+
+/* Encoded length of n bytes: 4*ceil(n/3) when padded, ceil(4n/3) when not
+ * (Sec. 2). */
+size_t b64_encoded_length(size_t n, int padded);
+
+/* Capacity a decode output needs for m input characters: 3*ceil(m/4). */
+size_t b64_decoded_max_length(size_t m);
+
+/* ---------------------------------------------------------------- single buffer */
+
+/* Encodes len bytes at src into dst (capacity >= b64_encoded_length(len,
+ * padded)). Enqueues on stream and returns the output length immediately, or
+ * B64_E_INVAL / B64_E_CUDA. */
+int64_t b64_encode(const uint8_t* src, size_t len, uint8_t* dst, const b64_alphabet* a,
+                   void* stream);
+
+/* Strict decode of len characters at src into dst (capacity >=
+ * b64_decoded_max_length(len)). Enqueues, writes the result to the device
+ * int64 *d_result (8-byte aligned, caller-owned) and returns B64_SUCCESS
+ * without waiting. *d_result becomes the decoded length (>= 0) or
+ * -(offset+1), offset in [0, len] being the first error (offset == len: bad
+ * length). Returns B64_ERR_INVALID_ARGUMENT / B64_ERR_CUDA on failure to
+ * enqueue. */
+int b64_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b64_alphabet* a,
+                     int64_t* d_result, void* stream);
+
+/* As b64_decode_async, then waits for the stream and returns *d_result's
+ * value (or B64_E_INVAL / B64_E_CUDA). Uses one 8-byte device word and one
+ * pinned host word per calling thread and device, allocated on the thread's
+ * first call and kept until the process exits. */
+int64_t b64_decode(const uint8_t* src, size_t len, uint8_t* dst, const b64_alphabet* a,
+                   void* stream);
+
+/* ---------------------------------------------------------------- diagnostics */
+
+/* Thread-local message for the last failed call of this thread ("" if none). */
+const char* b64_last_error(void);
+
+/* Every wait inside the library's kernels is bounded in time; a kernel whose
+ * wait runs out sets a per-device flag and returns early (its output is then
+ * incomplete). Returns the flag of the current device (0 = never set) and
+ * clears it if clear != 0. Synchronises the device. Negative on CUDA error. */
+int b64_device_fault_flag(int clear);
+
+/* Library version: major*10000 + minor*100 + patch. */
+int b64_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* B64GPU_H */

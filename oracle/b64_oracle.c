@@ -129,28 +129,34 @@ int64_t oracle_decode(const uint8_t* src, size_t m, uint8_t* dst,
     int inv[256];
     oracle_inverse(alph, inv);
 
-    /* R5: the positions of the characters that take part in decoding. */
-    size_t* pos = (size_t*)malloc((m ? m : 1) * sizeof(size_t));
-    if (!pos) return INT64_MIN;
-    size_t mc = 0;
-    for (size_t i = 0; i < m; ++i) {
-        if (mime && oracle_is_mime_space(src[i])) continue;
-        pos[mc++] = i;
+    /* R5: the positions of the characters that take part in decoding (in
+     * MIME mode a list; otherwise every position, POS(j) = j). */
+    size_t* pos = NULL;
+    size_t mc = m;
+    if (mime) {
+        pos = (size_t*)malloc((m ? m : 1) * sizeof(size_t));
+        if (!pos) return INT64_MIN;
+        mc = 0;
+        for (size_t i = 0; i < m; ++i) {
+            if (oracle_is_mime_space(src[i])) continue;
+            pos[mc++] = i;
+        }
     }
+#define POS(j) (pos ? pos[(j)] : (j))
 
     /* R1, R2, R4: scan in order; the first bad character is the smallest
      * offset, and the length error (offset m) is larger than any index. */
     int has_err = 0;
     size_t err = 0;
     for (size_t j = 0; j < mc; ++j) {
-        uint8_t ch = src[pos[j]];
+        uint8_t ch = src[POS(j)];
         if (inv[ch] != ORACLE_NOT_IN_TABLE) continue;
         int pad_ok = 0;
         if (ch == '=' && padded) {
             if (j == mc - 1) pad_ok = 1;
-            if (j + 2 == mc && src[pos[mc - 1]] == '=') pad_ok = 1;
+            if (j + 2 == mc && src[POS(mc - 1)] == '=') pad_ok = 1;
         }
-        if (!pad_ok) { has_err = 1; err = pos[j]; break; }
+        if (!pad_ok) { has_err = 1; err = POS(j); break; }
     }
     if (!has_err) {
         if (padded && mc % 4 != 0) { has_err = 1; err = m; }
@@ -163,8 +169,8 @@ int64_t oracle_decode(const uint8_t* src, size_t m, uint8_t* dst,
 
     size_t pads = 0;
     if (padded) {
-        if (mc >= 1 && src[pos[mc - 1]] == '=') pads = 1;
-        if (mc >= 2 && src[pos[mc - 2]] == '=') pads = 2;
+        if (mc >= 1 && src[POS(mc - 1)] == '=') pads = 1;
+        if (mc >= 2 && src[POS(mc - 2)] == '=') pads = 2;
     }
     size_t d = mc - pads;
 
@@ -175,7 +181,7 @@ int64_t oracle_decode(const uint8_t* src, size_t m, uint8_t* dst,
     for (size_t j = 0; j < d; j += 4) {
         unsigned v[4] = {0, 0, 0, 0};
         size_t k = d - j < 4 ? d - j : 4;
-        for (size_t t = 0; t < k; ++t) v[t] = (unsigned)inv[src[pos[j + t]]];
+        for (size_t t = 0; t < k; ++t) v[t] = (unsigned)inv[src[POS(j + t)]];
         unsigned a = v[0], b = v[1], c = v[2], dd = v[3];
         unsigned bytes[3];
         bytes[0] = (a * 4) + (b / 16);
@@ -185,6 +191,7 @@ int64_t oracle_decode(const uint8_t* src, size_t m, uint8_t* dst,
     }
     free(pos);
     return (int64_t)o;
+#undef POS
 }
 
 /* Batched forms: string i occupies src[src_off[i] .. src_off[i+1]) and is

@@ -1,0 +1,246 @@
+// C ABI of the library (declared in include/b64gpu.h): alphabet handles,
+// length helpers, argument checks, and the launches of the codec kernels.
+// Host code only; the kernels live in b64_encode.cu and b64_decode.cu.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "b64gpu.h"
+#include "b64_internal.h"
+
+struct b64_alphabet {
+    uint8_t chars[64];
+    int padded;
+    b64::EncodeTable enc;
+    b64::DecodeTable dec;
+};
+
+namespace b64 {
+namespace {
+
+thread_local std::string t_last_error;
+
+struct DeviceSlot {
+    std::once_flag once;
+    DeviceInfo info;
+};
+DeviceSlot g_devices[64];
+
+bool valid_chars(const uint8_t chars[64], char* why, size_t why_len) {
+    bool seen[256] = {false};
+    for (int k = 0; k < 64; ++k) {
+        const uint8_t c = chars[k];
+        if (c >= 0x80 || c == '=' || c == '\r' || c == '\n' || c == ' ') {
+            snprintf(why, why_len, "alphabet character %d (0x%02x) is reserved or not ASCII", k, c);
+            return false;
+        }
+        if (seen[c]) {
+            snprintf(why, why_len, "alphabet character 0x%02x appears twice", c);
+            return false;
+        }
+        seen[c] = true;
+    }
+    return true;
+}
+
+void fill_tables(b64_alphabet* a) {
+    memset(&a->enc, 0, sizeof(a->enc));
+    uint8_t* e = reinterpret_cast<uint8_t*>(a->enc.w);
+    uint8_t* d = reinterpret_cast<uint8_t*>(a->dec.w);
+    for (int c = 0; c < 256; ++c) d[c] = uint8_t(kBad);
+    for (int k = 0; k < 64; ++k) {
+        e[k] = a->chars[k];
+        d[a->chars[k]] = uint8_t(k);
+    }
+}
+
+b64_alphabet make_builtin(bool url) {
+    b64_alphabet a;
+    int k = 0;
+    for (char c = 'A'; c <= 'Z'; ++c) a.chars[k++] = uint8_t(c);
+    for (char c = 'a'; c <= 'z'; ++c) a.chars[k++] = uint8_t(c);
+    for (char c = '0'; c <= '9'; ++c) a.chars[k++] = uint8_t(c);
+    a.chars[62] = url ? '-' : '+';
+    a.chars[63] = url ? '_' : '/';
+    a.padded = url ? 0 : 1;
+    fill_tables(&a);
+    return a;
+}
+
+const b64_alphabet g_standard = make_builtin(false);
+const b64_alphabet g_url = make_builtin(true);
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return na && nb && x < y + nb && y < x + na;
+}
+
+// Per-thread, per-device scratch of the synchronous decode: one device word
+// for the result and one pinned host word to read it back into.
+struct SyncScratch {
+    int64_t* d_word = nullptr;
+    int64_t* h_word = nullptr;
+};
+thread_local SyncScratch t_scratch[64];
+
+}  // namespace
+
+const DeviceInfo& device_info(int device) {
+    if (device < 0) cudaGetDevice(&device);
+    DeviceSlot& slot = g_devices[device & 63];
+    std::call_once(slot.once, [&] {
+        slot.info.device = device;
+        cudaDeviceGetAttribute(&slot.info.sm_count, cudaDevAttrMultiProcessorCount, device);
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+        slot.info.smem_optin = size_t(optin);
+    });
+    return slot.info;
+}
+
+static void vset(const char* fmt, va_list ap) {
+    char buf[512];
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    t_last_error = buf;
+}
+
+int set_error(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vset(fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int64_t set_error64(int64_t code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vset(fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+void clear_error() { t_last_error.clear(); }
+
+}  // namespace b64
+
+using namespace b64;
+
+extern "C" {
+
+b64_alphabet* b64_alphabet_create(const uint8_t chars[64], int padded) {
+    if (!chars) {
+        set_error(0, "b64_alphabet_create: chars is NULL");
+        return nullptr;
+    }
+    char why[160];
+    if (!valid_chars(chars, why, sizeof(why))) {
+        set_error(0, "b64_alphabet_create: %s", why);
+        return nullptr;
+    }
+    b64_alphabet* a = new b64_alphabet;
+    memcpy(a->chars, chars, 64);
+    a->padded = padded ? 1 : 0;
+    fill_tables(a);
+    return a;
+}
+
+const b64_alphabet* b64_alphabet_standard(void) { return &g_standard; }
+const b64_alphabet* b64_alphabet_url(void) { return &g_url; }
+
+void b64_alphabet_destroy(b64_alphabet* a) {
+    if (!a || a == &g_standard || a == &g_url) return;
+    delete a;
+}
+
+int b64_alphabet_chars(const b64_alphabet* a, uint8_t out[64]) {
+    if (!a || !out) return set_error(B64_ERR_INVALID_ARGUMENT, "b64_alphabet_chars: NULL argument");
+    memcpy(out, a->chars, 64);
+    return a->padded;
+}
+
+size_t b64_encoded_length(size_t n, int padded) {
+    const size_t g = n / 3, r = n % 3;
+    if (r == 0) return 4 * g;
+    return 4 * g + (padded ? 4 : r + 1);
+}
+
+size_t b64_decoded_max_length(size_t m) { return (m / 4 + (m % 4 ? 1 : 0)) * 3; }
+
+int64_t b64_encode(const uint8_t* src, size_t len, uint8_t* dst, const b64_alphabet* a,
+                   void* stream) {
+    if (!a) return set_error64(B64_E_INVAL, "b64_encode: alphabet is NULL");
+    if (len == 0) return 0;
+    if (!src || !dst) return set_error64(B64_E_INVAL, "b64_encode: NULL src or dst");
+    if (len > (size_t(1) << 62)) return set_error64(B64_E_INVAL, "b64_encode: len too large");
+    const size_t out = b64_encoded_length(len, a->padded);
+    if (overlaps(src, len, dst, out)) return set_error64(B64_E_INVAL, "b64_encode: src and dst overlap");
+    const cudaError_t e =
+        launch_encode(src, len, dst, a->enc, a->padded, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return set_error64(B64_E_CUDA, "b64_encode: %s", cudaGetErrorString(e));
+    return int64_t(out);
+}
+
+int b64_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b64_alphabet* a,
+                     int64_t* d_result, void* stream) {
+    if (!a || !d_result)
+        return set_error(B64_ERR_INVALID_ARGUMENT, "b64_decode_async: NULL alphabet or d_result");
+    if (reinterpret_cast<uintptr_t>(d_result) & 7u)
+        return set_error(B64_ERR_INVALID_ARGUMENT, "b64_decode_async: d_result not 8-byte aligned");
+    if (len > 0 && (!src || !dst))
+        return set_error(B64_ERR_INVALID_ARGUMENT, "b64_decode_async: NULL src or dst");
+    if (len > (size_t(1) << 62))
+        return set_error(B64_ERR_INVALID_ARGUMENT, "b64_decode_async: len too large");
+    if (overlaps(src, len, dst, b64_decoded_max_length(len)))
+        return set_error(B64_ERR_INVALID_ARGUMENT, "b64_decode_async: src and dst overlap");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(d_result, 0xFF, sizeof(int64_t), s);
+    if (e == cudaSuccess) e = launch_decode(src, len, dst, a->dec, a->padded, d_result, s);
+    if (e != cudaSuccess)
+        return set_error(B64_ERR_CUDA, "b64_decode_async: %s", cudaGetErrorString(e));
+    return B64_SUCCESS;
+}
+
+int64_t b64_decode(const uint8_t* src, size_t len, uint8_t* dst, const b64_alphabet* a,
+                   void* stream) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_error64(B64_E_CUDA, "b64_decode: %s", cudaGetErrorString(e));
+    SyncScratch& sc = t_scratch[dev & 63];
+    if (!sc.d_word) {
+        e = cudaMalloc(&sc.d_word, sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMallocHost(&sc.h_word, sizeof(int64_t));
+        if (e != cudaSuccess) {
+            if (sc.d_word) cudaFree(sc.d_word);
+            sc.d_word = nullptr;
+            return set_error64(B64_E_CUDA, "b64_decode: scratch allocation: %s",
+                               cudaGetErrorString(e));
+        }
+    }
+    const int rc = b64_decode_async(src, len, dst, a, sc.d_word, stream);
+    if (rc == B64_ERR_INVALID_ARGUMENT) return B64_E_INVAL;
+    if (rc != B64_SUCCESS) return B64_E_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    e = cudaMemcpyAsync(sc.h_word, sc.d_word, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_error64(B64_E_CUDA, "b64_decode: %s", cudaGetErrorString(e));
+    return *sc.h_word;
+}
+
+const char* b64_last_error(void) { return t_last_error.c_str(); }
+
+int b64_device_fault_flag(int clear) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return set_error(B64_ERR_CUDA, "b64_device_fault_flag: %s", cudaGetErrorString(e));
+    uint32_t f = encode_fault_flag(clear != 0) | decode_fault_flag(clear != 0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(B64_ERR_CUDA, "b64_device_fault_flag: %s", cudaGetErrorString(e));
+    return int(f);
+}
+
+int b64_version(void) { return 100; }
+
+}  // extern "C"

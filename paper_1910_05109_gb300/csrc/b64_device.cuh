@@ -1,0 +1,189 @@
+// Device-side building blocks shared by the codec kernels: lookup-table
+// parameter blocks, the byte-level encode/decode steps, and thin inline-PTX
+// wrappers for mbarriers and bulk (TMA) copies on sm_103a.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace b64 {
+
+// ------------------------------------------------------------------ tables
+// The alphabet travels by value in the kernel parameters, so a launch needs
+// no device allocation and can be recorded in a CUDA graph.
+
+// 64 output characters indexed by a 6-bit value (Table 1 or any other
+// run-time table, Sec. 3.1).
+struct EncodeTable {
+    uint32_t w[16];
+};
+
+// 256 entries indexed by an input byte: the 6-bit value of an alphabet
+// character, 0x80 for every other byte (Sec. 3.2 uses 128 entries and ORs the
+// input's top bit into the error; indexing by the whole byte folds that OR
+// into the table: entries 128..255 are all 0x80).
+struct DecodeTable {
+    uint32_t w[64];
+};
+
+constexpr uint32_t kBad = 0x80u;
+constexpr uint64_t kNoError = ~0ull;
+
+// Bounded waits give up after this many nanoseconds of %globaltimer.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+// ------------------------------------------------------------------ encode step
+// Sec. 3.1: a triple (s1,s2,s3) is first spread into the 32-bit word whose
+// bytes, lowest first, are (s2,s1,s3,s2); then the four 6-bit values sit at
+// bit offsets 10, 4, 22 and 16 of that word. `g` is that word.
+__device__ __forceinline__ uint32_t encode_gathered(uint32_t g, const uint8_t* lut) {
+    const uint32_t c0 = lut[(g >> 10) & 63u];
+    const uint32_t c1 = lut[(g >> 4) & 63u];
+    const uint32_t c2 = lut[(g >> 22) & 63u];
+    const uint32_t c3 = lut[(g >> 16) & 63u];
+    return __byte_perm(__byte_perm(c0, c1, 0x7740u), __byte_perm(c2, c3, 0x7740u), 0x5410u);
+}
+
+// Encodes 12 bytes held in three little-endian words (x = bytes 0..3,
+// y = 4..7, z = 8..11) into 16 characters, returned as four words. The
+// __byte_perm selectors pick (s2,s1,s3,s2) of each of the four triples.
+__device__ __forceinline__ uint4 encode12(uint32_t x, uint32_t y, uint32_t z, const uint8_t* lut) {
+    uint4 o;
+    o.x = encode_gathered(__byte_perm(x, 0, 0x1201u), lut);
+    o.y = encode_gathered(__byte_perm(x, y, 0x4534u), lut);
+    o.z = encode_gathered(__byte_perm(y, z, 0x3423u), lut);
+    o.w = encode_gathered(__byte_perm(z, 0, 0x2312u), lut);
+    return o;
+}
+
+// ------------------------------------------------------------------ decode step
+// Sec. 2 / Sec. 3.2: four characters (little-endian word, first character in
+// the low byte) -> the 24-bit value a<<18 | b<<12 | c<<6 | d, whose bytes
+// from high to low are the three output bytes. `err` collects the OR of the
+// translated values; bit 7 set means a byte outside the alphabet.
+__device__ __forceinline__ uint32_t decode4(uint32_t w, const uint8_t* lut, uint32_t& err) {
+    const uint32_t a = lut[__byte_perm(w, 0, 0x4440u)];
+    const uint32_t b = lut[__byte_perm(w, 0, 0x4441u)];
+    const uint32_t c = lut[__byte_perm(w, 0, 0x4442u)];
+    const uint32_t d = lut[__byte_perm(w, 0, 0x4443u)];
+    err |= a | b | c | d;
+    return (((a << 6 | b) << 6 | c) << 6) | d;
+}
+
+// Packs four 24-bit values into 12 output bytes (three words), each value
+// contributing its bytes from high to low.
+__device__ __forceinline__ uint3 pack4x24(uint32_t q0, uint32_t q1, uint32_t q2, uint32_t q3) {
+    uint3 o;
+    o.x = __byte_perm(q0, q1, 0x6012u);
+    o.y = __byte_perm(q1, q2, 0x5601u);
+    o.z = __byte_perm(q2, q3, 0x4560u);
+    return o;
+}
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase with the given parity to complete; false after
+// kWaitLimitNs without completion.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        for (int i = 0; i < 16; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+// Bulk copy global -> shared; completion is signalled on `bar` as
+// transaction bytes. Addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_load(void* dst_smem, const void* src_gmem, uint32_t bytes,
+                                          uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bulk copy shared -> global in the current bulk group.
+__device__ __forceinline__ void bulk_store(void* dst_gmem, const void* src_smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem),
+                 "r"(smem_addr(src_smem)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Waits until at most N committed bulk groups still read shared memory.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+// Waits until at most N committed bulk groups are still in flight.
+template <int N>
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Orders this thread's generic-proxy shared-memory writes before later
+// async-proxy (bulk copy) reads of the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void st_global_cs(uint4* p, uint4 v) {
+    asm volatile("st.global.cs.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+// Minimum over the warp of a 64-bit value (only the full warp may call it).
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u < v ? u : v;
+    }
+    return v;
+}
+
+}  // namespace b64

@@ -1,0 +1,202 @@
+// Base64 encode kernels (Sec. 2 and Sec. 3.1 of Mula & Lemire).
+//
+// The paper's AVX-512 loop turns 48 input bytes into 64 characters per
+// iteration with one byte gather (vpermb), one multi-shift (vpmultishiftqb)
+// and one 64-entry table lookup (vpermb). Here the same three steps run per
+// thread on 12-byte units: __byte_perm builds the (s2,s1,s3,s2) word of each
+// triple, shifts by 10, 4, 22 and 16 pick the 6-bit values, and a 64-byte
+// shared-memory table maps them to characters (16 words in 16 distinct banks,
+// so lookups never conflict).
+//
+// Fast path (src and dst 16-byte aligned): a persistent grid, each CTA
+// streaming 12 KiB input chunks through a 4-stage ring of shared-memory
+// buffers filled by bulk (TMA) copies, and writing each warp's 512 output
+// bytes with coalesced 16-byte stores. The bytes after the last full chunk
+// (fewer than 12 KiB) and the final 1-2 bytes with their padding are done by
+// one CTA with plain loads.
+#include <mutex>
+
+#include "b64_internal.h"
+
+namespace b64 {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kUnits = 4;  // 12-byte units per thread per chunk
+constexpr uint32_t kChunkIn = kThreads * kUnits * 12;  // 12288 bytes
+constexpr uint32_t kChunkOut = kChunkIn / 3 * 4;       // 16384 characters
+constexpr int kStages = 4;
+constexpr size_t kSmem = size_t(kStages) * kChunkIn + kStages * sizeof(uint64_t);
+
+__device__ uint32_t g_fault;
+
+__device__ __forceinline__ void store4(uint8_t* p, uint32_t v, bool aligned4) {
+    if (aligned4) {
+        *reinterpret_cast<uint32_t*>(p) = v;
+    } else {
+        p[0] = uint8_t(v);
+        p[1] = uint8_t(v >> 8);
+        p[2] = uint8_t(v >> 16);
+        p[3] = uint8_t(v >> 24);
+    }
+}
+
+// Triples [t_begin, t_end) of src, strided over the calling threads.
+__device__ __forceinline__ void encode_triples_plain(const uint8_t* __restrict__ src, uint64_t t_begin,
+                                     uint64_t t_end, uint8_t* __restrict__ dst,
+                                     const uint8_t* lut, uint64_t tid, uint64_t nthreads,
+                                     bool dst_aligned4) {
+    for (uint64_t t = t_begin + tid; t < t_end; t += nthreads) {
+        const uint8_t* p = src + 3 * t;
+        const uint32_t s1 = p[0], s2 = p[1], s3 = p[2];
+        const uint32_t g = s2 | (s1 << 8) | (s3 << 16) | (s2 << 24);
+        store4(dst + 4 * t, encode_gathered(g, lut), dst_aligned4);
+    }
+}
+
+// The last n mod 3 bytes: the missing bytes count as zero, and '=' fills the
+// group to four characters when padded (Sec. 2).
+__device__ __forceinline__ void encode_tail(const uint8_t* __restrict__ src, uint64_t n,
+                            uint8_t* __restrict__ dst, const uint8_t* lut, int padded) {
+    const uint64_t t = n / 3;
+    const uint32_t r = uint32_t(n - 3 * t);
+    if (r == 0) return;
+    const uint32_t s1 = src[3 * t];
+    const uint32_t s2 = r == 2 ? src[3 * t + 1] : 0u;
+    const uint32_t g = s2 | (s1 << 8) | (s2 << 24);
+    uint8_t* o = dst + 4 * t;
+    o[0] = lut[(g >> 10) & 63u];
+    o[1] = lut[(g >> 4) & 63u];
+    if (r == 2) {
+        o[2] = lut[(g >> 22) & 63u];
+        if (padded) o[3] = '=';
+    } else if (padded) {
+        o[2] = '=';
+        o[3] = '=';
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    encode_tma_kernel(const uint8_t* __restrict__ src, uint64_t n, uint8_t* __restrict__ dst,
+                      const __grid_constant__ EncodeTable tab, int padded) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(16) uint8_t lut[64];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(kStages) * kChunkIn);
+
+    const int tid = threadIdx.x;
+    if (tid < 16) reinterpret_cast<uint32_t*>(lut)[tid] = tab.w[tid];
+
+    const uint64_t n_chunks = n / kChunkIn;
+    const uint64_t G = gridDim.x, b = blockIdx.x;
+    const uint64_t K = b < n_chunks ? (n_chunks - 1 - b) / G + 1 : 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (uint64_t k = 0; k < K && k < kStages; ++k) {
+            mbar_arrive_expect_tx(&full[k], kChunkIn);
+            bulk_load(smem + k * kChunkIn, src + (b + k * G) * kChunkIn, kChunkIn, &full[k]);
+        }
+    }
+
+    for (uint64_t k = 0; k < K; ++k) {
+        const int s = int(k % kStages);
+        const bool ok = mbar_wait(&full[s], uint32_t(k / kStages) & 1u);
+        const uint8_t* in = smem + size_t(s) * kChunkIn;
+        uint4* out = reinterpret_cast<uint4*>(dst + (b + k * G) * kChunkOut);
+#pragma unroll
+        for (int u = 0; u < kUnits; ++u) {
+            const int j = tid + u * kThreads;
+            const uint32_t* w = reinterpret_cast<const uint32_t*>(in + 12 * j);
+            out[j] = encode12(w[0], w[1], w[2], lut);
+        }
+        if (__syncthreads_or(!ok)) {
+            // A bulk copy did not arrive in time: flag it, let the copies in
+            // flight land (bounded), and stop.
+            if (tid == 0) {
+                atomicOr(&g_fault, 1u);
+                for (uint64_t k2 = k + 1; k2 < K && k2 < k + kStages; ++k2)
+                    mbar_wait(&full[k2 % kStages], uint32_t(k2 / kStages) & 1u);
+            }
+            return;
+        }
+        if (tid == 0 && k + kStages < K) {
+            mbar_arrive_expect_tx(&full[s], kChunkIn);
+            bulk_load(smem + size_t(s) * kChunkIn, src + (b + (k + kStages) * G) * kChunkIn,
+                      kChunkIn, &full[s]);
+        }
+    }
+
+    if (b == n_chunks % G) {
+        encode_triples_plain(src, n_chunks * (kChunkIn / 3), n / 3, dst, lut, tid, kThreads,
+                             true);
+        if (tid == 0) encode_tail(src, n, dst, lut, padded);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    encode_generic_kernel(const uint8_t* __restrict__ src, uint64_t n, uint8_t* __restrict__ dst,
+                          const __grid_constant__ EncodeTable tab, int padded) {
+    __shared__ __align__(16) uint8_t lut[64];
+    if (threadIdx.x < 16) reinterpret_cast<uint32_t*>(lut)[threadIdx.x] = tab.w[threadIdx.x];
+    __syncthreads();
+    const bool al4 = (reinterpret_cast<uintptr_t>(dst) & 3u) == 0;
+    encode_triples_plain(src, 0, n / 3, dst, lut, uint64_t(blockIdx.x) * blockDim.x + threadIdx.x,
+                         uint64_t(gridDim.x) * blockDim.x, al4);
+    if (blockIdx.x == 0 && threadIdx.x == 0) encode_tail(src, n, dst, lut, padded);
+}
+
+struct KernelSetup {
+    std::once_flag once;
+    cudaError_t err = cudaSuccess;
+    int ctas_per_sm = 1;
+};
+KernelSetup g_setup[64];
+
+}  // namespace
+
+cudaError_t launch_encode(const uint8_t* src, uint64_t n, uint8_t* dst, const EncodeTable& tab,
+                          int padded, cudaStream_t stream) {
+    const DeviceInfo& di = device_info();
+    const bool aligned = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) &
+                          15u) == 0;
+    if (aligned) {
+        KernelSetup& ks = g_setup[di.device & 63];
+        std::call_once(ks.once, [&] {
+            ks.err = cudaFuncSetAttribute(encode_tma_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmem));
+            if (ks.err == cudaSuccess)
+                ks.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &ks.ctas_per_sm, encode_tma_kernel, kThreads, kSmem);
+            if (ks.ctas_per_sm < 1) ks.ctas_per_sm = 1;
+        });
+        if (ks.err != cudaSuccess) return ks.err;
+        const uint64_t n_chunks = n / kChunkIn;
+        uint64_t grid = uint64_t(di.sm_count) * ks.ctas_per_sm;
+        if (n_chunks < grid) grid = n_chunks > 0 ? n_chunks : 1;
+        encode_tma_kernel<<<unsigned(grid), kThreads, kSmem, stream>>>(src, n, dst, tab, padded);
+    } else {
+        const uint64_t triples = n / 3;
+        uint64_t grid = (triples + kThreads - 1) / kThreads;
+        const uint64_t cap = uint64_t(di.sm_count) * 8;
+        if (grid > cap) grid = cap;
+        if (grid == 0) grid = 1;
+        encode_generic_kernel<<<unsigned(grid), kThreads, 0, stream>>>(src, n, dst, tab, padded);
+    }
+    return cudaGetLastError();
+}
+
+uint32_t encode_fault_flag(bool clear) {
+    uint32_t v = 0;
+    cudaMemcpyFromSymbol(&v, g_fault, sizeof(v));
+    if (clear && v) {
+        const uint32_t z = 0;
+        cudaMemcpyToSymbol(g_fault, &z, sizeof(z));
+    }
+    return v;
+}
+
+}  // namespace b64

@@ -1,0 +1,110 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+function include/*.h declares, and its host-only logic (alphabet handles,
+length helpers, argument checks) behaves as documented."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1910_05109_gb300 import build
+    build.build()
+    from paper_1910_05109_gb300 import binding
+    return binding.lib()
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(b64_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("b64_encode", "b64_decode", "b64_decode_async", "b64_alphabet_create",
+                 "b64_alphabet_standard", "b64_alphabet_url", "b64_encoded_length",
+                 "b64_decoded_max_length", "b64_last_error"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    from paper_1910_05109_gb300 import binding
+    for name in declared_functions():
+        assert hasattr(L, name), name
+        assert name in binding.SIGNATURES, f"binding lacks {name}"
+
+
+def test_lengths(L):
+    from paper_1910_05109_gb300 import binding as b
+    for n in range(0, 2000):
+        assert b.encoded_length(n, True) == 4 * ((n + 2) // 3)
+        assert b.encoded_length(n, False) == (4 * n + 2) // 3
+        assert b.decoded_max_length(n) == 3 * ((n + 3) // 4)
+    big = (1 << 40) + 1
+    assert b.encoded_length(big, True) == 4 * ((big + 2) // 3)
+
+
+def test_builtin_alphabets(L):
+    from paper_1910_05109_gb300 import binding as b
+    std, padded = b.Alphabet.standard().chars()
+    assert padded and std == b"ABCDEFGHIJKLMNOPQRSTUVWXYZabcdefghijklmnopqrstuvwxyz0123456789+/"
+    url, padded = b.Alphabet.url().chars()
+    assert not padded and url == std[:62] + b"-_"
+
+
+def test_alphabet_create_validation(L):
+    from paper_1910_05109_gb300 import binding as b
+    std = b.Alphabet.standard().chars()[0]
+    a = b.Alphabet.create(std[::-1], True)
+    assert a.chars() == (std[::-1], True)
+    for bad, why in ((std[:63] + b"A", "twice"), (std[:63] + b"=", "reserved"),
+                     (std[:63] + b"\n", "reserved"), (std[:63] + b" ", "reserved"),
+                     (std[:63] + b"\x80", "reserved")):
+        with pytest.raises(b.B64Error, match=why):
+            b.Alphabet.create(bad, True)
+    assert L.b64_alphabet_create(None, 1) is None
+
+
+def test_argument_errors_without_gpu(L):
+    from paper_1910_05109_gb300 import binding as b
+    std = L.b64_alphabet_standard()
+    # Rejected before any CUDA call is made.
+    assert L.b64_encode(None, 10, None, std, None) == b.B64_E_INVAL
+    assert "NULL" in b.last_error()
+    assert L.b64_encode(None, 0, None, std, None) == 0
+    assert L.b64_encode(16, 10, 16, None, None) == b.B64_E_INVAL
+    assert L.b64_decode_async(None, 4, None, std, None, None) == b.B64_ERR_INVALID_ARGUMENT
+    assert L.b64_decode_async(256, 4, 4096, std, 4099, None) == b.B64_ERR_INVALID_ARGUMENT
+    assert "aligned" in b.last_error()
+    # Overlapping src/dst are refused.
+    assert L.b64_encode(4096, 300, 4096 + 100, std, None) == b.B64_E_INVAL
+    assert "overlap" in b.last_error()
+    assert L.b64_decode_async(4096, 400, 4096 + 100, std, 8, None) == \
+        b.B64_ERR_INVALID_ARGUMENT
+
+
+def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
+    from paper_1910_05109_gb300 import binding as b
+    monkeypatch.setattr(b, "LIB_PATH", str(tmp_path / "absent.so"))
+    monkeypatch.setattr(b, "_lib", None)
+    with pytest.raises(b.B64Error, match="missing"):
+        b.lib()
+
+
+def test_package_never_imports_oracle():
+    pkg = os.path.join(ROOT, "paper_1910_05109_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in text.lower() or f == "workloads.py" and \
+                    "import oracle" not in text, f

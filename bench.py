@@ -364,7 +364,7 @@ def finish(args, v):
     dominant = "decode" if dec_avg >= enc_avg else "encode"
     dom_ms = dec_avg if dominant == "decode" else enc_avg
     achieved = (dec_alg if dominant == "decode" else enc_alg) / (dom_ms / 1e3) / 1e9
-    kname = "decode_tma_kernel" if dominant == "decode" else "encode_tma_kernel"
+    kname = "decode_fast_kernel" if dominant == "decode" else "encode_tma_kernel"
     tr = profiled_traffic(kname)
     traffic = None
     if tr is not None:

@@ -50,9 +50,10 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _inputs())
 
 
-def _compile(src: str, ptxas_verbose: bool) -> tuple[str, str]:
-    obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", src, "-o", obj]
+def _compile(src: str, ptxas_verbose: bool, build_dir: str = BUILD_DIR,
+             defines: tuple[str, ...] = ()) -> tuple[str, str]:
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
+    cmd = [nvcc(), *ARCH, *FLAGS, *[f"-D{d}" for d in defines], "-c", src, "-o", obj]
     if ptxas_verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -61,26 +62,33 @@ def _compile(src: str, ptxas_verbose: bool) -> tuple[str, str]:
     return obj, r.stdout + r.stderr
 
 
-def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True) -> str:
-    if not force and not ptxas_verbose and up_to_date():
+def build(force: bool = False, ptxas_verbose: bool = False, quiet: bool = True,
+          defines: tuple[str, ...] = (), lib_path: str | None = None) -> str:
+    """Builds the library. `defines` (NAME=VALUE) override the kernels'
+    compile-time tile parameters; with `lib_path` the result goes there
+    instead of the package directory (for building variants side by side)."""
+    out_path = lib_path or LIB_PATH
+    if not force and not ptxas_verbose and not defines and lib_path is None and up_to_date():
         return LIB_PATH
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    build_dir = BUILD_DIR if lib_path is None else os.path.join(os.path.dirname(out_path), "_obj")
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        results = list(ex.map(lambda s: _compile(s, ptxas_verbose), srcs))
+        results = list(ex.map(lambda s: _compile(s, ptxas_verbose, build_dir, tuple(defines)),
+                              srcs))
     objs = [o for o, _ in results]
     if not quiet or ptxas_verbose:
         for _, log in results:
             if log.strip():
                 print(log, file=sys.stderr)
-    tmp = LIB_PATH + f".{os.getpid()}.tmp"
+    tmp = out_path + f".{os.getpid()}.tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-lpthread",
            "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, out_path)
+    return out_path
 
 
 if __name__ == "__main__":

@@ -9,33 +9,46 @@
 // units: byte lookups in a 256-entry shared-memory table (entries >= 0x80 are
 // all 0x80, which folds in the test of the input's top bit), shifts and ORs
 // for the merge, __byte_perm for the pack, and an OR-accumulated error word
-// that is tested once per chunk by a block-wide vote. Only a chunk that holds
+// that is tested once per chunk by a warp-wide vote. Only a chunk that holds
 // a bad byte looks for its exact offset (cold path) and folds it into the
 // call's result with an atomic minimum.
 //
-// Fast path (src and dst 16-byte aligned): a persistent grid; each CTA
-// streams 16 KiB chunks through a 4-stage ring filled by bulk (TMA) loads,
-// writes the 12 KiB of output into a 2-stage shared-memory ring, and stores
-// it with bulk (TMA) stores. The body (all but the last 2 to 5 characters) is
-// done by this kernel; a one-thread kernel then checks the padding and length
-// rules on the tail, decodes it and writes the call's result.
+// Fast path (src and dst 16-byte aligned): a persistent grid in which every
+// warp works alone on "warp chunks" of 32 x kUnits x 16 characters. Each lane
+// loads its kUnits 16-byte units of the next chunk straight into registers
+// (coalesced: 512 contiguous bytes per warp instruction, streamed past L1)
+// while it decodes the current one, writes its 12-byte results into a ring
+// of kOutStages shared-memory buffers, and lane 0 stores each buffer with a
+// bulk (TMA) store. The error vote and the cold-path search are warp-wide, so
+// no block-wide barrier is taken inside the loop. The body (all but the last
+// 2 to 5 characters) is done by this kernel; a one-thread kernel then checks
+// the padding and length rules on the tail, decodes it and writes the call's
+// result.
 #include <mutex>
 
 #include "b64_internal.h"
 
+#ifndef B64_DEC_WARPS
+#define B64_DEC_WARPS 4
+#endif
+#ifndef B64_DEC_UNITS
+#define B64_DEC_UNITS 8
+#endif
+#ifndef B64_DEC_OUT_STAGES
+#define B64_DEC_OUT_STAGES 2
+#endif
+
 namespace b64 {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kUnits = 4;                              // 16-character units per thread
-constexpr uint32_t kChunkIn = kThreads * kUnits * 16;  // 16384 characters
-constexpr uint32_t kChunkOut = kChunkIn / 4 * 3;       // 12288 bytes
-constexpr int kStagesIn = 4;
-constexpr int kStagesOut = 2;
-constexpr size_t kSmem =
-    size_t(kStagesIn) * kChunkIn + size_t(kStagesOut) * kChunkOut + kStagesIn * sizeof(uint64_t);
-
-__device__ uint32_t g_fault;
+constexpr int kWarps = B64_DEC_WARPS;
+constexpr int kThreads = 32 * kWarps;
+constexpr int kUnits = B64_DEC_UNITS;                // 16-character units per lane per chunk
+constexpr int kStagesOut = B64_DEC_OUT_STAGES;
+constexpr uint32_t kChunkIn = 32 * kUnits * 16;      // characters per warp chunk
+constexpr uint32_t kChunkOut = kChunkIn / 4 * 3;     // bytes per warp chunk
+constexpr size_t kSmem = size_t(kWarps) * kStagesOut * kChunkOut;
+static_assert(kChunkOut % 16 == 0, "bulk copies need 16-byte multiples");
 
 // Characters [0, body) are whole groups of four that cannot contain valid
 // padding; the last 2..5 characters (all of them when m < 6) are the tail.
@@ -85,51 +98,60 @@ __device__ void block_min_to_global(uint64_t first, unsigned long long* d_err) {
     if ((threadIdx.x & 31) == 0 && w != kNoError) atomicMin(d_err, (unsigned long long)w);
 }
 
+__device__ __forceinline__ uint4 load_stream16(const uint8_t* p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ int first_bad_in(uint32_t w, const uint8_t* lut) {
+    for (int i = 0; i < 4; ++i)
+        if (lut[(w >> (8 * i)) & 0xFFu] & kBad) return i;
+    return -1;
+}
+
 __global__ void __launch_bounds__(kThreads)
-    decode_tma_kernel(const uint8_t* __restrict__ src, uint64_t body, uint8_t* __restrict__ dst,
-                      const __grid_constant__ DecodeTable tab, unsigned long long* d_err) {
+    decode_fast_kernel(const uint8_t* __restrict__ src, uint64_t body, uint8_t* __restrict__ dst,
+                       const __grid_constant__ DecodeTable tab, unsigned long long* d_err) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(16) uint8_t lut[256];
-    uint8_t* sin = smem;
-    uint8_t* sout = smem + size_t(kStagesIn) * kChunkIn;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sout + size_t(kStagesOut) * kChunkOut);
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint8_t* sout = smem + size_t(warp) * kStagesOut * kChunkOut;
     if (tid < 64) reinterpret_cast<uint32_t*>(lut)[tid] = tab.w[tid];
+    __syncthreads();
 
     const uint64_t n_chunks = body / kChunkIn;
-    const uint64_t G = gridDim.x, b = blockIdx.x;
-    const uint64_t K = b < n_chunks ? (n_chunks - 1 - b) / G + 1 : 0;
+    const uint64_t GW = uint64_t(gridDim.x) * kWarps;
+    const uint64_t gw = uint64_t(blockIdx.x) * kWarps + warp;
+    const uint64_t K = gw < n_chunks ? (n_chunks - 1 - gw) / GW + 1 : 0;
 
-    if (tid == 0) {
-        for (int s = 0; s < kStagesIn; ++s) mbar_init(&full[s], 1);
-        fence_mbar_init();
+    uint4 cur[kUnits], nxt[kUnits];
+    if (K > 0) {
+#pragma unroll
+        for (int u = 0; u < kUnits; ++u)
+            cur[u] = load_stream16(src + gw * kChunkIn + 16 * (lane + 32 * u));
     }
-    __syncthreads();
-    if (tid == 0) {
-        for (uint64_t k = 0; k < K && k < kStagesIn; ++k) {
-            mbar_arrive_expect_tx(&full[k], kChunkIn);
-            bulk_load(sin + k * kChunkIn, src + (b + k * G) * kChunkIn, kChunkIn, &full[k]);
-        }
-    }
-
     for (uint64_t k = 0; k < K; ++k) {
-        const int s = int(k % kStagesIn);
+        const uint64_t chunk = gw + k * GW;
+        if (k + 1 < K) {
+#pragma unroll
+            for (int u = 0; u < kUnits; ++u)
+                nxt[u] = load_stream16(src + (chunk + GW) * kChunkIn + 16 * (lane + 32 * u));
+        }
+        // The bulk store that last read this output buffer (kStagesOut chunks
+        // ago) must be done reading it before it is overwritten.
         const int so = int(k % kStagesOut);
-        const uint64_t chunk = b + k * G;
-        const bool ok = mbar_wait(&full[s], uint32_t(k / kStagesIn) & 1u);
-        // The bulk store that last read sout[so] (kStagesOut chunks ago) must
-        // be done reading before the buffer is overwritten.
-        if (tid == 0) bulk_wait_read<kStagesOut - 1>();
-        __syncthreads();
-
-        const uint4* in = reinterpret_cast<const uint4*>(sin + size_t(s) * kChunkIn);
+        if (lane == 0) bulk_wait_read<kStagesOut - 1>();
+        __syncwarp();
         uint8_t* out = sout + size_t(so) * kChunkOut;
         uint32_t err = 0;
 #pragma unroll
         for (int u = 0; u < kUnits; ++u) {
-            const int j = tid + u * kThreads;
-            const uint4 c = in[j];
+            const int j = lane + 32 * u;
+            const uint4 c = cur[u];
             const uint32_t q0 = decode4(c.x, lut, err);
             const uint32_t q1 = decode4(c.y, lut, err);
             const uint32_t q2 = decode4(c.z, lut, err);
@@ -141,51 +163,38 @@ __global__ void __launch_bounds__(kThreads)
             ow[2] = o.z;
         }
         fence_proxy_async_smem();
-        if (__syncthreads_or(int(err & kBad) | int(!ok))) {
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) {
-                    atomicOr(&g_fault, 1u);
-                    for (uint64_t k2 = k + 1; k2 < K && k2 < k + kStagesIn; ++k2)
-                        mbar_wait(&full[k2 % kStagesIn], uint32_t(k2 / kStagesIn) & 1u);
-                    bulk_wait_read<0>();
-                }
-                return;
-            }
-            // Cold path: the exact first bad offset of this chunk.
+        if (__any_sync(0xffffffffu, err & kBad)) {
+            // Cold path: the exact first bad offset of this warp chunk, from
+            // the characters still held in registers.
             uint64_t first = kNoError;
-            if (err & kBad) {
-                const uint8_t* cin = sin + size_t(s) * kChunkIn;
-                for (int u = 0; u < kUnits && first == kNoError; ++u) {
-                    const int j = tid + u * kThreads;
-                    for (int i = 0; i < 16; ++i) {
-                        if (lut[cin[16 * j + i]] & kBad) {
-                            first = chunk * kChunkIn + uint64_t(16 * j + i);
-                            break;
-                        }
-                    }
+#pragma unroll
+            for (int u = 0; u < kUnits; ++u) {
+                const uint32_t w4[4] = {cur[u].x, cur[u].y, cur[u].z, cur[u].w};
+                for (int q = 0; q < 4 && first == kNoError; ++q) {
+                    const int i = first_bad_in(w4[q], lut);
+                    if (i >= 0)
+                        first = chunk * kChunkIn + uint64_t(16 * (lane + 32 * u) + 4 * q + i);
                 }
+                if (first != kNoError) break;
             }
-            block_min_to_global(first, d_err);
-            // Every warp must be done rescanning sin[s] before thread 0
-            // refills it with the next chunk below.
-            __syncthreads();
+            const uint64_t w = warp_min_u64(first);
+            if (lane == 0 && w != kNoError) atomicMin(d_err, (unsigned long long)w);
         }
-        if (tid == 0) {
+        __syncwarp();
+        if (lane == 0) {
             bulk_store(dst + chunk * kChunkOut, out, kChunkOut);
             bulk_commit();
-            if (k + kStagesIn < K) {
-                mbar_arrive_expect_tx(&full[s], kChunkIn);
-                bulk_load(sin + size_t(s) * kChunkIn, src + (b + (k + kStagesIn) * G) * kChunkIn,
-                          kChunkIn, &full[s]);
-            }
         }
+#pragma unroll
+        for (int u = 0; u < kUnits; ++u) cur[u] = nxt[u];
     }
-    if (tid == 0) bulk_wait_read<0>();
+    if (lane == 0) bulk_wait_read<0>();
 
-    if (b == n_chunks % G) {
+    if (gw == n_chunks % GW) {
         const uint64_t first = decode_quads_plain(src, n_chunks * (kChunkIn / 4), body / 4, dst,
-                                                  lut, tid, kThreads, true);
-        block_min_to_global(first, d_err);
+                                                  lut, lane, 32, true);
+        const uint64_t w = warp_min_u64(first);
+        if (lane == 0 && w != kNoError) atomicMin(d_err, (unsigned long long)w);
     }
 }
 
@@ -274,19 +283,20 @@ cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const De
         if (aligned) {
             KernelSetup& ks = g_setup[di.device & 63];
             std::call_once(ks.once, [&] {
-                ks.err = cudaFuncSetAttribute(decode_tma_kernel,
+                ks.err = cudaFuncSetAttribute(decode_fast_kernel,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               int(kSmem));
                 if (ks.err == cudaSuccess)
                     ks.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        &ks.ctas_per_sm, decode_tma_kernel, kThreads, kSmem);
+                        &ks.ctas_per_sm, decode_fast_kernel, kThreads, kSmem);
                 if (ks.ctas_per_sm < 1) ks.ctas_per_sm = 1;
             });
             if (ks.err != cudaSuccess) return ks.err;
             const uint64_t n_chunks = body / kChunkIn;
+            const uint64_t want = (n_chunks + kWarps - 1) / kWarps;
             uint64_t grid = uint64_t(di.sm_count) * ks.ctas_per_sm;
-            if (n_chunks < grid) grid = n_chunks > 0 ? n_chunks : 1;
-            decode_tma_kernel<<<unsigned(grid), kThreads, kSmem, stream>>>(src, body, dst, tab,
+            if (want < grid) grid = want > 0 ? want : 1;
+            decode_fast_kernel<<<unsigned(grid), kThreads, kSmem, stream>>>(src, body, dst, tab,
                                                                              d_err);
         } else {
             const uint64_t quads = body / 4;
@@ -304,14 +314,5 @@ cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const De
     return cudaGetLastError();
 }
 
-uint32_t decode_fault_flag(bool clear) {
-    uint32_t v = 0;
-    cudaMemcpyFromSymbol(&v, g_fault, sizeof(v));
-    if (clear && v) {
-        const uint32_t z = 0;
-        cudaMemcpyToSymbol(g_fault, &z, sizeof(z));
-    }
-    return v;
-}
 
 }  // namespace b64

@@ -6,6 +6,10 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#ifndef B64_JOIN_WITH_PRMT
+#define B64_JOIN_WITH_PRMT 0
+#endif
+
 namespace b64 {
 
 // ------------------------------------------------------------------ tables
@@ -32,6 +36,17 @@ constexpr uint64_t kNoError = ~0ull;
 // Bounded waits give up after this many nanoseconds of %globaltimer.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
+// Joins four bytes (each < 256) into a word, c0 in the low byte. Written as
+// multiply-adds so that it runs on the FMA pipe, leaving the ALU pipe (which
+// the shifts, masks and byte permutes load) free.
+__device__ __forceinline__ uint32_t join4(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) {
+#if B64_JOIN_WITH_PRMT
+    return __byte_perm(__byte_perm(c0, c1, 0x7740u), __byte_perm(c2, c3, 0x7740u), 0x5410u);
+#else
+    return (c3 * 256u + c2) * 65536u + (c1 * 256u + c0);
+#endif
+}
+
 // ------------------------------------------------------------------ encode step
 // Sec. 3.1: a triple (s1,s2,s3) is first spread into the 32-bit word whose
 // bytes, lowest first, are (s2,s1,s3,s2); then the four 6-bit values sit at
@@ -41,7 +56,7 @@ __device__ __forceinline__ uint32_t encode_gathered(uint32_t g, const uint8_t* l
     const uint32_t c1 = lut[(g >> 4) & 63u];
     const uint32_t c2 = lut[(g >> 22) & 63u];
     const uint32_t c3 = lut[(g >> 16) & 63u];
-    return __byte_perm(__byte_perm(c0, c1, 0x7740u), __byte_perm(c2, c3, 0x7740u), 0x5410u);
+    return join4(c0, c1, c2, c3);
 }
 
 // Encodes 12 bytes held in three little-endian words (x = bytes 0..3,
@@ -67,7 +82,7 @@ __device__ __forceinline__ uint32_t decode4(uint32_t w, const uint8_t* lut, uint
     const uint32_t c = lut[__byte_perm(w, 0, 0x4442u)];
     const uint32_t d = lut[__byte_perm(w, 0, 0x4443u)];
     err |= a | b | c | d;
-    return (((a << 6 | b) << 6 | c) << 6) | d;
+    return ((a * 64u + b) * 64u + c) * 64u + d;
 }
 
 // Packs four 24-bit values into 12 output bytes (three words), each value

@@ -8,25 +8,40 @@
 // shared-memory table maps them to characters (16 words in 16 distinct banks,
 // so lookups never conflict).
 //
-// Fast path (src and dst 16-byte aligned): a persistent grid, each CTA
-// streaming 12 KiB input chunks through a 4-stage ring of shared-memory
-// buffers filled by bulk (TMA) copies, and writing each warp's 512 output
-// bytes with coalesced 16-byte stores. The bytes after the last full chunk
-// (fewer than 12 KiB) and the final 1-2 bytes with their padding are done by
-// one CTA with plain loads.
+// Fast path (src and dst 16-byte aligned): a persistent grid in which every
+// warp is its own pipeline. A warp streams "warp chunks" of 32 x kUnits x 12
+// input bytes through a ring of kStages shared-memory buffers that its lane 0
+// fills with bulk (TMA) copies, each completing on the warp's own mbarrier;
+// the lanes turn each chunk into characters and write them with coalesced
+// 16-byte stores (512 contiguous bytes per warp instruction). No block-wide
+// barrier is taken inside the loop, so warps never wait for one another.
+// The bytes after the last whole warp chunk and the final 1-2 bytes with
+// their padding are done by one warp with plain loads.
 #include <mutex>
 
 #include "b64_internal.h"
 
+#ifndef B64_ENC_WARPS
+#define B64_ENC_WARPS 16
+#endif
+#ifndef B64_ENC_UNITS
+#define B64_ENC_UNITS 1
+#endif
+#ifndef B64_ENC_STAGES
+#define B64_ENC_STAGES 4
+#endif
+
 namespace b64 {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kUnits = 4;  // 12-byte units per thread per chunk
-constexpr uint32_t kChunkIn = kThreads * kUnits * 12;  // 12288 bytes
-constexpr uint32_t kChunkOut = kChunkIn / 3 * 4;       // 16384 characters
-constexpr int kStages = 4;
-constexpr size_t kSmem = size_t(kStages) * kChunkIn + kStages * sizeof(uint64_t);
+constexpr int kWarps = B64_ENC_WARPS;
+constexpr int kThreads = 32 * kWarps;
+constexpr int kUnits = B64_ENC_UNITS;                // 12-byte units per lane per chunk
+constexpr int kStages = B64_ENC_STAGES;
+constexpr uint32_t kChunkIn = 32 * kUnits * 12;      // input bytes per warp chunk
+constexpr uint32_t kChunkOut = kChunkIn / 3 * 4;     // characters per warp chunk
+constexpr size_t kSmem = size_t(kWarps) * kStages * (kChunkIn + sizeof(uint64_t));
+static_assert(kChunkIn % 16 == 0 && kChunkIn % 3 == 0, "bulk copies need 16-byte multiples");
 
 __device__ uint32_t g_fault;
 
@@ -81,59 +96,62 @@ __global__ void __launch_bounds__(kThreads)
                       const __grid_constant__ EncodeTable tab, int padded) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(16) uint8_t lut[64];
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(kStages) * kChunkIn);
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint8_t* ring = smem + size_t(warp) * kStages * kChunkIn;
+    uint64_t* full =
+        reinterpret_cast<uint64_t*>(smem + size_t(kWarps) * kStages * kChunkIn) + warp * kStages;
+
     if (tid < 16) reinterpret_cast<uint32_t*>(lut)[tid] = tab.w[tid];
-
-    const uint64_t n_chunks = n / kChunkIn;
-    const uint64_t G = gridDim.x, b = blockIdx.x;
-    const uint64_t K = b < n_chunks ? (n_chunks - 1 - b) / G + 1 : 0;
-
-    if (tid == 0) {
+    if (lane == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    if (tid == 0) {
+
+    const uint64_t n_chunks = n / kChunkIn;
+    const uint64_t GW = uint64_t(gridDim.x) * kWarps;
+    const uint64_t gw = uint64_t(blockIdx.x) * kWarps + warp;
+    const uint64_t K = gw < n_chunks ? (n_chunks - 1 - gw) / GW + 1 : 0;
+
+    if (lane == 0) {
         for (uint64_t k = 0; k < K && k < kStages; ++k) {
             mbar_arrive_expect_tx(&full[k], kChunkIn);
-            bulk_load(smem + k * kChunkIn, src + (b + k * G) * kChunkIn, kChunkIn, &full[k]);
+            bulk_load(ring + k * kChunkIn, src + (gw + k * GW) * kChunkIn, kChunkIn, &full[k]);
         }
     }
-
     for (uint64_t k = 0; k < K; ++k) {
         const int s = int(k % kStages);
         const bool ok = mbar_wait(&full[s], uint32_t(k / kStages) & 1u);
-        const uint8_t* in = smem + size_t(s) * kChunkIn;
-        uint4* out = reinterpret_cast<uint4*>(dst + (b + k * G) * kChunkOut);
-#pragma unroll
-        for (int u = 0; u < kUnits; ++u) {
-            const int j = tid + u * kThreads;
-            const uint32_t* w = reinterpret_cast<const uint32_t*>(in + 12 * j);
-            out[j] = encode12(w[0], w[1], w[2], lut);
-        }
-        if (__syncthreads_or(!ok)) {
+        if (!__all_sync(0xffffffffu, ok)) {
             // A bulk copy did not arrive in time: flag it, let the copies in
-            // flight land (bounded), and stop.
-            if (tid == 0) {
+            // flight land (bounded), and stop this warp.
+            if (lane == 0) {
                 atomicOr(&g_fault, 1u);
-                for (uint64_t k2 = k + 1; k2 < K && k2 < k + kStages; ++k2)
+                for (uint64_t k2 = k; k2 < K && k2 < k + kStages; ++k2)
                     mbar_wait(&full[k2 % kStages], uint32_t(k2 / kStages) & 1u);
             }
             return;
         }
-        if (tid == 0 && k + kStages < K) {
+        const uint8_t* in = ring + size_t(s) * kChunkIn;
+        uint4* out = reinterpret_cast<uint4*>(dst + (gw + k * GW) * kChunkOut);
+#pragma unroll
+        for (int u = 0; u < kUnits; ++u) {
+            const int j = lane + 32 * u;
+            const uint32_t* w = reinterpret_cast<const uint32_t*>(in + 12 * j);
+            out[j] = encode12(w[0], w[1], w[2], lut);
+        }
+        __syncwarp();
+        if (lane == 0 && k + kStages < K) {
             mbar_arrive_expect_tx(&full[s], kChunkIn);
-            bulk_load(smem + size_t(s) * kChunkIn, src + (b + (k + kStages) * G) * kChunkIn,
+            bulk_load(ring + size_t(s) * kChunkIn, src + (gw + (k + kStages) * GW) * kChunkIn,
                       kChunkIn, &full[s]);
         }
     }
 
-    if (b == n_chunks % G) {
-        encode_triples_plain(src, n_chunks * (kChunkIn / 3), n / 3, dst, lut, tid, kThreads,
-                             true);
-        if (tid == 0) encode_tail(src, n, dst, lut, padded);
+    if (gw == n_chunks % GW) {
+        encode_triples_plain(src, n_chunks * (kChunkIn / 3), n / 3, dst, lut, lane, 32, true);
+        if (lane == 0) encode_tail(src, n, dst, lut, padded);
     }
 }
 
@@ -175,8 +193,9 @@ cudaError_t launch_encode(const uint8_t* src, uint64_t n, uint8_t* dst, const En
         });
         if (ks.err != cudaSuccess) return ks.err;
         const uint64_t n_chunks = n / kChunkIn;
+        const uint64_t want = (n_chunks + kWarps - 1) / kWarps;
         uint64_t grid = uint64_t(di.sm_count) * ks.ctas_per_sm;
-        if (n_chunks < grid) grid = n_chunks > 0 ? n_chunks : 1;
+        if (want < grid) grid = want > 0 ? want : 1;
         encode_tma_kernel<<<unsigned(grid), kThreads, kSmem, stream>>>(src, n, dst, tab, padded);
     } else {
         const uint64_t triples = n / 3;

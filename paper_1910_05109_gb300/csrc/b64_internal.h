@@ -34,6 +34,5 @@ uint32_t encode_fault_flag(bool clear);
 // or -(offset+1). d_result must already hold ~0 (no error) if m > 0.
 cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const DecodeTable& tab,
                           int padded, int64_t* d_result, cudaStream_t stream);
-uint32_t decode_fault_flag(bool clear);
 
 }  // namespace b64

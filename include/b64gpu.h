@@ -122,6 +122,49 @@ int b64_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b64_alp
 int64_t b64_decode(const uint8_t* src, size_t len, uint8_t* dst, const b64_alphabet* a,
                    void* stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent strings in one launch sequence (prep kernel, one
+ * persistent tile kernel, and for decode a per-string finalize kernel), all
+ * on `stream`, so it can be recorded in a CUDA graph. Batching is not in the
+ * paper; each string is coded exactly as the single-buffer calls code it.
+ *
+ * String i is src[src_off[i] .. src_off[i+1]) (src_off: n+1 device int64,
+ * non-decreasing, src_off[0] may be > 0) and is written at dst + dst_off[i]
+ * (dst_off: n device int64; each string needs its capacity, see
+ * b64_batch_offsets). alph_id: n device bytes selecting one of the
+ * n_alphabets (1..B64_BATCH_MAX_ALPHABETS) handles, or NULL for alphabet 0;
+ * an id >= n_alphabets is a caller error (it is taken modulo
+ * B64_BATCH_MAX_ALPHABETS and reads a repeat of alphabet 0). results: n
+ * device int64, receiving what the single-buffer call returns for that string
+ * (encode: output length; decode: length or -(offset+1), offset within the
+ * string). tile_units: bytes per thread of a tile as 1, 2, 4 or 8 units of
+ * 12 input bytes (encode) or 16 characters (decode); 0 picks 4. workspace:
+ * device memory of at least b64_batch_workspace_size(n) bytes, 256-byte
+ * aligned, owned by the caller and busy until the enqueued work completes.
+ * Strings may start at any alignment; src and dst may be NULL only if every
+ * string is empty. Returns B64_SUCCESS or an error code; nothing is enqueued
+ * on error. n == 0 enqueues nothing. */
+#define B64_BATCH_MAX_ALPHABETS 4
+
+size_t b64_batch_workspace_size(int64_t n);
+
+int b64_encode_batch(const uint8_t* src, const int64_t* src_off, int64_t n, uint8_t* dst,
+                     const int64_t* dst_off, const b64_alphabet* const* alphabets,
+                     int n_alphabets, const uint8_t* alph_id, int64_t* results, int tile_units,
+                     void* workspace, size_t workspace_bytes, void* stream);
+
+int b64_decode_batch(const uint8_t* src, const int64_t* src_off, int64_t n, uint8_t* dst,
+                     const int64_t* dst_off, const b64_alphabet* const* alphabets,
+                     int n_alphabets, const uint8_t* alph_id, int64_t* results, int tile_units,
+                     void* workspace, size_t workspace_bytes, void* stream);
+
+/* dst_off[0..n] (n+1 device int64) = exclusive scan of each string's output
+ * capacity: its encoded length (decode == 0) or 3*ceil(len/4) (decode != 0).
+ * dst_off[n] is the total. One kernel on `stream`. */
+int b64_batch_offsets(const int64_t* src_off, int64_t n, const b64_alphabet* const* alphabets,
+                      int n_alphabets, const uint8_t* alph_id, int decode, int64_t* dst_off,
+                      void* stream);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 /* Thread-local message for the last failed call of this thread ("" if none). */

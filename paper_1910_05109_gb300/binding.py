@@ -37,6 +37,10 @@ SIGNATURES = {
     "b64_encode": (_I64, [_P, _SZ, _P, _P, _P]),
     "b64_decode_async": (_I, [_P, _SZ, _P, _P, _P, _P]),
     "b64_decode": (_I64, [_P, _SZ, _P, _P, _P]),
+    "b64_batch_workspace_size": (_SZ, [_I64]),
+    "b64_encode_batch": (_I, [_P, _P, _I64, _P, _P, _P, _I, _P, _P, _I, _P, _SZ, _P]),
+    "b64_decode_batch": (_I, [_P, _P, _I64, _P, _P, _P, _I, _P, _P, _I, _P, _SZ, _P]),
+    "b64_batch_offsets": (_I, [_P, _I64, _P, _I, _P, _I, _P, _P]),
     "b64_last_error": (ctypes.c_char_p, []),
     "b64_device_fault_flag": (_I, [_I]),
     "b64_version": (_I, []),
@@ -187,3 +191,85 @@ def device_fault_flag(clear: bool = False) -> int:
     if r < 0:
         raise B64Error(last_error())
     return r
+
+
+# ---------------------------------------------------------------- batches
+
+BATCH_MAX_ALPHABETS = 4
+
+
+def _alphabet_array(alphabets):
+    alphabets = list(alphabets)
+    if not 1 <= len(alphabets) <= BATCH_MAX_ALPHABETS:
+        raise B64Error(f"need 1..{BATCH_MAX_ALPHABETS} alphabets")
+    arr = (ctypes.c_void_p * len(alphabets))(*[a.handle for a in alphabets])
+    return arr, len(alphabets)
+
+
+def _dev(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
+    if t.device.type != "cuda" or t.dtype != dtype or not t.is_contiguous():
+        raise B64Error(f"{name} must be a contiguous CUDA {dtype} tensor")
+    return t
+
+
+def batch_workspace(n: int, device=None) -> torch.Tensor:
+    nbytes = lib().b64_batch_workspace_size(n)
+    # torch's caching allocator returns blocks aligned to at least 512 bytes
+    return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device or "cuda")
+
+
+def batch_offsets(src_off: torch.Tensor, alphabets, alph_id: torch.Tensor | None,
+                  decode: bool, stream=None) -> torch.Tensor:
+    """Device int64[n+1]: exclusive scan of per-string output capacities."""
+    src_off = _dev(src_off, torch.int64, "src_off")
+    n = src_off.numel() - 1
+    arr, na = _alphabet_array(alphabets)
+    out = torch.empty(n + 1, dtype=torch.int64, device=src_off.device)
+    aid = 0 if alph_id is None else _dev(alph_id, torch.uint8, "alph_id").data_ptr()
+    rc = lib().b64_batch_offsets(src_off.data_ptr(), n, arr, na, aid, int(decode),
+                                 out.data_ptr(), _stream_ptr(stream))
+    if rc != B64_SUCCESS:
+        raise B64Error(last_error())
+    return out
+
+
+def _batch(fn, src, src_off, dst, dst_off, alphabets, alph_id, results, tile_units, workspace,
+           stream):
+    src = _dev_u8(src, "src")
+    dst = _dev_u8(dst, "dst")
+    src_off = _dev(src_off, torch.int64, "src_off")
+    dst_off = _dev(dst_off, torch.int64, "dst_off")
+    results = _dev(results, torch.int64, "results")
+    n = src_off.numel() - 1
+    arr, na = _alphabet_array(alphabets)
+    aid = 0 if alph_id is None else _dev(alph_id, torch.uint8, "alph_id").data_ptr()
+    if workspace is None:
+        workspace = batch_workspace(n, src.device)
+    rc = fn(src.data_ptr(), src_off.data_ptr(), n, dst.data_ptr(), dst_off.data_ptr(), arr, na,
+            aid, results.data_ptr(), int(tile_units), workspace.data_ptr(), workspace.numel(),
+            _stream_ptr(stream))
+    if rc != B64_SUCCESS:
+        raise B64Error(last_error())
+    return workspace
+
+
+def encode_batch(src, src_off, dst, dst_off, alphabets, alph_id=None, results=None,
+                 tile_units: int = 0, workspace=None, stream=None):
+    """Enqueues a batched encode; returns the results tensor (int64[n])."""
+    n = src_off.numel() - 1
+    if results is None:
+        results = torch.empty(max(n, 1), dtype=torch.int64, device=src.device)
+    _batch(lib().b64_encode_batch, src, src_off, dst, dst_off, alphabets, alph_id, results,
+           tile_units, workspace, stream)
+    return results[:n]
+
+
+def decode_batch(src, src_off, dst, dst_off, alphabets, alph_id=None, results=None,
+                 tile_units: int = 0, workspace=None, stream=None):
+    """Enqueues a batched strict decode; returns the results tensor (int64[n])."""
+    n = src_off.numel() - 1
+    if results is None:
+        results = torch.empty(max(n, 1), dtype=torch.int64, device=src.device)
+    _batch(lib().b64_decode_batch, src, src_off, dst, dst_off, alphabets, alph_id, results,
+           tile_units, workspace, stream)
+    return results[:n]

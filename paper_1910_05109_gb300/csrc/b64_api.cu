@@ -230,6 +230,82 @@ int64_t b64_decode(const uint8_t* src, size_t len, uint8_t* dst, const b64_alpha
     return *sc.h_word;
 }
 
+size_t b64_batch_workspace_size(int64_t n) { return n > 0 ? batch_workspace_bytes(n) : 0; }
+
+static int batch_tables(const char* fn, const b64_alphabet* const* alphabets, int n_alphabets,
+                        BatchTables* t) {
+    if (!alphabets || n_alphabets < 1 || n_alphabets > B64_BATCH_MAX_ALPHABETS)
+        return set_error(B64_ERR_INVALID_ARGUMENT, "%s: need 1..%d alphabets", fn,
+                         B64_BATCH_MAX_ALPHABETS);
+    for (int k = 0; k < kMaxAlphabets; ++k) {
+        const b64_alphabet* a = alphabets[k < n_alphabets ? k : 0];
+        if (!a) return set_error(B64_ERR_INVALID_ARGUMENT, "%s: alphabet %d is NULL", fn, k);
+        t->enc[k] = a->enc;
+        t->dec[k] = a->dec;
+        t->padded[k] = a->padded;
+    }
+    return B64_SUCCESS;
+}
+
+static int batch_common(bool decode, const uint8_t* src, const int64_t* src_off, int64_t n,
+                        uint8_t* dst, const int64_t* dst_off, const b64_alphabet* const* alphabets,
+                        int n_alphabets, const uint8_t* alph_id, int64_t* results, int tile_units,
+                        void* workspace, size_t workspace_bytes, void* stream) {
+    const char* fn = decode ? "b64_decode_batch" : "b64_encode_batch";
+    if (n < 0) return set_error(B64_ERR_INVALID_ARGUMENT, "%s: n < 0", fn);
+    BatchTables tabs;
+    const int rc = batch_tables(fn, alphabets, n_alphabets, &tabs);
+    if (rc != B64_SUCCESS) return rc;
+    if (n == 0) return B64_SUCCESS;
+    // src and dst may be NULL when every string is empty (nothing reads them).
+    if (!src_off || !dst_off || !results || !workspace)
+        return set_error(B64_ERR_INVALID_ARGUMENT, "%s: NULL pointer argument", fn);
+    if (tile_units == 0) tile_units = 4;
+    if (tile_units != 1 && tile_units != 2 && tile_units != 4 && tile_units != 8)
+        return set_error(B64_ERR_INVALID_ARGUMENT, "%s: tile_units must be 0, 1, 2, 4 or 8", fn);
+    if (workspace_bytes < batch_workspace_bytes(n))
+        return set_error(B64_ERR_INVALID_ARGUMENT, "%s: workspace holds %zu bytes, %zu needed", fn,
+                         workspace_bytes, batch_workspace_bytes(n));
+    if (reinterpret_cast<uintptr_t>(workspace) & 255)
+        return set_error(B64_ERR_INVALID_ARGUMENT, "%s: workspace not 256-byte aligned", fn);
+    BatchArgs a{src, src_off, n, dst, dst_off, alph_id, results};
+    const cudaError_t e =
+        launch_batch(decode, a, tabs, tile_units, workspace, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return set_error(B64_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
+    return B64_SUCCESS;
+}
+
+int b64_encode_batch(const uint8_t* src, const int64_t* src_off, int64_t n, uint8_t* dst,
+                     const int64_t* dst_off, const b64_alphabet* const* alphabets,
+                     int n_alphabets, const uint8_t* alph_id, int64_t* results, int tile_units,
+                     void* workspace, size_t workspace_bytes, void* stream) {
+    return batch_common(false, src, src_off, n, dst, dst_off, alphabets, n_alphabets, alph_id,
+                        results, tile_units, workspace, workspace_bytes, stream);
+}
+
+int b64_decode_batch(const uint8_t* src, const int64_t* src_off, int64_t n, uint8_t* dst,
+                     const int64_t* dst_off, const b64_alphabet* const* alphabets,
+                     int n_alphabets, const uint8_t* alph_id, int64_t* results, int tile_units,
+                     void* workspace, size_t workspace_bytes, void* stream) {
+    return batch_common(true, src, src_off, n, dst, dst_off, alphabets, n_alphabets, alph_id,
+                        results, tile_units, workspace, workspace_bytes, stream);
+}
+
+int b64_batch_offsets(const int64_t* src_off, int64_t n, const b64_alphabet* const* alphabets,
+                      int n_alphabets, const uint8_t* alph_id, int decode, int64_t* dst_off,
+                      void* stream) {
+    if (n < 0 || !src_off || !dst_off)
+        return set_error(B64_ERR_INVALID_ARGUMENT, "b64_batch_offsets: bad argument");
+    BatchTables tabs;
+    const int rc = batch_tables("b64_batch_offsets", alphabets, n_alphabets, &tabs);
+    if (rc != B64_SUCCESS) return rc;
+    const cudaError_t e = launch_batch_offsets(decode != 0, src_off, n, tabs, alph_id, dst_off,
+                                               static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return set_error(B64_ERR_CUDA, "b64_batch_offsets: %s", cudaGetErrorString(e));
+    return B64_SUCCESS;
+}
+
 const char* b64_last_error(void) { return t_last_error.c_str(); }
 
 int b64_device_fault_flag(int clear) {

@@ -35,4 +35,36 @@ uint32_t encode_fault_flag(bool clear);
 cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const DecodeTable& tab,
                           int padded, int64_t* d_result, cudaStream_t stream);
 
+// ---- batches (b64_batch.cu)
+constexpr int kMaxAlphabets = 4;
+
+// The alphabets of one batched call, passed by value in the kernel
+// parameters. Slots past the caller's count repeat alphabet 0, and alphabet
+// ids are taken modulo kMaxAlphabets, so no id reads outside the table.
+struct BatchTables {
+    EncodeTable enc[kMaxAlphabets];
+    DecodeTable dec[kMaxAlphabets];
+    int padded[kMaxAlphabets];
+};
+
+struct BatchArgs {
+    const uint8_t* src;
+    const int64_t* src_off;  // n+1 device offsets
+    int64_t n;
+    uint8_t* dst;
+    const int64_t* dst_off;  // n+1 device offsets (only the first n are read)
+    const uint8_t* alph_id;  // n device ids, or NULL (all alphabet 0)
+    int64_t* results;        // n device results
+};
+
+size_t batch_workspace_bytes(int64_t n);
+// Enqueues prep + tile kernel (+ decode finalize). `units` in {1, 2, 4, 8}.
+cudaError_t launch_batch(bool decode, const BatchArgs& a, const BatchTables& tabs, int units,
+                         void* workspace, cudaStream_t stream);
+// dst_off[0..n] = exclusive scan of per-string output capacities (encoded
+// length, or 3*ceil(m/4) for decode).
+cudaError_t launch_batch_offsets(bool decode, const int64_t* src_off, int64_t n,
+                                 const BatchTables& tabs, const uint8_t* alph_id,
+                                 int64_t* dst_off, cudaStream_t stream);
+
 }  // namespace b64

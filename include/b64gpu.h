@@ -158,6 +158,23 @@ int b64_decode_batch(const uint8_t* src, const int64_t* src_off, int64_t n, uint
                      int n_alphabets, const uint8_t* alph_id, int64_t* results, int tile_units,
                      void* workspace, size_t workspace_bytes, void* stream);
 
+/* Batched strict decode for callers that cannot allocate device memory where
+ * they decode (a plugin handed only its buffers, a process whose memory budget
+ * another component owns, a path that must never enter an allocator). The
+ * paper has no counterpart; this is b64_decode_batch with its workspace in a
+ * device array the library reserves at load time (about 1 MiB on every GPU
+ * that loads it, kept until exit) instead of caller memory. Same arguments
+ * and results as b64_decode_batch, without workspace. At most 65536 strings
+ * per call (more returns B64_ERR_INVALID_ARGUMENT). Calls no allocator. All
+ * calls share the one array: calls whose work overlaps on the GPU race, so
+ * serialise them (e.g. one stream). The first call on each device looks up
+ * the array's device address; make it before any stream capture. */
+int b64_decode_batch_noalloc(const uint8_t* src, const int64_t* src_off, int64_t n,
+                             uint8_t* dst, const int64_t* dst_off,
+                             const b64_alphabet* const* alphabets, int n_alphabets,
+                             const uint8_t* alph_id, int64_t* results, int tile_units,
+                             void* stream);
+
 /* dst_off[0..n] (n+1 device int64) = exclusive scan of each string's output
  * capacity: its encoded length (decode == 0) or 3*ceil(len/4) (decode != 0).
  * dst_off[n] is the total. One kernel on `stream`. */

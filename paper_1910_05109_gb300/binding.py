@@ -41,6 +41,7 @@ SIGNATURES = {
     "b64_encode_batch": (_I, [_P, _P, _I64, _P, _P, _P, _I, _P, _P, _I, _P, _SZ, _P]),
     "b64_decode_batch": (_I, [_P, _P, _I64, _P, _P, _P, _I, _P, _P, _I, _P, _SZ, _P]),
     "b64_batch_offsets": (_I, [_P, _I64, _P, _I, _P, _I, _P, _P]),
+    "b64_decode_batch_noalloc": (_I, [_P, _P, _I64, _P, _P, _P, _I, _P, _P, _I, _P]),
     "b64_last_error": (ctypes.c_char_p, []),
     "b64_device_fault_flag": (_I, [_I]),
     "b64_version": (_I, []),

@@ -10,13 +10,6 @@
 #include "b64gpu.h"
 #include "b64_internal.h"
 
-struct b64_alphabet {
-    uint8_t chars[64];
-    int padded;
-    b64::EncodeTable enc;
-    b64::DecodeTable dec;
-};
-
 namespace b64 {
 namespace {
 
@@ -128,6 +121,25 @@ void clear_error() { t_last_error.clear(); }
 
 using namespace b64;
 
+namespace b64 {
+
+int batch_tables(const char* fn, const b64_alphabet* const* alphabets, int n_alphabets,
+                 BatchTables* t) {
+    if (!alphabets || n_alphabets < 1 || n_alphabets > B64_BATCH_MAX_ALPHABETS)
+        return set_error(B64_ERR_INVALID_ARGUMENT, "%s: need 1..%d alphabets", fn,
+                         B64_BATCH_MAX_ALPHABETS);
+    for (int k = 0; k < kMaxAlphabets; ++k) {
+        const b64_alphabet* a = alphabets[k < n_alphabets ? k : 0];
+        if (!a) return set_error(B64_ERR_INVALID_ARGUMENT, "%s: alphabet %d is NULL", fn, k);
+        t->enc[k] = a->enc;
+        t->dec[k] = a->dec;
+        t->padded[k] = a->padded;
+    }
+    return B64_SUCCESS;
+}
+
+}  // namespace b64
+
 extern "C" {
 
 b64_alphabet* b64_alphabet_create(const uint8_t chars[64], int padded) {
@@ -232,20 +244,6 @@ int64_t b64_decode(const uint8_t* src, size_t len, uint8_t* dst, const b64_alpha
 
 size_t b64_batch_workspace_size(int64_t n) { return n > 0 ? batch_workspace_bytes(n) : 0; }
 
-static int batch_tables(const char* fn, const b64_alphabet* const* alphabets, int n_alphabets,
-                        BatchTables* t) {
-    if (!alphabets || n_alphabets < 1 || n_alphabets > B64_BATCH_MAX_ALPHABETS)
-        return set_error(B64_ERR_INVALID_ARGUMENT, "%s: need 1..%d alphabets", fn,
-                         B64_BATCH_MAX_ALPHABETS);
-    for (int k = 0; k < kMaxAlphabets; ++k) {
-        const b64_alphabet* a = alphabets[k < n_alphabets ? k : 0];
-        if (!a) return set_error(B64_ERR_INVALID_ARGUMENT, "%s: alphabet %d is NULL", fn, k);
-        t->enc[k] = a->enc;
-        t->dec[k] = a->dec;
-        t->padded[k] = a->padded;
-    }
-    return B64_SUCCESS;
-}
 
 static int batch_common(bool decode, const uint8_t* src, const int64_t* src_off, int64_t n,
                         uint8_t* dst, const int64_t* dst_off, const b64_alphabet* const* alphabets,

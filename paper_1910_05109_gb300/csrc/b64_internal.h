@@ -6,6 +6,15 @@
 #include <cuda_runtime.h>
 
 #include "b64_device.cuh"
+#include "b64gpu.h"
+
+// The alphabet handle behind the C ABI's opaque pointer.
+struct b64_alphabet {
+    uint8_t chars[64];
+    int padded;
+    b64::EncodeTable enc;
+    b64::DecodeTable dec;
+};
 
 namespace b64 {
 
@@ -58,6 +67,10 @@ struct BatchArgs {
 };
 
 size_t batch_workspace_bytes(int64_t n);
+// Fills the by-value tables of a batched call from 1..kMaxAlphabets handles
+// (later slots repeat alphabet 0). Returns B64_SUCCESS or sets the error.
+int batch_tables(const char* fn, const b64_alphabet* const* alphabets, int n_alphabets,
+                 BatchTables* t);
 // Enqueues prep + tile kernel (+ decode finalize). `units` in {1, 2, 4, 8}.
 cudaError_t launch_batch(bool decode, const BatchArgs& a, const BatchTables& tabs, int units,
                          void* workspace, cudaStream_t stream);

@@ -221,3 +221,27 @@ def test_batch_graph_and_per_string_identity(b64, orc, tables):
             b64.encode(d_src[off[i]:off[i + 1]], alph[aid[i]], per[hoff[i]:hoff[i + 1]])
     torch.cuda.synchronize()
     assert torch.equal(per, first)
+
+
+def test_batch_codec_graph_and_autotune_cache(b64, orc, tables, tmp_path):
+    from paper_1910_05109_gb300 import autotune
+    from paper_1910_05109_gb300.batch import BatchCodec
+    data, off, aid, padded = make_batch(orc, 800, seed=70, hi=1 << 14)
+    want, eoff, _ = oracle_encode(orc, tables, data, off, aid, padded)
+    n = off.size - 1
+    codec = BatchCodec("encode", n, data.size, tables[0])
+    total = codec.load(torch.from_numpy(data).cuda(), torch.from_numpy(off).cuda(),
+                       torch.from_numpy(aid).cuda())
+    assert total == want.size
+    path = str(tmp_path / "autotune.json")
+    args = (codec.src, codec.src_off, codec.dst, codec.dst_off, tables[0], codec.alph_id[:n])
+    units, timings = autotune.best_units("encode", *args, path=path)
+    assert units in autotune.UNITS and set(timings) == set(autotune.UNITS)
+    again, t2 = autotune.best_units("encode", *args, path=path)
+    assert again == units and t2 == {}          # served from the cache file
+    codec.tile_units = units
+    for _ in range(3):                          # first call direct, then graph replays
+        codec.dst.zero_()
+        codec.run()
+        codec.synchronize()
+        assert np.array_equal(codec.dst[:total].cpu().numpy(), want)

@@ -60,6 +60,9 @@ extern "C" {
  * decode error offset. */
 #define B64_E_INVAL (INT64_MIN + 1)
 #define B64_E_CUDA (INT64_MIN + 2)
+/* A device-side wait inside the call ran out of time (see
+ * b64_device_fault_flag); the output is incomplete. */
+#define B64_E_TIMEOUT (INT64_MIN + 3)
 
 /* ---------------------------------------------------------------- alphabets
  * A 64-character table (Table 1 and its base64url variant, Sec. 2; any other
@@ -121,6 +124,24 @@ int b64_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b64_alp
  * first call and kept until the process exits. */
 int64_t b64_decode(const uint8_t* src, size_t len, uint8_t* dst, const b64_alphabet* a,
                    void* stream);
+
+/* ---------------------------------------------------------------- MIME
+ * Strict decode that first skips CR, LF and space anywhere in the input
+ * (line-wrapped base64 as in MIME; the paper names MIME only as motivation,
+ * Sec. 1). The remaining characters are decoded exactly as b64_decode_async
+ * decodes them (Sec. 2, Sec. 3.2, and the rules at the top of this file);
+ * error offsets are offsets into the original input, and a bad length is
+ * reported at offset len. One pass over the input (tiles publish running
+ * counts of data characters to their successors), then a one-thread kernel
+ * writes *d_result: the decoded length, -(offset+1), or B64_E_TIMEOUT.
+ * workspace: device memory of b64_mime_workspace_size(len) bytes, 8-byte
+ * aligned, caller-owned, busy until the work completes (one call at a time per
+ * workspace). dst needs b64_decoded_max_length(len) bytes. */
+size_t b64_mime_workspace_size(size_t len);
+
+int b64_mime_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b64_alphabet* a,
+                          int64_t* d_result, void* workspace, size_t workspace_bytes,
+                          void* stream);
 
 /* ---------------------------------------------------------------- batches
  * Many independent strings in one launch sequence (prep kernel, one
@@ -192,6 +213,16 @@ const char* b64_last_error(void);
  * incomplete). Returns the flag of the current device (0 = never set) and
  * clears it if clear != 0. Synchronises the device. Negative on CUDA error. */
 int b64_device_fault_flag(int clear);
+
+/* Self-test of the bounded device waits: runs b64_mime_decode_async on the
+ * given input (at least 8193 bytes) with its first tile never claimed, so the
+ * other tiles' waits for it run out after wait_limit_ns nanoseconds.
+ * *d_result then becomes B64_E_TIMEOUT and b64_device_fault_flag reports the
+ * timeout; no wait lasts longer than the limit and the context stays usable.
+ * Returns B64_SUCCESS if the work was enqueued. */
+int b64_selftest_wait_timeout(const uint8_t* src, size_t len, uint8_t* dst,
+                              const b64_alphabet* a, int64_t* d_result, void* workspace,
+                              size_t workspace_bytes, uint64_t wait_limit_ns, void* stream);
 
 /* Library version: major*10000 + minor*100 + patch. */
 int b64_version(void);

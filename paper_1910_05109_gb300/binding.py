@@ -20,6 +20,7 @@ B64_ERR_INVALID_ARGUMENT = -1
 B64_ERR_CUDA = -2
 B64_E_INVAL = -(2**63) + 1
 B64_E_CUDA = -(2**63) + 2
+B64_E_TIMEOUT = -(2**63) + 3
 
 _lock = threading.Lock()
 _lib = None
@@ -42,6 +43,9 @@ SIGNATURES = {
     "b64_decode_batch": (_I, [_P, _P, _I64, _P, _P, _P, _I, _P, _P, _I, _P, _SZ, _P]),
     "b64_batch_offsets": (_I, [_P, _I64, _P, _I, _P, _I, _P, _P]),
     "b64_decode_batch_noalloc": (_I, [_P, _P, _I64, _P, _P, _P, _I, _P, _P, _I, _P]),
+    "b64_mime_workspace_size": (_SZ, [_SZ]),
+    "b64_mime_decode_async": (_I, [_P, _SZ, _P, _P, _P, _P, _SZ, _P]),
+    "b64_selftest_wait_timeout": (_I, [_P, _SZ, _P, _P, _P, _P, _SZ, ctypes.c_uint64, _P]),
     "b64_last_error": (ctypes.c_char_p, []),
     "b64_device_fault_flag": (_I, [_I]),
     "b64_version": (_I, []),
@@ -274,3 +278,42 @@ def decode_batch(src, src_off, dst, dst_off, alphabets, alph_id=None, results=No
     _batch(lib().b64_decode_batch, src, src_off, dst, dst_off, alphabets, alph_id, results,
            tile_units, workspace, stream)
     return results[:n]
+
+
+# ---------------------------------------------------------------- MIME
+
+def mime_workspace(m: int, device=None) -> torch.Tensor:
+    return torch.empty(max(lib().b64_mime_workspace_size(m), 8), dtype=torch.uint8,
+                       device=device or "cuda")
+
+
+def mime_decode_async(src: torch.Tensor, dst: torch.Tensor, d_result: torch.Tensor,
+                      alphabet: Alphabet | None = None, workspace=None, stream=None):
+    """Enqueues a whitespace-skipping strict decode; returns the workspace used."""
+    alphabet = alphabet or Alphabet.standard()
+    src, dst = _dev_u8(src, "src"), _dev_u8(dst, "dst")
+    m = src.numel()
+    if dst.numel() < decoded_max_length(m):
+        raise B64Error("dst is smaller than decoded_max_length(len(src))")
+    if workspace is None:
+        workspace = mime_workspace(m, src.device)
+    rc = lib().b64_mime_decode_async(src.data_ptr(), m, dst.data_ptr(), alphabet.handle,
+                                     d_result.data_ptr(), workspace.data_ptr(),
+                                     workspace.numel(), _stream_ptr(stream))
+    if rc != B64_SUCCESS:
+        raise B64Error(last_error())
+    return workspace
+
+
+def mime_decode(src: torch.Tensor, alphabet: Alphabet | None = None, dst=None, workspace=None,
+                stream=None) -> tuple[int, torch.Tensor]:
+    """Whitespace-skipping strict decode (synchronises). Returns (result, view)."""
+    m = src.numel()
+    if dst is None:
+        dst = torch.empty(max(decoded_max_length(m), 1), dtype=torch.uint8, device=src.device)
+    res = torch.empty(1, dtype=torch.int64, device=src.device)
+    mime_decode_async(src, dst, res, alphabet, workspace, stream)
+    r = int(res.item())
+    if r == B64_E_TIMEOUT:
+        raise B64Error("a device wait ran out of time (see device_fault_flag)")
+    return r, dst[: max(r, 0)]

@@ -304,12 +304,52 @@ int b64_batch_offsets(const int64_t* src_off, int64_t n, const b64_alphabet* con
     return B64_SUCCESS;
 }
 
+size_t b64_mime_workspace_size(size_t len) { return mime_workspace_bytes(len); }
+
+static int mime_common(const char* fn, const uint8_t* src, size_t len, uint8_t* dst,
+                       const b64_alphabet* a, int64_t* d_result, void* workspace,
+                       size_t workspace_bytes, uint64_t skip, uint64_t limit_ns, void* stream) {
+    if (!a || !d_result || !workspace)
+        return set_error(B64_ERR_INVALID_ARGUMENT, "%s: NULL alphabet, d_result or workspace", fn);
+    if ((reinterpret_cast<uintptr_t>(d_result) | reinterpret_cast<uintptr_t>(workspace)) & 7u)
+        return set_error(B64_ERR_INVALID_ARGUMENT, "%s: d_result/workspace not 8-byte aligned", fn);
+    if (len > 0 && (!src || !dst))
+        return set_error(B64_ERR_INVALID_ARGUMENT, "%s: NULL src or dst", fn);
+    if (len > (size_t(1) << 62)) return set_error(B64_ERR_INVALID_ARGUMENT, "%s: len too large", fn);
+    if (workspace_bytes < mime_workspace_bytes(len))
+        return set_error(B64_ERR_INVALID_ARGUMENT, "%s: workspace holds %zu bytes, %zu needed", fn,
+                         workspace_bytes, mime_workspace_bytes(len));
+    if (overlaps(src, len, dst, b64_decoded_max_length(len)))
+        return set_error(B64_ERR_INVALID_ARGUMENT, "%s: src and dst overlap", fn);
+    const cudaError_t e = launch_mime_decode(src, len, dst, a->dec, a->padded, d_result, workspace,
+                                             skip, limit_ns, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return set_error(B64_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
+    return B64_SUCCESS;
+}
+
+int b64_mime_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b64_alphabet* a,
+                          int64_t* d_result, void* workspace, size_t workspace_bytes,
+                          void* stream) {
+    return mime_common("b64_mime_decode_async", src, len, dst, a, d_result, workspace,
+                       workspace_bytes, 0, kWaitLimitNs, stream);
+}
+
+int b64_selftest_wait_timeout(const uint8_t* src, size_t len, uint8_t* dst,
+                              const b64_alphabet* a, int64_t* d_result, void* workspace,
+                              size_t workspace_bytes, uint64_t wait_limit_ns, void* stream) {
+    if (len <= 8192)
+        return set_error(B64_ERR_INVALID_ARGUMENT,
+                         "b64_selftest_wait_timeout: needs more than one tile (8192 bytes)");
+    return mime_common("b64_selftest_wait_timeout", src, len, dst, a, d_result, workspace,
+                       workspace_bytes, 1, wait_limit_ns, stream);
+}
+
 const char* b64_last_error(void) { return t_last_error.c_str(); }
 
 int b64_device_fault_flag(int clear) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return set_error(B64_ERR_CUDA, "b64_device_fault_flag: %s", cudaGetErrorString(e));
-    uint32_t f = encode_fault_flag(clear != 0);
+    uint32_t f = encode_fault_flag(clear != 0) | mime_fault_flag(clear != 0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(B64_ERR_CUDA, "b64_device_fault_flag: %s", cudaGetErrorString(e));
     return int(f);

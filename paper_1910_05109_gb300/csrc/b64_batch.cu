@@ -113,16 +113,6 @@ __device__ __forceinline__ void warp_stage_in(uint8_t* sbuf, const uint8_t* base
     }
 }
 
-// Four aligned words starting `off` bytes into sbuf (off a multiple of 4 plus
-// `sh`, sh in 0..3), re-aligned with funnel shifts from five word loads.
-__device__ __forceinline__ uint4 load16_shifted(const uint8_t* sbuf, uint32_t off, uint32_t sh) {
-    const uint32_t* w = reinterpret_cast<const uint32_t*>(sbuf + (off & ~3u));
-    const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = sh ? w[4] : 0u;
-    const uint32_t s = 8 * sh;
-    return make_uint4(__funnelshift_r(w0, w1, s), __funnelshift_r(w1, w2, s),
-                      __funnelshift_r(w2, w3, s), __funnelshift_r(w3, w4, s));
-}
-
 // Writes sbuf[0 .. len) to global q (any alignment): aligned 16-byte stores
 // for the middle, byte stores for the ragged head and tail. Warp-collective.
 __device__ __forceinline__ void warp_stage_out(uint8_t* q, const uint8_t* sbuf, uint32_t len,

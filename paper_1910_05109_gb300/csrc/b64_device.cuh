@@ -95,6 +95,17 @@ __device__ __forceinline__ uint3 pack4x24(uint32_t q0, uint32_t q1, uint32_t q2,
     return o;
 }
 
+// 16 bytes starting `off` bytes into a 4-byte aligned shared buffer (off a
+// multiple of 4 plus `sh`, sh in 0..3), re-aligned with funnel shifts from
+// five word loads. Reads up to 4 bytes past off + 16 when sh != 0.
+__device__ __forceinline__ uint4 load16_shifted(const uint8_t* sbuf, uint32_t off, uint32_t sh) {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(sbuf + (off & ~3u));
+    const uint32_t w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3], w4 = sh ? w[4] : 0u;
+    const uint32_t s = 8 * sh;
+    return make_uint4(__funnelshift_r(w0, w1, s), __funnelshift_r(w1, w2, s),
+                      __funnelshift_r(w2, w3, s), __funnelshift_r(w3, w4, s));
+}
+
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

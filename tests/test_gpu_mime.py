@@ -1,0 +1,162 @@
+"""Parity of the MIME (whitespace-skipping) strict decode with the oracle.
+
+Inputs are base64 text from the oracle, line-wrapped with CRLF every 76
+characters or with CR/LF/space inserted at random places (long runs that
+cover whole tiles included), '=' padding split across tiles, injected bad
+bytes, both padding modes, any alignment; the full-size case is 256 MiB of
+seed-3 random bytes (357,913,944 characters, 367,332,730 bytes with CRLF),
+plus 256 documents of 1 MiB each with a stray bad byte at p = 0.01.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1910_05109_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TILE = 8192
+
+
+@pytest.fixture(scope="module")
+def b64():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1910_05109_gb300 import binding
+    binding.lib()
+    yield binding
+    assert binding.device_fault_flag() == 0
+
+
+def run(b64, text, alph, src_off=0, dst_off=0):
+    buf = torch.empty(text.size + src_off + 16, dtype=torch.uint8, device="cuda")
+    src = buf[src_off:src_off + text.size]
+    if text.size:
+        src.copy_(torch.from_numpy(np.ascontiguousarray(text)))
+    cap = b64.decoded_max_length(text.size)
+    out = torch.full((cap + dst_off + 32,), 0xA5, dtype=torch.uint8, device="cuda")
+    r, _ = b64.mime_decode(src, alph, out[dst_off:dst_off + max(cap, 1)])
+    host = out.cpu().numpy()
+    assert (host[:dst_off] == 0xA5).all()
+    written = r if r >= 0 else cap
+    assert (host[dst_off + written:] == 0xA5).all()
+    return r, host[dst_off:dst_off + max(r, 0)]
+
+
+def check(b64, orc, text, alph, chars, padded, **kw):
+    want_r, want = orc.decode(text, chars, padded, mime=True)
+    r, got = run(b64, text, alph, **kw)
+    assert r == want_r, (r, want_r)
+    if r >= 0:
+        assert np.array_equal(got, want)
+    return r
+
+
+def test_wrapped_sizes(b64, orc):
+    std = b64.Alphabet.standard()
+    for i, n in enumerate([0, 1, 2, 3, 56, 57, 58, 1000, 6144, 6145, 6146, 12287, 50_000,
+                           200_001]):
+        text = wl.mime_wrap(orc.encode(wl.random_bytes(n, 300 + i)))
+        assert check(b64, orc, text, std, orc.standard_alphabet(), True) == n
+
+
+def test_random_whitespace_and_long_runs(b64, orc):
+    url = b64.Alphabet.url()
+    for i in range(12):
+        data = wl.random_bytes(int(wl.rng(i).integers(0, 60_000)), 400 + i)
+        text = orc.encode(data, orc.url_alphabet(), False)
+        text = wl.insert_spaces(text, seed=500 + i, count=int(text.size * 0.3) + 1)
+        if i % 3 == 0:  # a run of spaces longer than a tile somewhere in the middle
+            p = text.size // 2
+            text = np.concatenate([text[:p], np.full(TILE * 2 + 5, 32, np.uint8), text[p:]])
+        assert check(b64, orc, text, url, orc.url_alphabet(), False) == data.size
+
+
+def test_padding_across_tile_edges(b64, orc):
+    std = b64.Alphabet.standard()
+    for n in (1, 2, 4, 5):
+        body = orc.encode(wl.random_bytes(6141 + n, 600 + n))   # ends with '=' or '=='
+        for gap in range(0, 6):
+            # place the padding right at a tile boundary, with whitespace around it
+            k = int((body[-2:] == ord("=")).sum())
+            head, pad = body[:body.size - k], body[body.size - k:]
+            filler = np.full(max(0, TILE - head.size - gap), 10, np.uint8)
+            text = np.concatenate([head, filler, np.full(gap, 13, np.uint8), pad,
+                                   np.full(gap, 32, np.uint8)])
+            check(b64, orc, text, std, orc.standard_alphabet(), True)
+
+
+def test_errors_and_alignment(b64, orc):
+    std = b64.Alphabet.standard()
+    base = wl.mime_wrap(orc.encode(wl.random_bytes(40_000, 700)))
+    g = wl.rng(701)
+    for t in range(60):
+        text = base.copy()
+        p = int(g.integers(0, text.size))
+        text[p] = int(g.choice([0x00, 0x09, 0x2D, 0x3D, 0x7F, 0xC3, 0xFF, ord("+")]))
+        check(b64, orc, text, std, orc.standard_alphabet(), True, src_off=t % 7, dst_off=t % 5)
+    for bad in (b"QQ\r\n=A", b"QQ=\r\n=", b"Q===", b"QQ==\r\nQQ==", b"QQ \t", b"\r\n\r\n",
+                b"QUJD\r\n", b" QUI=\r\n", b"QQ\r\n"):
+        check(b64, orc, np.frombuffer(bad, np.uint8), std, orc.standard_alphabet(), True)
+
+
+def test_config4_full_size(b64, orc):
+    """256 MiB of seed-3 random bytes, encoded and wrapped at 76 characters
+    with CRLF (no trailing CRLF): 367,332,730 bytes of input."""
+    data = wl.random_bytes(256 << 20, 3)
+    text = wl.mime_wrap(orc.encode(data))
+    assert text.size == 367_332_730
+    src = torch.from_numpy(text).cuda()
+    r, dec = b64.mime_decode(src, b64.Alphabet.standard())
+    want_r, want = orc.decode(text, mime=True)
+    assert r == want_r == data.size
+    assert torch.equal(dec, torch.from_numpy(want).cuda())
+
+
+def test_config4_documents_with_stray_bytes(b64, orc):
+    """256 documents of 1 MiB source each; each gets a stray bad byte with
+    p = 0.01 (seed 13, at least one forced); offsets against the oracle."""
+    g = wl.rng(13)
+    hit = g.random(256) < 0.01
+    if not hit.any():
+        hit[int(g.integers(0, 256))] = True
+    std = b64.Alphabet.standard()
+    ws = b64.mime_workspace(1_500_000)
+    for d in range(256):
+        text = wl.mime_wrap(orc.encode(wl.random_bytes(1 << 20, 10_000 + d)))
+        if hit[d]:
+            text[int(g.integers(0, text.size))] = 0xFF
+        want_r, _ = orc.decode(text, mime=True)
+        res = torch.empty(1, dtype=torch.int64, device="cuda")
+        dst = torch.empty(b64.decoded_max_length(text.size), dtype=torch.uint8, device="cuda")
+        b64.mime_decode_async(torch.from_numpy(text).cuda(), dst, res, std, ws)
+        assert int(res.item()) == want_r, d
+        if not hit[d]:
+            assert want_r == 1 << 20
+
+
+def test_bounded_wait_timeout_selftest(b64, orc):
+    """A look-back wait that nothing will satisfy: the call reports
+    B64_E_TIMEOUT within the limit, the fault flag is raised, and the context
+    keeps working."""
+    import ctypes
+    import time
+    text = wl.mime_wrap(orc.encode(wl.random_bytes(60_000, 800)))
+    src = torch.from_numpy(text).cuda()
+    dst = torch.empty(b64.decoded_max_length(text.size), dtype=torch.uint8, device="cuda")
+    res = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ws = b64.mime_workspace(text.size)
+    t0 = time.time()
+    rc = b64.lib().b64_selftest_wait_timeout(src.data_ptr(), text.size, dst.data_ptr(),
+                                             b64.Alphabet.standard().handle, res.data_ptr(),
+                                             ws.data_ptr(), ws.numel(), ctypes.c_uint64(50_000_000),
+                                             torch.cuda.current_stream().cuda_stream)
+    assert rc == b64.B64_SUCCESS, b64.last_error()
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 30
+    assert int(res.item()) == b64.B64_E_TIMEOUT
+    assert b64.device_fault_flag(clear=True) != 0
+    assert b64.device_fault_flag() == 0
+    r, got = b64.mime_decode(src, b64.Alphabet.standard())
+    assert r == 60_000

@@ -537,6 +537,53 @@ def run_batch(args):
           "encode": out["encode"], "decode": out["decode"], "gpu_launches": 5 * args.steps})
 
 
+# ---------------------------------------------------------------- serving workload
+
+def run_serve(args):
+    """Poisson arrivals (mean 20,000 req/s, seed 4) over `--duration` seconds,
+    60% decode / 40% encode, sizes clip(lognormal(10.62, 2.0), 100 B, 16 MiB)
+    (seed 5), served under a 4 GiB device budget with continuous batching;
+    latency = arrival -> result back on the host."""
+    import torch
+    from paper_1910_05109_gb300 import binding as b64
+    from paper_1910_05109_gb300 import build as gpu_build
+    from paper_1910_05109_gb300 import serve
+    from paper_1910_05109_gb300 import workloads as wl
+
+    gpu_build.build()
+    torch.cuda.set_device(0)
+    raw = wl.random_bytes(1 << 30, 5)
+    d_raw = torch.from_numpy(raw).cuda()
+    text = b64.encode(d_raw, b64.Alphabet.standard()).cpu().numpy()   # decode payloads
+    del d_raw
+    arrivals, ops, sizes, pick = serve.poisson_requests(args.rate, args.duration, 4, 5)
+    srv = serve.Server(4 << 30, [b64.Alphabet.standard()], n_streams=args.streams)
+    with ClockSampler(f"GPU-{torch.cuda.get_device_properties(0).uuid}".replace("GPU-GPU-", "GPU-")) as clocks:
+        lat, results, wall, _ = serve.run_open_loop(srv, arrivals, ops, sizes, pick,
+                                                    [(raw, 1), (text, 4)], 8 << 30)
+    n = arrivals.size
+    want = np.where(ops == 0, (sizes + 2) // 3 * 4, sizes // 4 * 3)   # no padding in payloads
+    ok = int((results == want).sum())
+    in_bytes = int(sizes.sum())
+    emit({"metric": METRIC, "workload": "serving loop", "value": float(np.percentile(lat, 99) * 1e3),
+          "unit": "ms (p99 latency)", "n_gpus": 1, "steps": n, "warmup": 0,
+          "ms_per_step": wall / n * 1e3, "higher_is_better": False, "scaling": "weak",
+          "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+          "config": {"workload": f"Poisson {args.rate:.0f} req/s for {args.duration:.0f} s, 60% "
+                                 "decode / 40% encode, sizes clip(lognormal(10.62, 2.0), 100 B, "
+                                 "16 MiB), 4 GiB device budget, continuous batching",
+                     "requests": n, "streams": args.streams},
+          "p50_ms": float(np.percentile(lat, 50) * 1e3),
+          "p99_ms": float(np.percentile(lat, 99) * 1e3),
+          "max_ms": float(lat.max() * 1e3),
+          "aggregate_gbps": in_bytes / wall / 1e9,
+          "offered_gbps": in_bytes / args.duration / 1e9,
+          "achieved_req_per_s": n / wall, "batches": srv.batches(),
+          "results_correct": ok, "clocks": clocks.summary(),
+          "gpu_launches": 4 * srv.batches()})
+    srv.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -547,15 +594,21 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--bytes", type=int, default=N_BYTES,
                     help="input size (default 1 GiB; smaller sizes are for profiling)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
                     help="single: the 1 GiB single-buffer step (default); batch: 100,000 "
-                         "strings in one launch sequence vs one launch per string")
+                         "strings in one launch sequence vs one launch per string; serve: "
+                         "Poisson request stream through the continuous-batching engine")
     ap.add_argument("--strings", type=int, default=100_000)
+    ap.add_argument("--rate", type=float, default=20_000.0)
+    ap.add_argument("--duration", type=float, default=30.0)
+    ap.add_argument("--streams", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

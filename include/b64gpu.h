@@ -203,6 +203,49 @@ int b64_batch_offsets(const int64_t* src_off, int64_t n, const b64_alphabet* con
                       int n_alphabets, const uint8_t* alph_id, int decode, int64_t* dst_off,
                       void* stream);
 
+/* ---------------------------------------------------------------- serving
+ * A request engine with continuous batching (not in the paper; it drives the
+ * codec above). The server owns a device arena of budget_bytes and a pinned
+ * host staging area of the same size, allocated once here. b64_server_submit
+ * queues a request (host input and output buffers, owned by the caller and
+ * untouched until the request completes). b64_server_poll makes progress
+ * without blocking: it hands back finished requests and, whenever one of the
+ * n_streams streams is idle and arena space is free, launches the queued
+ * requests in arrival order (up to max_batch_bytes of input+output, 0 = 64
+ * MiB) as one batched encode and/or one batched decode: a host-to-device
+ * copy, the batched kernels, device-to-host copies. Batches on different
+ * streams overlap, and requests that arrive while others run join the next
+ * batch. A server is used by one thread at a time. */
+typedef struct b64_server b64_server;
+
+typedef struct {
+    uint64_t tag;      /* the caller's tag from b64_server_submit */
+    int64_t result;    /* as b64_encode / b64_decode return for this request */
+    double latency_us; /* from submit to the poll that handed it back */
+} b64_completion;
+
+/* Returns NULL on failure (b64_last_error). alphabets: 1..B64_BATCH_MAX_ALPHABETS. */
+b64_server* b64_server_create(size_t budget_bytes, int n_streams, size_t max_batch_bytes,
+                              const b64_alphabet* const* alphabets, int n_alphabets);
+
+/* op: 0 = encode, 1 = strict decode; alph_id indexes the server's alphabets.
+ * out_cap: at least b64_encoded_length (encode) or b64_decoded_max_length
+ * (decode) of len. A request that could never fit the budget is refused. */
+int b64_server_submit(b64_server* s, uint64_t tag, int op, int alph_id, const uint8_t* in,
+                      size_t len, uint8_t* out, size_t out_cap);
+
+/* Writes up to max_out completions; returns how many (or an error code < 0). */
+int b64_server_poll(b64_server* s, b64_completion* out, int max_out);
+
+/* Requests submitted and not yet handed back. */
+int b64_server_outstanding(const b64_server* s);
+
+/* Batches launched so far. */
+uint64_t b64_server_batches(const b64_server* s);
+
+/* Waits for in-flight work, then frees the server. */
+void b64_server_destroy(b64_server* s);
+
 /* ---------------------------------------------------------------- diagnostics */
 
 /* Thread-local message for the last failed call of this thread ("" if none). */

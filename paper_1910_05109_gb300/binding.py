@@ -46,6 +46,12 @@ SIGNATURES = {
     "b64_mime_workspace_size": (_SZ, [_SZ]),
     "b64_mime_decode_async": (_I, [_P, _SZ, _P, _P, _P, _P, _SZ, _P]),
     "b64_selftest_wait_timeout": (_I, [_P, _SZ, _P, _P, _P, _P, _SZ, ctypes.c_uint64, _P]),
+    "b64_server_create": (_P, [_SZ, _I, _SZ, _P, _I]),
+    "b64_server_submit": (_I, [_P, ctypes.c_uint64, _I, _I, _P, _SZ, _P, _SZ]),
+    "b64_server_poll": (_I, [_P, _P, _I]),
+    "b64_server_outstanding": (_I, [_P]),
+    "b64_server_batches": (ctypes.c_uint64, [_P]),
+    "b64_server_destroy": (None, [_P]),
     "b64_last_error": (ctypes.c_char_p, []),
     "b64_device_fault_flag": (_I, [_I]),
     "b64_version": (_I, []),

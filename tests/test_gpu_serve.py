@@ -1,0 +1,96 @@
+"""Serving engine: continuous batching under a device-memory budget.
+
+Requests arrive as a Poisson stream (mixed encode / decode, lognormal sizes)
+and are replayed in real time; every result must be identical to the same
+request served alone, and the sampled ones must equal the oracle's. A small
+budget forces requests to wait for memory; a request larger than the budget
+is refused.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1910_05109_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env(orc):
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1910_05109_gb300 import binding, serve
+    raw = wl.random_bytes(8 << 20, 5)
+    text = orc.encode(raw)                      # decode payloads: valid base64
+    return binding, serve, [(raw, 1), (text, 4)]
+
+
+def serve_alone(serve, b64, req, pools):
+    op, data = req
+    srv = serve.Server(64 << 20, [b64.Alphabet.standard()], n_streams=1)
+    cap = (data.size + 2) // 3 * 4 if op == 0 else (data.size + 3) // 4 * 3
+    out = np.zeros(max(cap, 1), np.uint8)
+    srv.submit(7, op, 0, data.ctypes.data, data.size, out.ctypes.data, cap)
+    while True:
+        c = srv.poll()
+        if c.size:
+            r = int(c["result"][0])
+            srv.close()
+            return r, out[:max(r, 0)].copy()
+
+
+def payloads(ops, sizes, pick, pools):
+    out = []
+    for i in range(ops.size):
+        arr, unit = pools[ops[i]]
+        room = (arr.size - sizes[i]) // unit
+        off = int(pick[i] * room) * unit
+        out.append((int(ops[i]), arr[off:off + sizes[i]]))
+    return out
+
+
+def test_mix_equals_alone_and_oracle(env, orc):
+    b64, serve, pools = env
+    arrivals, ops, sizes, pick = serve.poisson_requests(20_000, 0.25, 4, 5, hi=1 << 18)
+    srv = serve.Server(256 << 20, [b64.Alphabet.standard()], n_streams=4)
+    lat, results, wall, outputs = serve.run_open_loop(srv, arrivals, ops, sizes, pick, pools,
+                                                      1 << 30, keep_outputs=True)
+    n = arrivals.size
+    assert n > 3000 and not np.isnan(lat).any()
+    assert srv.batches() < n                    # requests were batched together
+    reqs = payloads(ops, sizes, pick, pools)
+    for i in range(n):
+        op, data = reqs[i]
+        want_len = (data.size + 2) // 3 * 4 if op == 0 else data.size // 4 * 3 - \
+            int((data[-2:] == ord("=")).sum())
+        assert results[i] == want_len, i
+    g = wl.rng(9)
+    for i in g.choice(n, 150, replace=False):
+        r, out = serve_alone(serve, b64, reqs[i], pools)
+        assert r == results[i] and np.array_equal(out, outputs[i]), i
+        op, data = reqs[i]
+        want = orc.encode(data) if op == 0 else orc.decode(data)[1]
+        assert np.array_equal(outputs[i], want), i
+    srv.close()
+
+
+def test_small_budget_waits_and_refuses(env):
+    b64, serve, pools = env
+    arrivals, ops, sizes, pick = serve.poisson_requests(20_000, 0.05, 6, 7, hi=1 << 18)
+    srv = serve.Server(4 << 20, [b64.Alphabet.standard()], n_streams=2)
+    lat, results, wall, outputs = serve.run_open_loop(srv, arrivals, ops, sizes, pick, pools,
+                                                      1 << 28, keep_outputs=True)
+    reqs = payloads(ops, sizes, pick, pools)
+    for i in range(arrivals.size):
+        op, data = reqs[i]
+        if op == 0:
+            assert np.array_equal(outputs[i], np.frombuffer(
+                __import__("base64").b64encode(data.tobytes()), np.uint8)), i
+        else:
+            assert results[i] >= 0, i
+    big = np.zeros(8 << 20, np.uint8)
+    out = np.zeros((8 << 20) // 3 * 4 + 4, np.uint8)
+    with pytest.raises(b64.B64Error, match="budget"):
+        srv.submit(1, 0, 0, big.ctypes.data, big.size, out.ctypes.data, out.size)
+    srv.close()

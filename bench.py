@@ -47,10 +47,17 @@ def peaks() -> dict:
         return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def csrc_digest() -> str:
+# The source files each profiled kernel is built from.
+KERNEL_SOURCES = {
+    "encode_tma_kernel": ("b64_encode.cu", "b64_device.cuh"),
+    "decode_fast_kernel": ("b64_decode.cu", "b64_device.cuh"),
+}
+
+
+def source_digest(kernel: str) -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1910_05109_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
+    for name in KERNEL_SOURCES[kernel]:
         with open(os.path.join(d, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
@@ -58,16 +65,16 @@ def csrc_digest() -> str:
 
 def profiled_traffic(kernel: str) -> dict | None:
     """DRAM traffic per input byte of `kernel` from the committed ncu summary,
-    if it was taken on the current kernel sources."""
+    if it was taken on the kernel's current sources."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
         return None
-    digest = csrc_digest()
+    digest = source_digest(kernel)
     for line in open(path):
         if line.startswith("#") or not line.strip():
             continue
         kv = dict(x.split("=", 1) for x in line.split())
-        if kv.get("kernel") == kernel and kv.get("csrc") == digest:
+        if kv.get("kernel") == kernel and kv.get("sources") == digest:
             return {"bytes_per_input_byte": float(kv["dram_bytes_per_input_byte"])}
     return None
 
@@ -440,8 +447,11 @@ def run_batch(args):
             src, src_off = texts
         codec = BatchCodec(op, n, src.numel(), alphs, dev)
         cap = codec.load(src, src_off, d_aid)
-        units, timings = autotune.best_units(op, codec.src, codec.src_off, codec.dst,
-                                             codec.dst_off, alphs, codec.alph_id[:n])
+        if args.tile_units:
+            units, timings = args.tile_units, {}
+        else:
+            units, timings = autotune.best_units(op, codec.src, codec.src_off, codec.dst,
+                                                 codec.dst_off, alphs, codec.alph_id[:n])
         codec.tile_units = units
         for _ in range(max(args.warmup, 3)):
             codec.run()
@@ -462,6 +472,10 @@ def run_batch(args):
         else:
             assert torch.equal(res, d_off[1:] - d_off[:-1])
 
+        if args.no_per_string:
+            out[op] = {"batch_ms": batch_ms, "input_gbps": in_bytes / (batch_ms / 1e3) / 1e9,
+                       "tile_units": units, "autotune_ms": timings}
+            continue
         # One launch per string through the single-buffer calls.
         hoff = codec.src_off.cpu().numpy()
         hdo = codec.dst_off.cpu().numpy()
@@ -537,6 +551,65 @@ def run_batch(args):
           "encode": out["encode"], "decode": out["decode"], "gpu_launches": 5 * args.steps})
 
 
+# ---------------------------------------------------------------- MIME workload
+
+def run_mime(args):
+    """256 MiB of seed-3 random bytes, encoded with the standard table and
+    wrapped as 76-character lines with CRLF (367,332,730 bytes), decoded with
+    CR/LF/space skipped; against a D2D memcpy of the same bytes."""
+    import torch
+    from paper_1910_05109_gb300 import binding as b64
+    from paper_1910_05109_gb300 import build as gpu_build
+    from paper_1910_05109_gb300 import workloads as wl
+
+    gpu_build.build()
+    torch.cuda.set_device(0)
+    n = args.mime_bytes
+    data = wl.random_bytes(n, 3)
+    d = torch.from_numpy(data).cuda()
+    text = wl.mime_wrap(b64.encode(d, b64.Alphabet.standard()).cpu().numpy())
+    src = torch.from_numpy(text).cuda()
+    m = src.numel()
+    dst = torch.empty(b64.decoded_max_length(m), dtype=torch.uint8, device="cuda")
+    res = torch.empty(1, dtype=torch.int64, device="cuda")
+    ws = b64.mime_workspace(m)
+    std = b64.Alphabet.standard()
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        b64.mime_decode_async(src, dst, res, std, ws)
+    torch.cuda.synchronize()
+    assert int(res.item()) == n and torch.equal(dst[:n], d)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        b64.mime_decode_async(src, dst, res, std, ws)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    cp = torch.empty_like(src)
+    for _ in range(3):
+        cp.copy_(src)
+    e0.record(stream)
+    for _ in range(20):
+        cp.copy_(src)
+    e1.record(stream)
+    e1.synchronize()
+    mc = e0.elapsed_time(e1) / 20
+    pk = peaks()
+    dram = (m + n) / (ms / 1e3) / 1e9
+    emit({"metric": METRIC, "workload": "MIME line-wrapped decode", "value": m / (ms / 1e3) / 1e9,
+          "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+          "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+          "dtype": "u8", "data": "synthetic",
+          "config": {"workload": f"{n} random bytes (seed 3), standard table, 76-char lines + "
+                                 "CRLF, no trailing CRLF", "input_bytes": m, "output_bytes": n},
+          "memcpy_gbps": m / (mc / 1e3) / 1e9, "frac_of_memcpy": mc / ms,
+          "roofline": {"bound": "hbm", "kernel": "mime_decode_kernel", "achieved": dram,
+                       "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": dram / pk["hbm_gbs"],
+                       "peak_source": pk["source"], "traffic": None},
+          "gpu_launches": 2 * args.steps})
+
+
 # ---------------------------------------------------------------- serving workload
 
 def run_serve(args):
@@ -594,7 +667,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--bytes", type=int, default=N_BYTES,
                     help="input size (default 1 GiB; smaller sizes are for profiling)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "mime"],
                     help="single: the 1 GiB single-buffer step (default); batch: 100,000 "
                          "strings in one launch sequence vs one launch per string; serve: "
                          "Poisson request stream through the continuous-batching engine")
@@ -602,6 +675,11 @@ def main():
     ap.add_argument("--rate", type=float, default=20_000.0)
     ap.add_argument("--duration", type=float, default=30.0)
     ap.add_argument("--streams", type=int, default=4)
+    ap.add_argument("--mime-bytes", type=int, default=256 << 20)
+    ap.add_argument("--tile-units", type=int, default=0,
+                    help="batch workload: fixed tile size instead of the autotuner's")
+    ap.add_argument("--no-per-string", action="store_true",
+                    help="batch workload: skip the one-launch-per-string comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -609,6 +687,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "mime":
+        run_mime(args)
     else:
         run_gpu(args)
 

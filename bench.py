@@ -189,6 +189,22 @@ def emit(obj: dict):
     print(json.dumps(obj), flush=True)
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest `value` over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(bytes_per_rank_step: float, world_size: int, steps: int, max_ms: float) -> float:
+    """Whole-job GB/s: what every rank processed, over the slowest rank's time."""
+    return bytes_per_rank_step * world_size * steps / (max_ms / 1e3) / 1e9
+
+
 # ---------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -291,10 +307,7 @@ def run_gpu(args):
     ms = start.elapsed_time(stop)
     t_enc = [e[4 * i].elapsed_time(e[4 * i + 1]) for e in evs for i in range(2)]
     t_dec = [e[4 * i + 2].elapsed_time(e[4 * i + 3]) for e in evs for i in range(2)]
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     assert int(res[0]) == n and int(res[1]) == n
 
     # D2D memcpy of the same bytes (torch copy_ issues cudaMemcpyAsync D2D).
@@ -364,7 +377,7 @@ def finish(args, v):
     e2e_ms = v.get("e2e_ms")
 
     step_in = 2 * (n + m)                       # input bytes per step (both tables)
-    value = step_in * ws / (ms / K / 1e3) / 1e9
+    value = job_throughput(step_in, ws, K, ms)
     pk = peaks()
     enc_alg = n + m                             # algorithmic bytes per encode launch
     dec_alg = m + n                             # per decode call (reads m, writes n)

@@ -32,9 +32,10 @@ namespace b64 {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kPerThread = 32;
-constexpr uint32_t kTile = kThreads * kPerThread;       // raw bytes per tile
-constexpr uint32_t kOutCap = kTile / 4 * 3 + 32;        // output bytes a tile may write
+constexpr int kChunks = 4;                              // rounds of 32 bytes per thread
+constexpr uint32_t kChunk = kThreads * 32;              // 8 KiB
+constexpr uint32_t kTile = kChunk * kChunks;            // raw bytes per tile (32 KiB)
+constexpr uint32_t kSpace = 0xC0u;                      // table class of CR, LF, space
 
 // Tile state word: [flag:2][last data byte:8][data characters:54].
 constexpr int kFlagShift = 62;
@@ -43,12 +44,15 @@ constexpr uint64_t kFlagAggregate = 1, kFlagPrefix = 2, kFlagPoison = 3;
 
 __device__ uint32_t g_fault;
 
-__device__ __forceinline__ uint64_t make_state(uint64_t flag, uint32_t last, uint64_t count) {
+__host__ __device__ __forceinline__ uint64_t make_state(uint64_t flag, uint32_t last,
+                                                        uint64_t count) {
     return (flag << kFlagShift) | (uint64_t(last & 0xFFu) << 54) | (count & kCountMask);
 }
-__device__ __forceinline__ uint64_t st_flag(uint64_t s) { return s >> kFlagShift; }
-__device__ __forceinline__ uint32_t st_last(uint64_t s) { return uint32_t(s >> 54) & 0xFFu; }
-__device__ __forceinline__ uint64_t st_count(uint64_t s) { return s & kCountMask; }
+__host__ __device__ __forceinline__ uint64_t st_flag(uint64_t s) { return s >> kFlagShift; }
+__host__ __device__ __forceinline__ uint32_t st_last(uint64_t s) {
+    return uint32_t(s >> 54) & 0xFFu;
+}
+__host__ __device__ __forceinline__ uint64_t st_count(uint64_t s) { return s & kCountMask; }
 
 __device__ __forceinline__ uint64_t ld_relaxed(const unsigned long long* p) {
     unsigned long long v;
@@ -60,35 +64,101 @@ __device__ __forceinline__ void st_relaxed(unsigned long long* p, uint64_t v) {
                  : "memory");
 }
 
+// Four already-translated 6-bit values (one per byte, first in the low byte)
+// -> their 24-bit value a<<18 | b<<12 | c<<6 | d. Each byte is masked to six
+// bits first, so that a byte holding anything larger (a value past the end of
+// the valid data: stale shared memory) cannot carry into the output bytes of
+// the other values.
+__device__ __forceinline__ uint32_t decode4_values(uint32_t w) {
+    w &= 0x3F3F3F3Fu;
+    const uint32_t a = w & 0xFFu, b = (w >> 8) & 0xFFu, c = (w >> 16) & 0xFFu, d = w >> 24;
+    return ((a * 64u + b) * 64u + c) * 64u + d;
+}
+
 __host__ __device__ __forceinline__ uint64_t bytes_for(uint64_t j) {
     const uint64_t r = j & 3;
     return 3 * (j >> 2) + (r ? r - 1 : 0);
 }
 
-__device__ __forceinline__ bool is_space(uint32_t c) { return c == 13 || c == 10 || c == 32; }
+// Dynamic shared memory: raw[kTile] (the tile; later the output bytes) then
+// vals[kTile + 32] (compacted values at (P & 3) + index).
+constexpr size_t kDynSmem = 2 * size_t(kTile) + 32;
 
 struct TileShared {
-    uint8_t lut[256];
-    uint8_t vals[kTile];
-    uint8_t out[kOutCap + 16];
-    uint32_t warp_count[kThreads / 32];
-    uint32_t warp_last[kThreads / 32];
+    uint8_t lut[256];                       // 0..63, 0x80 (bad or '='), kSpace
+    unsigned long long warp_tot[kThreads / 32];
     unsigned long long tile;
     unsigned long long excl;
     uint32_t prev_last;
     uint32_t poisoned;
+    uint32_t last_key;                      // (raw position + 1) << 8 | byte of the last data byte
     uint32_t min_bad_raw, min_eq_raw, min_eq_comp, min_stop_comp;
 };
 
-__global__ void __launch_bounds__(kThreads)
+// The tile's predecessors' published states, 32 at a time (warp 0): the data
+// characters before the tile and the last data byte before it. Returns false
+// if a wait ran out or a predecessor was poisoned.
+__device__ bool look_back(const unsigned long long* __restrict__ states, uint64_t tile,
+                          const unsigned long long* timeout, uint64_t wait_limit_ns,
+                          uint64_t* excl_out, uint32_t* prev_last_out, bool* have_prev_out) {
+    const int lane = threadIdx.x & 31;
+    uint64_t excl = 0;
+    uint32_t prev_last = 0;
+    bool have_prev = false;
+    int64_t wend = int64_t(tile);
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        const int64_t t = wend - 1 - lane;
+        uint64_t s = t >= 0 ? ld_relaxed(states + t) : make_state(kFlagPrefix, 0, 0);
+        uint32_t spins = 0;
+        for (;;) {
+            const bool ready = st_flag(s) != 0;
+            if (__all_sync(0xffffffffu, ready)) break;
+            if (!ready) s = ld_relaxed(states + t);
+            if ((++spins & 31) == 0) {
+                const bool give_up =
+                    global_timer_ns() - t0 > wait_limit_ns || ld_relaxed(timeout) != 0;
+                if (__any_sync(0xffffffffu, give_up)) return false;
+            }
+        }
+        if (__any_sync(0xffffffffu, st_flag(s) == kFlagPoison)) return false;
+        const uint32_t pmask = __ballot_sync(0xffffffffu, st_flag(s) == kFlagPrefix);
+        const int pl = pmask ? __ffs(pmask) - 1 : 31;  // nearest inclusive prefix
+        const bool mine = lane <= pl;
+        uint64_t c = mine ? st_count(s) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        excl += c;
+        if (!have_prev) {
+            const uint32_t lmask = __ballot_sync(0xffffffffu, mine && st_count(s) > 0);
+            if (lmask) {
+                prev_last = __shfl_sync(0xffffffffu, st_last(s), __ffs(lmask) - 1);
+                have_prev = true;
+            }
+        }
+        if (pmask) break;
+        wend -= 32;
+    }
+    *excl_out = excl;
+    *prev_last_out = prev_last;
+    *have_prev_out = have_prev;
+    return true;
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
     mime_decode_kernel(const uint8_t* __restrict__ src, uint64_t m, uint8_t* __restrict__ dst,
                        const __grid_constant__ DecodeTable tab, int padded,
                        unsigned long long* __restrict__ status,
                        unsigned long long* __restrict__ states, uint64_t ntiles,
                        uint64_t skip_tiles, uint64_t wait_limit_ns) {
-    __shared__ __align__(16) TileShared sh;
+    __shared__ TileShared sh;
+    extern __shared__ __align__(16) uint8_t dyn[];
+    uint8_t* raw = dyn;
+    uint8_t* vals = dyn + kTile;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < 64) reinterpret_cast<uint32_t*>(sh.lut)[tid] = tab.w[tid];
+    __syncthreads();
+    if (tid == 0) sh.lut['\r'] = sh.lut['\n'] = sh.lut[' '] = uint8_t(kSpace);
     const bool aligned = (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
     unsigned long long* counter = status + 3;
     unsigned long long* timeout = status + 4;
@@ -98,6 +168,7 @@ __global__ void __launch_bounds__(kThreads)
         if (tid == 0) {
             sh.tile = atomicAdd(counter, 1ull) + skip_tiles;
             sh.min_bad_raw = sh.min_eq_raw = sh.min_eq_comp = sh.min_stop_comp = 0xFFFFFFFFu;
+            sh.last_key = 0;
             sh.poisoned = 0;
         }
         __syncthreads();
@@ -106,141 +177,146 @@ __global__ void __launch_bounds__(kThreads)
         const uint64_t base = tile * kTile;
         const uint32_t len = uint32_t(m - base < kTile ? m - base : kTile);
 
-        // ---- load and classify this thread's 32 bytes (absent bytes read as spaces)
-        uint32_t w[8];
-        const uint32_t lo = uint32_t(tid) * kPerThread;
-        if (aligned && lo + kPerThread <= len) {
-            const uint4 a = *reinterpret_cast<const uint4*>(src + base + lo);
-            const uint4 b = *reinterpret_cast<const uint4*>(src + base + lo + 16);
-            w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
-            w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
-        } else {
+        // ---- stage the tile (coalesced 16-byte loads; bytes past the end read as spaces)
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            constexpr int kLoads = int(kTile / 16 / kThreads) / 2;
+            uint4 v[kLoads];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                uint32_t v = 0;
-                for (int i = 0; i < 4; ++i) {
-                    const uint32_t p = lo + 4 * k + i;
-                    v |= uint32_t(p < len ? src[base + p] : 32u) << (8 * i);
-                }
-                w[k] = v;
-            }
-        }
-        uint32_t count = 0, last = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint32_t c = (w[k] >> (8 * i)) & 0xFFu;
-                if (!is_space(c)) {
-                    ++count;
-                    last = c;
+            for (int i = 0; i < kLoads; ++i) {
+                const uint32_t off = 16 * (tid + kThreads * (i + kLoads * half));
+                if (aligned && off + 16 <= len) {
+                    v[i] = *reinterpret_cast<const uint4*>(src + base + off);
+                } else {
+                    uint8_t* b = reinterpret_cast<uint8_t*>(&v[i]);
+                    for (int k = 0; k < 16; ++k) b[k] = off + k < len ? src[base + off + k] : 32;
                 }
             }
-
-        // ---- block scan of data-character counts; the tile's last data byte
-        uint32_t incl = count;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const uint32_t nonempty = __ballot_sync(0xffffffffu, count > 0);
-        const uint32_t wlast =
-            __shfl_sync(0xffffffffu, last, nonempty ? 31 - __clz(nonempty) : 0);
-        if (lane == 31) {
-            sh.warp_count[warp] = incl;
-            sh.warp_last[warp] = nonempty ? (wlast | 0x100u) : 0u;
+            for (int i = 0; i < kLoads; ++i)
+                *reinterpret_cast<uint4*>(raw + 16 * (tid + kThreads * (i + kLoads * half))) =
+                    v[i];
         }
         __syncthreads();
-        uint32_t wbase = 0, tile_count = 0, tile_last = 0;
-        bool tile_has_last = false;
-        for (int q = 0; q < kThreads / 32; ++q) {
-            if (q < warp) wbase += sh.warp_count[q];
-            tile_count += sh.warp_count[q];
-            if (sh.warp_last[q]) {
-                tile_last = sh.warp_last[q] & 0xFFu;
-                tile_has_last = true;
-            }
-        }
-        const uint32_t excl_local = wbase + incl - count;
 
-        // ---- publish, look back, publish the inclusive prefix
-        if (tid == 0) {
+        // ---- count data characters per 32-byte piece; 4 pieces per thread,
+        //      piece c covers raw bytes [c*kChunk + 32*tid, +32)
+        uint64_t cnt = 0;  // four 16-bit counts, piece c in bits 16c..16c+15
+        uint32_t my_last = 0;
+#pragma unroll 1
+        for (int c = 0; c < kChunks; ++c) {
+            const uint32_t p0 = c * kChunk + 32 * tid;
+            const uint4 x = *reinterpret_cast<const uint4*>(raw + p0);
+            const uint4 y = *reinterpret_cast<const uint4*>(raw + p0 + 16);
+            const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+            uint32_t k = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t ch = __byte_perm(w[q], 0, 0x4440u + i);
+                    if (sh.lut[ch] != kSpace) {
+                        ++k;
+                        my_last = ((p0 + 4 * q + i + 1) << 8) | ch;  // never 0
+                    }
+                }
+            cnt |= uint64_t(k) << (16 * c);
+        }
+        if (my_last) atomicMax(&sh.last_key, my_last);
+        uint64_t incl = cnt;  // scan of the four counts at once (fields never overflow)
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) sh.warp_tot[warp] = incl;
+        __syncthreads();
+        uint64_t before = 0, total = 0;
+#pragma unroll
+        for (int q = 0; q < kThreads / 32; ++q) {
+            if (q < warp) before += sh.warp_tot[q];
+            total += sh.warp_tot[q];
+        }
+        const uint64_t excl_fields = before + incl - cnt;
+        // piece c of this thread starts at data index
+        //   (totals of pieces < c) + (this thread's exclusive count in piece c)
+        uint32_t tile_count = 0;
+#pragma unroll
+        for (int c = 0; c < kChunks; ++c) tile_count += uint32_t((total >> (16 * c)) & 0xFFFFu);
+        const uint32_t tile_last = sh.last_key & 0xFFu;
+        const bool tile_has_last = sh.last_key != 0;
+
+        // ---- publish the aggregate, look back, publish the inclusive prefix
+        if (warp == 0) {
             unsigned long long* my = states + tile;
             uint64_t excl = 0;
             uint32_t prev_last = 0;
-            bool have_prev = false, poison = false;
+            bool have_prev = false, ok = true;
             if (tile == 0) {
-                st_relaxed(my, make_state(kFlagPrefix, tile_last, tile_count));
+                if (lane == 0) st_relaxed(my, make_state(kFlagPrefix, tile_last, tile_count));
             } else {
-                st_relaxed(my, make_state(kFlagAggregate, tile_last, tile_count));
-                const uint64_t t0 = global_timer_ns();
-                for (int64_t t = int64_t(tile) - 1; t >= 0; --t) {
-                    uint64_t s = ld_relaxed(states + t);
-                    uint32_t spins = 0;
-                    while (st_flag(s) == 0) {
-                        // give up after the limit, or as soon as any tile has given up
-                        if ((++spins & 63) == 0 &&
-                            (global_timer_ns() - t0 > wait_limit_ns || ld_relaxed(timeout)))
-                            break;
-                        s = ld_relaxed(states + t);
+                if (lane == 0) st_relaxed(my, make_state(kFlagAggregate, tile_last, tile_count));
+                ok = look_back(states, tile, timeout, wait_limit_ns, &excl, &prev_last,
+                               &have_prev);
+                if (lane == 0) {
+                    if (ok) {
+                        st_relaxed(my, make_state(kFlagPrefix,
+                                                  tile_has_last ? tile_last : prev_last,
+                                                  excl + tile_count));
+                    } else {
+                        st_relaxed(my, make_state(kFlagPoison, 0, 0));
+                        atomicExch(timeout, 1ull);
+                        atomicOr(&g_fault, 1u);
                     }
-                    const uint64_t f = st_flag(s);
-                    if (f == 0 || f == kFlagPoison) {
-                        poison = true;
-                        break;
-                    }
-                    if (!have_prev && st_count(s) > 0) {
-                        prev_last = st_last(s);
-                        have_prev = true;
-                    }
-                    excl += st_count(s);
-                    if (f == kFlagPrefix) break;
-                }
-                if (poison) {
-                    st_relaxed(my, make_state(kFlagPoison, 0, 0));
-                    atomicExch(timeout, 1ull);
-                    atomicOr(&g_fault, 1u);
-                } else {
-                    st_relaxed(my, make_state(kFlagPrefix, tile_has_last ? tile_last : prev_last,
-                                              excl + tile_count));
                 }
             }
-            sh.excl = excl;
-            sh.prev_last = have_prev ? prev_last : 0u;
-            sh.poisoned = poison ? 1u : 0u;
+            if (lane == 0) {
+                sh.excl = excl;
+                sh.prev_last = have_prev ? prev_last : 0u;
+                sh.poisoned = ok ? 0u : 1u;
+            }
         }
         __syncthreads();
         if (sh.poisoned) continue;  // uniform: the whole block skips this tile
         const uint64_t P = sh.excl;
+        const uint32_t shift = uint32_t(P & 3);
 
-        // ---- compact the 6-bit values; note the first bad byte and first '='
-        uint32_t pos = excl_local;
+        // ---- compact the 6-bit values to vals[shift + index]; note errors
+        if (tid == 0 && shift) vals[shift - 1] = sh.lut[sh.prev_last];
         uint32_t bad_raw = 0xFFFFFFFFu, eq_raw = 0xFFFFFFFFu, eq_comp = 0xFFFFFFFFu,
                  stop = 0xFFFFFFFFu;
+#pragma unroll 1
+        for (int c = 0; c < kChunks; ++c) {
+            const uint32_t p0 = c * kChunk + 32 * tid;
+            uint32_t pos = uint32_t((excl_fields >> (16 * c)) & 0xFFFFu);
+            for (int c2 = 0; c2 < c; ++c2) pos += uint32_t((total >> (16 * c2)) & 0xFFFFu);
+            const uint4 x = *reinterpret_cast<const uint4*>(raw + p0);
+            const uint4 y = *reinterpret_cast<const uint4*>(raw + p0 + 16);
+            const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+            for (int q = 0; q < 8; ++q)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint32_t c = (w[k] >> (8 * i)) & 0xFFu;
-                if (!is_space(c)) {
-                    const uint32_t v = sh.lut[c];
-                    sh.vals[pos] = uint8_t(v);
-                    if (v & kBad) {
-                        if (stop == 0xFFFFFFFFu) stop = pos;
-                        const uint32_t raw = lo + 4 * k + i;
-                        if (c == '=' && padded) {
-                            if (eq_raw == 0xFFFFFFFFu) {
-                                eq_raw = raw;
-                                eq_comp = pos;
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t ch = __byte_perm(w[q], 0, 0x4440u + i);
+                    const uint32_t v = sh.lut[ch];
+                    if (v != kSpace) {
+                        vals[shift + pos] = uint8_t(v);
+                        if (v & kBad) {
+                            if (stop == 0xFFFFFFFFu) stop = pos;
+                            const uint32_t raw = p0 + 4 * q + i;
+                            if (ch == '=' && padded) {
+                                if (eq_raw == 0xFFFFFFFFu) {
+                                    eq_raw = raw;
+                                    eq_comp = pos;
+                                }
+                            } else if (bad_raw == 0xFFFFFFFFu) {
+                                bad_raw = raw;
                             }
-                        } else if (bad_raw == 0xFFFFFFFFu) {
-                            bad_raw = raw;
                         }
+                        ++pos;
                     }
-                    ++pos;
                 }
-            }
+        }
         if (stop != 0xFFFFFFFFu) {
             atomicMin(&sh.min_stop_comp, stop);
             if (bad_raw != 0xFFFFFFFFu) atomicMin(&sh.min_bad_raw, bad_raw);
@@ -258,38 +334,35 @@ __global__ void __launch_bounds__(kThreads)
             }
         }
 
-        // ---- the output bytes whose second character is here, before any '=' / bad byte
+        // ---- whole quads, four per thread: 16 values -> 12 bytes into the raw
+        //      buffer (free now); quad Q's values sit at vals[4 * (Q - P/4)]
         const uint32_t jend = sh.min_stop_comp < tile_count ? sh.min_stop_comp : tile_count;
         const uint64_t ob = bytes_for(P), oe = bytes_for(P + jend);
         const uint32_t nout = uint32_t(oe > ob ? oe - ob : 0);
-        const uint32_t vprev = sh.lut[sh.prev_last];
-        for (uint32_t t = tid; t < nout; t += kThreads) {
-            const uint64_t b = ob + t;
-            const uint64_t q = b / 3;
-            const uint32_t r = uint32_t(b - 3 * q);
-            const uint64_t j = 4 * q + r + 1;  // global index of the pair's second character
-            const uint32_t jl = uint32_t(j - P);
-            const uint32_t v1 = jl >= 1 ? sh.vals[jl - 1] : vprev;
-            const uint32_t v2 = sh.vals[jl];
-            uint32_t byte;
-            if (r == 0) byte = (v1 << 2) | (v2 >> 4);
-            else if (r == 1) byte = ((v1 & 15u) << 4) | (v2 >> 2);
-            else byte = ((v1 & 3u) << 6) | v2;
-            sh.out[t] = uint8_t(byte);
+        const uint32_t skip = shift ? shift - 1 : 0;    // bytes of the first quad not ours
+        const uint32_t ngroups = (shift + jend + 15) / 16;
+        uint8_t* out = raw;
+        for (uint32_t g = tid; g < ngroups; g += kThreads) {
+            const uint4 c = *reinterpret_cast<const uint4*>(vals + 16 * g);
+            const uint3 o = pack4x24(decode4_values(c.x), decode4_values(c.y),
+                                     decode4_values(c.z), decode4_values(c.w));
+            uint32_t* ow = reinterpret_cast<uint32_t*>(out + 12 * g);
+            ow[0] = o.x;
+            ow[1] = o.y;
+            ow[2] = o.z;
         }
         __syncthreads();
         // copy out: aligned 16-byte stores for the middle, bytes at the edges
         uint8_t* q = dst + ob;
         const uint32_t head = uint32_t((16 - (reinterpret_cast<uintptr_t>(q) & 15)) & 15);
         const uint32_t h = head < nout ? head : nout;
-        if (tid < int(h)) q[tid] = sh.out[tid];
+        if (tid < int(h)) q[tid] = out[skip + tid];
         const uint32_t body = (nout - h) & ~15u;
         for (uint32_t k = tid; k < body / 16; k += kThreads) {
-            const uint32_t off = h + 16 * k;
-            *reinterpret_cast<uint4*>(q + off) = load16_shifted(sh.out, off, off & 3);
+            const uint32_t off = skip + h + 16 * k;
+            *reinterpret_cast<uint4*>(q + h + 16 * k) = load16_shifted(out, off, off & 3);
         }
-        for (uint32_t i = h + body + tid; i < nout; i += kThreads) q[i] = sh.out[i];
-        __syncthreads();
+        for (uint32_t i = h + body + tid; i < nout; i += kThreads) q[i] = out[skip + i];
     }
 }
 
@@ -320,6 +393,7 @@ __global__ void mime_finalize_kernel(uint64_t m, int padded,
 
 struct Occ {
     std::once_flag once;
+    cudaError_t err = cudaSuccess;
     int ctas = 1;
 };
 Occ g_occ[64];
@@ -349,14 +423,19 @@ cudaError_t launch_mime_decode(const uint8_t* src, uint64_t m, uint8_t* dst,
         Occ& occ = g_occ[di.device & 63];
         std::call_once(occ.once, [&] {
             int c = 1;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, mime_decode_kernel, kThreads,
-                                                              0) != cudaSuccess)
+            occ.err = cudaFuncSetAttribute(mime_decode_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           int(kDynSmem));
+            if (occ.err == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, mime_decode_kernel, kThreads,
+                                                              kDynSmem) != cudaSuccess)
                 c = 1;
             occ.ctas = c > 0 ? c : 1;
         });
+        if (occ.err != cudaSuccess) return occ.err;
         uint64_t grid = uint64_t(di.sm_count) * occ.ctas;
         if (ntiles < grid) grid = ntiles;
-        mime_decode_kernel<<<unsigned(grid), kThreads, 0, st>>>(
+        mime_decode_kernel<<<unsigned(grid), kThreads, kDynSmem, st>>>(
             src, m, dst, tab, padded, status, states, ntiles, skip_tiles, wait_limit_ns);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

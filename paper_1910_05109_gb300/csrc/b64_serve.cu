@@ -57,8 +57,6 @@ public:
         return true;
     }
     void release_front() { blocks_.pop_front(); }
-    bool empty() const { return blocks_.empty(); }
-    size_t cap() const { return cap_; }
 
 private:
     size_t cap_;

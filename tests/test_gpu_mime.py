@@ -15,7 +15,7 @@ from paper_1910_05109_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-TILE = 8192
+TILE = 32768
 
 
 @pytest.fixture(scope="module")
@@ -160,3 +160,21 @@ def test_bounded_wait_timeout_selftest(b64, orc):
     assert b64.device_fault_flag() == 0
     r, got = b64.mime_decode(src, b64.Alphabet.standard())
     assert r == 60_000
+
+
+def test_stale_tile_memory_does_not_leak_into_seams(b64, orc):
+    """A tile's last output byte comes from a group of four that the next tile
+    finishes; the values past the tile's end are stale shared memory. Fill
+    that memory with out-of-range values first (decode an all-bad input), then
+    decode valid text whose tiles end mid-group: every byte must match."""
+    std = b64.Alphabet.standard()
+    junk = np.full(40 * TILE, ord("!"), np.uint8)
+    r, _ = b64.mime_decode(torch.from_numpy(junk).cuda(), std)
+    assert r == -1
+    data = wl.random_bytes(24 << 20, 900)
+    text = wl.mime_wrap(orc.encode(data))
+    for _ in range(3):
+        b64.mime_decode(torch.from_numpy(junk).cuda(), std)
+        r, out = b64.mime_decode(torch.from_numpy(text).cuda(), std)
+        assert r == data.size
+        assert torch.equal(out, torch.from_numpy(data).cuda())

@@ -7,7 +7,7 @@
 #include <cuda_runtime.h>
 
 #ifndef B64_JOIN_WITH_PRMT
-#define B64_JOIN_WITH_PRMT 0
+#define B64_JOIN_WITH_PRMT 1
 #endif
 
 namespace b64 {
@@ -36,9 +36,8 @@ constexpr uint64_t kNoError = ~0ull;
 // Bounded waits give up after this many nanoseconds of %globaltimer.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
-// Joins four bytes (each < 256) into a word, c0 in the low byte. Written as
-// multiply-adds so that it runs on the FMA pipe, leaving the ALU pipe (which
-// the shifts, masks and byte permutes load) free.
+// Joins four bytes (each < 256) into a word, c0 in the low byte: three byte
+// permutes, or (B64_JOIN_WITH_PRMT=0) three multiply-adds on the FMA pipe.
 __device__ __forceinline__ uint32_t join4(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) {
 #if B64_JOIN_WITH_PRMT
     return __byte_perm(__byte_perm(c0, c1, 0x7740u), __byte_perm(c2, c3, 0x7740u), 0x5410u);
@@ -59,15 +58,49 @@ __device__ __forceinline__ uint32_t encode_gathered(uint32_t g, const uint8_t* l
     return join4(c0, c1, c2, c3);
 }
 
+#ifndef B64_ENC_VARIANT
+#define B64_ENC_VARIANT 1
+#endif
+
+// Sec. 2 as a 24-bit number: v = s1<<16 | s2<<8 | s3, whose four 6-bit
+// fields from the top are the four values. The outer fields need one
+// instruction each when the top byte is clean (v >> 18, v & 63); the middle
+// two are taken either with shift-and-mask
+// (ALU pipe) or with a multiply and a multiply-high (FMA pipe), to balance
+// the two pipes.
+// kClean: the top byte of v is zero (otherwise the first field is masked).
+template <bool kClean>
+__device__ __forceinline__ uint32_t encode_v24(uint32_t v, const uint8_t* lut) {
+    const uint32_t c0 = lut[kClean ? v >> 18 : (v >> 18) & 63u];
+#if B64_ENC_VARIANT == 2
+    const uint32_t c1 = lut[__umulhi(v * 16384u, 64u)];
+    const uint32_t c2 = lut[__umulhi(v * 1048576u, 64u)];
+#else
+    const uint32_t c1 = lut[(v >> 12) & 63u];
+    const uint32_t c2 = lut[(v >> 6) & 63u];
+#endif
+    const uint32_t c3 = lut[v & 63u];
+    return join4(c0, c1, c2, c3);
+}
+
 // Encodes 12 bytes held in three little-endian words (x = bytes 0..3,
-// y = 4..7, z = 8..11) into 16 characters, returned as four words. The
-// __byte_perm selectors pick (s2,s1,s3,s2) of each of the four triples.
+// y = 4..7, z = 8..11) into 16 characters, returned as four words. Variant 0:
+// the __byte_perm selectors pick (s2,s1,s3,s2) of each of the four triples
+// (the paper's gather, Sec. 3.1); variants 1, 2: they pick (s3,s2,s1,0), the
+// triple as a big-endian 24-bit number.
 __device__ __forceinline__ uint4 encode12(uint32_t x, uint32_t y, uint32_t z, const uint8_t* lut) {
     uint4 o;
+#if B64_ENC_VARIANT == 0
     o.x = encode_gathered(__byte_perm(x, 0, 0x1201u), lut);
     o.y = encode_gathered(__byte_perm(x, y, 0x4534u), lut);
     o.z = encode_gathered(__byte_perm(y, z, 0x3423u), lut);
     o.w = encode_gathered(__byte_perm(z, 0, 0x2312u), lut);
+#else
+    o.x = encode_v24<true>(__byte_perm(x, 0, 0x4012u), lut);
+    o.y = encode_v24<false>(__byte_perm(x, y, 0x3345u), lut);
+    o.z = encode_v24<false>(__byte_perm(y, z, 0x2234u), lut);
+    o.w = encode_v24<true>(__byte_perm(z, 0, 0x4123u), lut);
+#endif
     return o;
 }
 

@@ -183,7 +183,7 @@ int b64_decode_batch(const uint8_t* src, const int64_t* src_off, int64_t n, uint
  * they decode (a plugin handed only its buffers, a process whose memory budget
  * another component owns, a path that must never enter an allocator). The
  * paper has no counterpart; this is b64_decode_batch with its workspace in a
- * device array the library reserves at load time (about 1 MiB on every GPU
+ * device array the library reserves at load time (512 KiB on every GPU
  * that loads it, kept until exit) instead of caller memory. Same arguments
  * and results as b64_decode_batch, without workspace. At most 65536 strings
  * per call (more returns B64_ERR_INVALID_ARGUMENT). Calls no allocator. All

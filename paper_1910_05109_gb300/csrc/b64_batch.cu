@@ -8,17 +8,23 @@
 // 16 characters (decode), U chosen at launch (the autotuner's tile size).
 //
 // Launch sequence (all on one stream, so it can be recorded in a CUDA graph):
-//   1. prep kernel (one block): tiles per string, exclusive scan into the
-//      caller's workspace; encode writes each string's output length to
-//      results, decode sets each string's error word to "none";
-//   2. tile kernel (persistent): every warp takes an equal, contiguous range
-//      of tiles, finds the string of its first tile by binary search over the
-//      scan and then walks forward. A tile is staged through the warp's
-//      shared memory with aligned 16-byte loads (strings start anywhere),
-//      re-aligned with funnel shifts, coded with the same per-unit steps as
-//      the single-buffer kernels, and copied out with aligned 16-byte stores
-//      and byte stores at the edges. Decode tiles fold bad-byte offsets into
-//      the string's error word with an atomic minimum;
+//   1. encode: one thread per string writes the string's output length to
+//      results; decode: the per-string error words in the caller's workspace
+//      are set to "none" (a memset);
+//   2. tile kernel (persistent): the concatenated input is split into equal
+//      byte ranges, one per warp. A warp finds the strings that hold its
+//      range ends with a 32-way search over src_off and moves both ends up to
+//      the next 3-byte (encode) or 4-character (decode) group boundary of
+//      their string, so neighbouring warps meet without talking to each other
+//      and no per-string scan is needed. It then walks its range string by
+//      string in tiles of at most 32 x U units. A tile is brought into the
+//      warp's shared memory by a bulk (TMA) copy of its 16-byte aligned span
+//      (the next tile's copy is started before the current one is coded), or
+//      staged with aligned loads where the span would leave the source
+//      buffer, re-aligned with funnel shifts, coded with the same per-unit
+//      steps as the single-buffer kernels, and copied out with aligned 16-byte
+//      stores and byte stores at the edges. Decode tiles fold bad-byte offsets
+//      into the string's error word with an atomic minimum;
 //   3. decode only: one thread per string applies the padding and length
 //      rules to the string's last 2..5 characters and writes its result.
 #include <mutex>
@@ -28,7 +34,7 @@
 namespace b64 {
 namespace {
 
-constexpr int kPrepThreads = 1024;
+constexpr int kScanThreads = 1024;
 
 // Warps per block of the tile kernels: the per-warp staging buffers are
 // static shared memory, which must stay under 48 KiB per block.
@@ -45,48 +51,6 @@ __host__ __device__ __forceinline__ uint64_t dec_body_length(uint64_t m) {
 __host__ __device__ __forceinline__ uint64_t enc_length(uint64_t n, int padded) {
     const uint64_t g = n / 3, r = n % 3;
     return r == 0 ? 4 * g : 4 * g + (padded ? 4 : r + 1);
-}
-
-// ------------------------------------------------------------------ prep
-// tile_start[0..n] = exclusive scan of tiles per string (tile_start[n] = total).
-template <bool kDecode>
-__global__ void __launch_bounds__(kPrepThreads)
-    batch_prep_kernel(const int64_t* __restrict__ src_off, int64_t n, uint32_t tile_bytes,
-                      const __grid_constant__ BatchTables tabs, const uint8_t* __restrict__ alph_id,
-                      int64_t* __restrict__ tile_start, int64_t* __restrict__ results,
-                      unsigned long long* __restrict__ err) {
-    __shared__ int64_t part[kPrepThreads];
-    const int tid = threadIdx.x;
-    const int64_t per = (n + kPrepThreads - 1) / kPrepThreads;
-    const int64_t b = per * tid, e = b + per < n ? b + per : n;
-    int64_t sum = 0;
-    for (int64_t i = b; i < e; ++i) {
-        const uint64_t len = uint64_t(src_off[i + 1] - src_off[i]);
-        const uint64_t work = kDecode ? dec_body_length(len) : len;
-        sum += int64_t((work + tile_bytes - 1) / tile_bytes);
-    }
-    part[tid] = sum;
-    __syncthreads();
-    for (int o = 1; o < kPrepThreads; o <<= 1) {  // inclusive scan of the partial sums
-        const int64_t v = tid >= o ? part[tid - o] : 0;
-        __syncthreads();
-        part[tid] += v;
-        __syncthreads();
-    }
-    int64_t run = part[tid] - sum;
-    for (int64_t i = b; i < e; ++i) {
-        tile_start[i] = run;
-        const uint64_t len = uint64_t(src_off[i + 1] - src_off[i]);
-        const uint64_t work = kDecode ? dec_body_length(len) : len;
-        run += int64_t((work + tile_bytes - 1) / tile_bytes);
-        if (kDecode) {
-            err[i] = kNoError;
-        } else {
-            const int a = alph_id ? (alph_id[i] & (kMaxAlphabets - 1)) : 0;
-            results[i] = int64_t(enc_length(len, tabs.padded[a]));
-        }
-    }
-    if (tid == kPrepThreads - 1) tile_start[n] = part[kPrepThreads - 1];
 }
 
 // ------------------------------------------------------------------ staging helpers
@@ -113,6 +77,42 @@ __device__ __forceinline__ void warp_stage_in(uint8_t* sbuf, const uint8_t* base
     }
 }
 
+__device__ uint32_t g_fault;
+
+// Lane 0 only: if the 16-byte aligned span around [a, b) lies inside the
+// source buffer [0, src_end), start one bulk (TMA) copy of it into sbuf
+// (byte a lands at sbuf[(base + a) & 15], as warp_stage_in places it),
+// completing on `bar`, and return true; otherwise return false and the warp
+// stages the tile itself when it gets to it.
+__device__ __forceinline__ bool issue_tile_load(uint8_t* sbuf, const uint8_t* base, uint64_t a,
+                                                uint64_t b, uint64_t src_end, uint64_t* bar) {
+    const uintptr_t pa = reinterpret_cast<uintptr_t>(base + a) & ~uintptr_t(15);
+    const uintptr_t pb = (reinterpret_cast<uintptr_t>(base + b) + 15) & ~uintptr_t(15);
+    if (pa < reinterpret_cast<uintptr_t>(base) ||
+        pb > reinterpret_cast<uintptr_t>(base + src_end) || pb == pa)
+        return false;
+    const uint32_t bytes = uint32_t(pb - pa);
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_load(sbuf, reinterpret_cast<const void*>(pa), bytes, bar);
+    return true;
+}
+
+// Makes tile t's staged bytes available in sbuf: waits for its bulk copy
+// (bounded), or stages it now. Returns false if the wait ran out.
+__device__ __forceinline__ bool tile_ready(bool by_copy, uint8_t* sbuf, uint64_t* bar,
+                                           uint32_t& phases, int k, const uint8_t* base,
+                                           uint64_t a, uint64_t b, uint64_t src_end, int lane) {
+    if (by_copy) {
+        const bool ok = mbar_wait(bar, (phases >> k) & 1u);
+        phases ^= 1u << k;
+        return __all_sync(0xffffffffu, ok);
+    }
+    warp_stage_in(sbuf, base, a, b, 0, src_end, lane);
+    fence_proxy_async_smem();  // before a later bulk copy reuses this buffer
+    __syncwarp();
+    return true;
+}
+
 // Writes sbuf[0 .. len) to global q (any alignment): aligned 16-byte stores
 // for the middle, byte stores for the ragged head and tail. Warp-collective.
 __device__ __forceinline__ void warp_stage_out(uint8_t* q, const uint8_t* sbuf, uint32_t len,
@@ -129,17 +129,82 @@ __device__ __forceinline__ void warp_stage_out(uint8_t* q, const uint8_t* sbuf, 
     for (uint32_t i = h + body + lane; i < len; i += 32) q[i] = sbuf[i];
 }
 
-// Binary search (every lane computes the same result): the string s with
-// tile_start[s] <= t < tile_start[s+1], which skips strings with no tiles.
-__device__ __forceinline__ int64_t find_string(const int64_t* __restrict__ tile_start, int64_t n,
-                                               int64_t t) {
-    int64_t lo = 0, hi = n;  // invariant: tile_start[lo] <= t < tile_start[hi]
+// Warp-cooperative search: the largest string s in [0, n) with
+// src_off[s] <= x, for src_off[0] <= x < src_off[n] (that string is never
+// empty). Each round every lane probes one of 32 evenly spaced candidates.
+__device__ __forceinline__ int64_t warp_find_string(const int64_t* __restrict__ src_off,
+                                                    int64_t n, int64_t x, int lane) {
+    int64_t lo = 0, hi = n;  // src_off[lo] <= x < src_off[hi]
     while (hi - lo > 1) {
-        const int64_t mid = lo + (hi - lo) / 2;
-        if (tile_start[mid] <= t) lo = mid;
-        else hi = mid;
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t probe = lo + int64_t(lane) * step;
+        const bool le = probe < hi && src_off[probe] <= x;
+        const uint32_t mask = __ballot_sync(0xffffffffu, le);
+        const int k = 31 - __clz(mask);  // lane 0 always holds (probe = lo)
+        const int64_t nlo = lo + int64_t(k) * step;
+        const int64_t nhi = nlo + step < hi ? nlo + step : hi;
+        lo = nlo;
+        hi = nhi;
     }
     return lo;
+}
+
+// Where a warp's range boundary at byte x (src_off coordinates) really falls:
+// rounded up to the next group boundary (3 bytes for encode, 4 characters for
+// decode) of the string that holds x, but not past the end of the string's
+// coded part (its end; for decode, its body). Every warp rounds the same way,
+// so neighbouring ranges meet exactly.
+template <bool kDecode>
+__device__ __forceinline__ int64_t round_boundary(const int64_t* __restrict__ src_off, int64_t n,
+                                                  int64_t x, int lane) {
+    if (x >= src_off[n]) return src_off[n];
+    const int64_t s = warp_find_string(src_off, n, x, lane);
+    const int64_t s0 = src_off[s];
+    const int64_t len = src_off[s + 1] - s0;
+    const int64_t lim = kDecode ? int64_t(dec_body_length(uint64_t(len))) : len;
+    constexpr int64_t g = kDecode ? 4 : 3;
+    const int64_t r = (x - s0 + g - 1) / g * g;
+    return s0 + (r < lim ? r : lim);
+}
+
+// The warp's walk over its range [pos, end): strings in order, tiles of at
+// most T bytes, each starting on a group boundary of its string.
+template <bool kDecode>
+struct Cursor {
+    int64_t s, pos, end;
+    __device__ __forceinline__ bool next(const int64_t* __restrict__ src_off, int64_t n, int64_t T,
+                                         int64_t* ts, int64_t* ta, int64_t* tb) {
+        for (;;) {
+            if (pos >= end || s >= n) return false;
+            const int64_t s0 = src_off[s], len = src_off[s + 1] - s0;
+            const int64_t lim = s0 + (kDecode ? int64_t(dec_body_length(uint64_t(len))) : len);
+            if (pos < s0) pos = s0;
+            if (pos >= end) return false;
+            if (pos >= lim) {  // string done (or empty): on to the next one
+                ++s;
+                continue;
+            }
+            int64_t b = pos + T;
+            if (b > lim) b = lim;
+            if (b > end) b = end;
+            *ts = s;
+            *ta = pos;
+            *tb = b;
+            pos = b;
+            return true;
+        }
+    }
+};
+
+// Each string's encoded length (encode results), one thread per string.
+__global__ void encode_results_kernel(const int64_t* __restrict__ src_off, int64_t n,
+                                      const __grid_constant__ BatchTables tabs,
+                                      const uint8_t* __restrict__ alph_id,
+                                      int64_t* __restrict__ results) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int a = alph_id ? (alph_id[i] & (kMaxAlphabets - 1)) : 0;
+    results[i] = int64_t(enc_length(uint64_t(src_off[i + 1] - src_off[i]), tabs.padded[a]));
 }
 
 // ------------------------------------------------------------------ encode tiles
@@ -148,49 +213,72 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
     encode_batch_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
                         int64_t n, uint8_t* __restrict__ dst, const int64_t* __restrict__ dst_off,
                         const __grid_constant__ BatchTables tabs,
-                        const uint8_t* __restrict__ alph_id,
-                        const int64_t* __restrict__ tile_start) {
+                        const uint8_t* __restrict__ alph_id) {
     constexpr int kWarps = TileShape<U>::kWarps, kThreads = TileShape<U>::kThreads;
     constexpr uint32_t T = 32 * U * 12;        // input bytes per tile
     constexpr uint32_t TO = T / 3 * 4 + 4;     // output characters per tile (+ padding group)
     constexpr uint32_t SIN = T + 32;           // staging room for a ragged start
     constexpr uint32_t SOUT = (TO + 16 + 15) & ~15u;  // rows stay 16-byte aligned
     __shared__ __align__(16) uint8_t luts[kMaxAlphabets][64];
-    __shared__ __align__(16) uint8_t sin_all[kWarps][SIN];
+    __shared__ __align__(16) uint8_t sin_all[kWarps][2][SIN];
     __shared__ __align__(16) uint8_t sout_all[kWarps][SOUT];
+    __shared__ uint64_t bars[kWarps][2];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < kMaxAlphabets * 16; i += kThreads)
         reinterpret_cast<uint32_t*>(luts)[i] = tabs.enc[i / 16].w[i % 16];
+    if (lane == 0) {
+        mbar_init(&bars[warp][0], 1);
+        mbar_init(&bars[warp][1], 1);
+        fence_mbar_init();
+    }
     __syncthreads();
-    uint8_t* sin = sin_all[warp];
     uint8_t* sout = sout_all[warp];
 
-    const int64_t total = tile_start[n];
+    const int64_t origin = src_off[0], bytes = src_off[n] - origin;
     const int64_t GW = int64_t(gridDim.x) * kWarps;
     const int64_t gw = int64_t(blockIdx.x) * kWarps + warp;
-    const int64_t per = (total + GW - 1) / GW;
-    const int64_t t0 = gw * per, t1 = t0 + per < total ? t0 + per : total;
-    if (t0 >= t1) return;
-    int64_t s = find_string(tile_start, n, t0);
+    if (bytes <= 0) return;
+    const int64_t x0 = origin + bytes * gw / GW, x1 = origin + bytes * (gw + 1) / GW;
+    Cursor<false> cur{0, round_boundary<false>(src_off, n, x0, lane),
+                      gw + 1 == GW ? src_off[n] : round_boundary<false>(src_off, n, x1, lane)};
+    if (cur.pos >= cur.end) return;
+    cur.s = cur.pos < src_off[n] ? warp_find_string(src_off, n, cur.pos, lane) : n;
     const uint64_t src_end = uint64_t(src_off[n]);
 
-    for (int64_t t = t0; t < t1; ++t) {
-        while (t >= tile_start[s + 1]) ++s;
-        const int64_t lt = t - tile_start[s];
-        const uint64_t s0 = uint64_t(src_off[s]), s1 = uint64_t(src_off[s + 1]);
-        const uint64_t a = s0 + uint64_t(lt) * T;
-        const uint64_t b = a + T < s1 ? a + T : s1;
+    // The tile after the current one is described and its bulk copy started
+    // before the current one is coded (two staging buffers per warp).
+    int64_t cs, ns = 0, ia, ib, na = 0, nb = 0;
+    if (!cur.next(src_off, n, T, &cs, &ia, &ib)) return;
+    uint64_t a = uint64_t(ia), b = uint64_t(ib);
+    bool by_copy = false, n_by_copy = false;
+    if (lane == 0) by_copy = issue_tile_load(sin_all[warp][0], src, a, b, src_end, &bars[warp][0]);
+    by_copy = __shfl_sync(0xffffffffu, by_copy, 0);
+    uint32_t phases = 0;
+
+    for (int64_t t = 0;; ++t) {
+        const int k = int(t & 1);
+        fence_proxy_async_smem();  // this lane's reads of tile t - 1 before the copy below
+        __syncwarp();              // every lane is done with the other buffer
+        const bool more = cur.next(src_off, n, T, &ns, &na, &nb);
+        if (more) {
+            if (lane == 0)
+                n_by_copy = issue_tile_load(sin_all[warp][k ^ 1], src, uint64_t(na),
+                                            uint64_t(nb), src_end, &bars[warp][k ^ 1]);
+            n_by_copy = __shfl_sync(0xffffffffu, n_by_copy, 0);
+        }
+        uint8_t* sin = sin_all[warp][k];
+        if (!tile_ready(by_copy, sin, &bars[warp][k], phases, k, src, a, b, src_end, lane)) {
+            if (lane == 0) atomicOr(&g_fault, 1u);
+            return;
+        }
+        const uint64_t s1 = uint64_t(src_off[cs + 1]);
         const bool last = b == s1;
-        const int ai = alph_id ? (alph_id[s] & (kMaxAlphabets - 1)) : 0;
+        const int ai = alph_id ? (alph_id[cs] & (kMaxAlphabets - 1)) : 0;
         const uint8_t* lut = luts[ai];
         const uint32_t nbytes = uint32_t(b - a);
         const uint32_t triples = nbytes / 3;
         const uint32_t delta = uint32_t((reinterpret_cast<uintptr_t>(src + a)) & 15);
-
-        __syncwarp();
-        warp_stage_in(sin, src, a, b, 0, src_end, lane);
-        __syncwarp();
         const uint32_t sh = delta & 3;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -225,7 +313,11 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
             nout += tabs.padded[ai] ? 4 : r + 1;
         }
         __syncwarp();
-        warp_stage_out(dst + dst_off[s] + uint64_t(lt) * (T / 3 * 4), sout, nout, lane);
+        const uint64_t rel = a - uint64_t(src_off[cs]);  // a multiple of 3
+        warp_stage_out(dst + dst_off[cs] + rel / 3 * 4, sout, nout, lane);
+        __syncwarp();  // sout is rewritten by the next tile
+        if (!more) break;
+        a = uint64_t(na); b = uint64_t(nb); cs = ns; by_copy = n_by_copy;
     }
 }
 
@@ -236,7 +328,6 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
                         int64_t n, uint8_t* __restrict__ dst, const int64_t* __restrict__ dst_off,
                         const __grid_constant__ BatchTables tabs,
                         const uint8_t* __restrict__ alph_id,
-                        const int64_t* __restrict__ tile_start,
                         unsigned long long* __restrict__ err) {
     constexpr int kWarps = TileShape<U>::kWarps, kThreads = TileShape<U>::kThreads;
     constexpr uint32_t T = 32 * U * 16;  // characters per tile
@@ -244,39 +335,61 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
     constexpr uint32_t SIN = T + 32;
     constexpr uint32_t SOUT = (TO + 16 + 15) & ~15u;
     __shared__ __align__(16) uint8_t luts[kMaxAlphabets][256];
-    __shared__ __align__(16) uint8_t sin_all[kWarps][SIN];
+    __shared__ __align__(16) uint8_t sin_all[kWarps][2][SIN];
     __shared__ __align__(16) uint8_t sout_all[kWarps][SOUT];
+    __shared__ uint64_t bars[kWarps][2];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < kMaxAlphabets * 64; i += kThreads)
         reinterpret_cast<uint32_t*>(luts)[i] = tabs.dec[i / 64].w[i % 64];
+    if (lane == 0) {
+        mbar_init(&bars[warp][0], 1);
+        mbar_init(&bars[warp][1], 1);
+        fence_mbar_init();
+    }
     __syncthreads();
-    uint8_t* sin = sin_all[warp];
     uint8_t* sout = sout_all[warp];
 
-    const int64_t total = tile_start[n];
+    const int64_t origin = src_off[0], bytes = src_off[n] - origin;
     const int64_t GW = int64_t(gridDim.x) * kWarps;
     const int64_t gw = int64_t(blockIdx.x) * kWarps + warp;
-    const int64_t per = (total + GW - 1) / GW;
-    const int64_t t0 = gw * per, t1 = t0 + per < total ? t0 + per : total;
-    if (t0 >= t1) return;
-    int64_t s = find_string(tile_start, n, t0);
+    if (bytes <= 0) return;
+    const int64_t x0 = origin + bytes * gw / GW, x1 = origin + bytes * (gw + 1) / GW;
+    Cursor<true> cur{0, round_boundary<true>(src_off, n, x0, lane),
+                      gw + 1 == GW ? src_off[n] : round_boundary<true>(src_off, n, x1, lane)};
+    if (cur.pos >= cur.end) return;
+    cur.s = cur.pos < src_off[n] ? warp_find_string(src_off, n, cur.pos, lane) : n;
     const uint64_t src_end = uint64_t(src_off[n]);
 
-    for (int64_t t = t0; t < t1; ++t) {
-        while (t >= tile_start[s + 1]) ++s;
-        const int64_t lt = t - tile_start[s];
-        const uint64_t s0 = uint64_t(src_off[s]);
-        const uint64_t body = dec_body_length(uint64_t(src_off[s + 1]) - s0);
-        const uint64_t a = s0 + uint64_t(lt) * T;
-        const uint64_t b = a + T < s0 + body ? a + T : s0 + body;
-        const uint8_t* lut = luts[alph_id ? (alph_id[s] & (kMaxAlphabets - 1)) : 0];
+    // The tile after the current one is described and its bulk copy started
+    // before the current one is coded (two staging buffers per warp).
+    int64_t cs, ns = 0, ia, ib, na = 0, nb = 0;
+    if (!cur.next(src_off, n, T, &cs, &ia, &ib)) return;
+    uint64_t a = uint64_t(ia), b = uint64_t(ib);
+    bool by_copy = false, n_by_copy = false;
+    if (lane == 0) by_copy = issue_tile_load(sin_all[warp][0], src, a, b, src_end, &bars[warp][0]);
+    by_copy = __shfl_sync(0xffffffffu, by_copy, 0);
+    uint32_t phases = 0;
+
+    for (int64_t t = 0;; ++t) {
+        const int k = int(t & 1);
+        fence_proxy_async_smem();  // this lane's reads of tile t - 1 before the copy below
+        __syncwarp();              // every lane is done with the other buffer
+        const bool more = cur.next(src_off, n, T, &ns, &na, &nb);
+        if (more) {
+            if (lane == 0)
+                n_by_copy = issue_tile_load(sin_all[warp][k ^ 1], src, uint64_t(na),
+                                            uint64_t(nb), src_end, &bars[warp][k ^ 1]);
+            n_by_copy = __shfl_sync(0xffffffffu, n_by_copy, 0);
+        }
+        uint8_t* sin = sin_all[warp][k];
+        if (!tile_ready(by_copy, sin, &bars[warp][k], phases, k, src, a, b, src_end, lane)) {
+            if (lane == 0) atomicOr(&g_fault, 1u);
+            return;
+        }
+        const uint8_t* lut = luts[alph_id ? (alph_id[cs] & (kMaxAlphabets - 1)) : 0];
         const uint32_t nchars = uint32_t(b - a);  // a multiple of 4
         const uint32_t delta = uint32_t((reinterpret_cast<uintptr_t>(src + a)) & 15);
-
-        __syncwarp();
-        warp_stage_in(sin, src, a, b, 0, src_end, lane);
-        __syncwarp();
         const uint32_t sh = delta & 3;
         uint64_t first = kNoError;
 #pragma unroll
@@ -294,7 +407,7 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
                 if (e & kBad) {
                     for (uint32_t i = 0; i < 16; ++i) {
                         if (lut[sin[delta + 16 * j + i]] & kBad) {
-                            const uint64_t off = uint64_t(lt) * T + 16 * j + i;
+                            const uint64_t off = a - uint64_t(src_off[cs]) + 16 * j + i;
                             first = off < first ? off : first;
                             break;
                         }
@@ -313,7 +426,7 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
                     if (e & kBad) {
                         for (uint32_t i = 0; i < 4; ++i) {
                             if (lut[sin[p + i]] & kBad) {
-                                const uint64_t off = uint64_t(lt) * T + 4 * q + i;
+                                const uint64_t off = a - uint64_t(src_off[cs]) + 4 * q + i;
                                 first = off < first ? off : first;
                                 break;
                             }
@@ -323,9 +436,13 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
             }
         }
         const uint64_t wmin = warp_min_u64(first);
-        if (lane == 0 && wmin != kNoError) atomicMin(&err[s], (unsigned long long)wmin);
+        if (lane == 0 && wmin != kNoError) atomicMin(&err[cs], (unsigned long long)wmin);
         __syncwarp();
-        warp_stage_out(dst + dst_off[s] + uint64_t(lt) * TO, sout, nchars / 4 * 3, lane);
+        const uint64_t rel = a - uint64_t(src_off[cs]);  // a multiple of 4
+        warp_stage_out(dst + dst_off[cs] + rel / 4 * 3, sout, nchars / 4 * 3, lane);
+        __syncwarp();  // sout is rewritten by the next tile
+        if (!more) break;
+        a = uint64_t(na); b = uint64_t(nb); cs = ns; by_copy = n_by_copy;
     }
 }
 
@@ -406,99 +523,130 @@ Occ g_enc_occ[4][64], g_dec_occ[4][64];
 int unit_slot(int units) { return units == 1 ? 0 : units == 2 ? 1 : units == 4 ? 2 : 3; }
 
 template <int U>
-cudaError_t launch_encode_tiles(const BatchArgs& a, const BatchTables& t, const int64_t* tiles,
-                                cudaStream_t st) {
+cudaError_t launch_encode_tiles(const BatchArgs& a, const BatchTables& t, cudaStream_t st) {
     const DeviceInfo& di = device_info();
     constexpr int threads = TileShape<U>::kThreads;
     const int occ =
         occupancy(encode_batch_kernel<U>, threads, g_enc_occ[unit_slot(U)][di.device & 63]);
     encode_batch_kernel<U><<<unsigned(di.sm_count * occ), threads, 0, st>>>(
-        a.src, a.src_off, a.n, a.dst, a.dst_off, t, a.alph_id, tiles);
+        a.src, a.src_off, a.n, a.dst, a.dst_off, t, a.alph_id);
     return cudaGetLastError();
 }
 
 template <int U>
-cudaError_t launch_decode_tiles(const BatchArgs& a, const BatchTables& t, const int64_t* tiles,
+cudaError_t launch_decode_tiles(const BatchArgs& a, const BatchTables& t,
                                 unsigned long long* err, cudaStream_t st) {
     const DeviceInfo& di = device_info();
     constexpr int threads = TileShape<U>::kThreads;
     const int occ =
         occupancy(decode_batch_kernel<U>, threads, g_dec_occ[unit_slot(U)][di.device & 63]);
     decode_batch_kernel<U><<<unsigned(di.sm_count * occ), threads, 0, st>>>(
-        a.src, a.src_off, a.n, a.dst, a.dst_off, t, a.alph_id, tiles, err);
+        a.src, a.src_off, a.n, a.dst, a.dst_off, t, a.alph_id, err);
     return cudaGetLastError();
 }
 
-// dst_off = exclusive scan of per-string output capacities (one block).
+// Inclusive scan over the warp's lanes.
+__device__ __forceinline__ int64_t warp_inclusive_scan(int64_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// dst_off = exclusive scan of per-string output capacities. One block walks
+// the strings in chunks of kScanThreads x kScanItems (each thread takes
+// kScanItems consecutive strings), scanning each chunk with warp shuffles and
+// carrying the running total.
+constexpr int kScanItems = 8;
+
 template <bool kDecode>
-__global__ void __launch_bounds__(kPrepThreads)
+__global__ void __launch_bounds__(kScanThreads)
     batch_offsets_kernel(const int64_t* __restrict__ src_off, int64_t n,
                          const __grid_constant__ BatchTables tabs,
                          const uint8_t* __restrict__ alph_id, int64_t* __restrict__ dst_off) {
-    __shared__ int64_t part[kPrepThreads];
-    const int tid = threadIdx.x;
-    const int64_t per = (n + kPrepThreads - 1) / kPrepThreads;
-    const int64_t b = per * tid, e = b + per < n ? b + per : n;
-    auto cap = [&](int64_t i) -> int64_t {
-        const uint64_t len = uint64_t(src_off[i + 1] - src_off[i]);
-        if (kDecode) return int64_t((len + 3) / 4 * 3);
-        const int a = alph_id ? (alph_id[i] & (kMaxAlphabets - 1)) : 0;
-        return int64_t(enc_length(len, tabs.padded[a]));
-    };
-    int64_t sum = 0;
-    for (int64_t i = b; i < e; ++i) sum += cap(i);
-    part[tid] = sum;
-    __syncthreads();
-    for (int o = 1; o < kPrepThreads; o <<= 1) {
-        const int64_t v = tid >= o ? part[tid - o] : 0;
+    __shared__ int64_t warp_sum[kScanThreads / 32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int64_t carry = 0;
+    for (int64_t base = 0; base < n; base += int64_t(kScanThreads) * kScanItems) {
+        const int64_t i0 = base + int64_t(tid) * kScanItems;
+        int64_t cap[kScanItems];
+        int64_t sum = 0;
+        int64_t prev = i0 < n ? src_off[i0] : 0;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            const int64_t i = i0 + j;
+            cap[j] = 0;
+            if (i < n) {
+                const int64_t next = src_off[i + 1];
+                const uint64_t len = uint64_t(next - prev);
+                prev = next;
+                if (kDecode) {
+                    cap[j] = int64_t((len + 3) / 4 * 3);
+                } else {
+                    const int al = alph_id ? (alph_id[i] & (kMaxAlphabets - 1)) : 0;
+                    cap[j] = int64_t(enc_length(len, tabs.padded[al]));
+                }
+            }
+            sum += cap[j];
+        }
+        const int64_t incl = warp_inclusive_scan(sum, lane);
+        if (lane == 31) warp_sum[warp] = incl;
         __syncthreads();
-        part[tid] += v;
+        if (warp == 0) warp_sum[lane] = warp_inclusive_scan(warp_sum[lane], lane);
         __syncthreads();
+        int64_t run = carry + (warp ? warp_sum[warp - 1] : 0) + incl - sum;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            if (i0 + j < n) dst_off[i0 + j] = run;
+            run += cap[j];
+        }
+        carry += warp_sum[kScanThreads / 32 - 1];
+        __syncthreads();  // warp_sum is rewritten by the next chunk
     }
-    int64_t run = part[tid] - sum;
-    for (int64_t i = b; i < e; ++i) {
-        dst_off[i] = run;
-        run += cap(i);
-    }
-    if (tid == kPrepThreads - 1) dst_off[n] = part[kPrepThreads - 1];
+    if (tid == 0) dst_off[n] = carry;
 }
 
 }  // namespace
 
+uint32_t batch_fault_flag(bool clear) {
+    uint32_t v = 0;
+    cudaMemcpyFromSymbol(&v, g_fault, sizeof(v));
+    if (clear && v) {
+        const uint32_t z = 0;
+        cudaMemcpyToSymbol(g_fault, &z, sizeof(z));
+    }
+    return v;
+}
+
 size_t batch_workspace_bytes(int64_t n) {
-    // tile scan (n+1 int64) then one error word per string, 256-byte aligned.
-    const size_t scan = (size_t(n) + 1) * sizeof(int64_t);
-    return ((scan + 255) & ~size_t(255)) + size_t(n) * sizeof(uint64_t);
+    // One error word per string (decode).
+    return size_t(n) * sizeof(uint64_t);
 }
 
 cudaError_t launch_batch(bool decode, const BatchArgs& a, const BatchTables& tabs, int units,
                          void* workspace, cudaStream_t st) {
-    int64_t* tiles = static_cast<int64_t*>(workspace);
-    const size_t scan = (size_t(a.n) + 1) * sizeof(int64_t);
-    unsigned long long* err = reinterpret_cast<unsigned long long*>(
-        static_cast<uint8_t*>(workspace) + ((scan + 255) & ~size_t(255)));
-    const uint32_t tile_bytes = uint32_t(32 * units * (decode ? 16 : 12));
-    if (decode)
-        batch_prep_kernel<true><<<1, kPrepThreads, 0, st>>>(a.src_off, a.n, tile_bytes, tabs,
-                                                            a.alph_id, tiles, a.results, err);
-    else
-        batch_prep_kernel<false><<<1, kPrepThreads, 0, st>>>(a.src_off, a.n, tile_bytes, tabs,
-                                                             a.alph_id, tiles, a.results, err);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     if (!decode) {
+        encode_results_kernel<<<unsigned((a.n + 255) / 256), 256, 0, st>>>(a.src_off, a.n, tabs,
+                                                                           a.alph_id, a.results);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
         switch (units) {
-            case 1: return launch_encode_tiles<1>(a, tabs, tiles, st);
-            case 2: return launch_encode_tiles<2>(a, tabs, tiles, st);
-            case 4: return launch_encode_tiles<4>(a, tabs, tiles, st);
-            default: return launch_encode_tiles<8>(a, tabs, tiles, st);
+            case 1: return launch_encode_tiles<1>(a, tabs, st);
+            case 2: return launch_encode_tiles<2>(a, tabs, st);
+            case 4: return launch_encode_tiles<4>(a, tabs, st);
+            default: return launch_encode_tiles<8>(a, tabs, st);
         }
     }
+    unsigned long long* err = static_cast<unsigned long long*>(workspace);
+    cudaError_t e = cudaMemsetAsync(err, 0xFF, size_t(a.n) * sizeof(uint64_t), st);  // kNoError
+    if (e != cudaSuccess) return e;
     switch (units) {
-        case 1: e = launch_decode_tiles<1>(a, tabs, tiles, err, st); break;
-        case 2: e = launch_decode_tiles<2>(a, tabs, tiles, err, st); break;
-        case 4: e = launch_decode_tiles<4>(a, tabs, tiles, err, st); break;
-        default: e = launch_decode_tiles<8>(a, tabs, tiles, err, st); break;
+        case 1: e = launch_decode_tiles<1>(a, tabs, err, st); break;
+        case 2: e = launch_decode_tiles<2>(a, tabs, err, st); break;
+        case 4: e = launch_decode_tiles<4>(a, tabs, err, st); break;
+        default: e = launch_decode_tiles<8>(a, tabs, err, st); break;
     }
     if (e != cudaSuccess) return e;
     const unsigned grid = unsigned((a.n + 255) / 256);
@@ -515,9 +663,9 @@ cudaError_t launch_batch_offsets(bool decode, const int64_t* src_off, int64_t n,
                                  const BatchTables& tabs, const uint8_t* alph_id,
                                  int64_t* dst_off, cudaStream_t st) {
     if (decode)
-        batch_offsets_kernel<true><<<1, kPrepThreads, 0, st>>>(src_off, n, tabs, alph_id, dst_off);
+        batch_offsets_kernel<true><<<1, kScanThreads, 0, st>>>(src_off, n, tabs, alph_id, dst_off);
     else
-        batch_offsets_kernel<false><<<1, kPrepThreads, 0, st>>>(src_off, n, tabs, alph_id, dst_off);
+        batch_offsets_kernel<false><<<1, kScanThreads, 0, st>>>(src_off, n, tabs, alph_id, dst_off);
     return cudaGetLastError();
 }
 

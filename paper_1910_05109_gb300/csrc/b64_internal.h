@@ -67,6 +67,7 @@ struct BatchArgs {
 };
 
 size_t batch_workspace_bytes(int64_t n);
+uint32_t batch_fault_flag(bool clear);
 // Fills the by-value tables of a batched call from 1..kMaxAlphabets handles
 // (later slots repeat alphabet 0). Returns B64_SUCCESS or sets the error.
 int batch_tables(const char* fn, const b64_alphabet* const* alphabets, int n_alphabets,

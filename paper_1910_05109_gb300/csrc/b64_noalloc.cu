@@ -1,7 +1,7 @@
 // Batched strict decode that allocates nothing.
 //
-// b64_decode_batch needs a device workspace (the per-string tile scan and
-// the per-string error words) that its caller allocates. Some callers cannot
+// b64_decode_batch needs a device workspace (one error word per string) that
+// its caller allocates. Some callers cannot
 // allocate device memory at the point where they decode: a plugin or
 // extension that is handed only its input and output buffers, code that runs
 // while another component owns the whole device-memory budget (a fixed pool,
@@ -13,7 +13,7 @@
 // Limits and rules:
 //   - at most kNoAllocMaxStrings strings per call; larger batches are refused
 //     with an error (use b64_decode_batch with your own workspace);
-//   - every GPU that loads the library keeps this array (about 1 MiB) until
+//   - every GPU that loads the library keeps this array (512 KiB) until
 //     the process exits;
 //   - all calls share the one array, so calls whose work overlaps on the GPU
 //     (different streams, or different host threads) race and corrupt each
@@ -30,11 +30,9 @@ namespace b64 {
 namespace {
 
 constexpr int64_t kNoAllocMaxStrings = 65536;
-// Same layout as batch_workspace_bytes(kNoAllocMaxStrings): the tile scan
-// (n+1 int64, rounded up to 256 bytes), then one error word per string.
-constexpr size_t kNoAllocBytes =
-    (((size_t(kNoAllocMaxStrings) + 1) * sizeof(int64_t) + 255) & ~size_t(255)) +
-    size_t(kNoAllocMaxStrings) * sizeof(uint64_t);
+// Same layout as batch_workspace_bytes(kNoAllocMaxStrings): one error word
+// per string (512 KiB).
+constexpr size_t kNoAllocBytes = size_t(kNoAllocMaxStrings) * sizeof(uint64_t);
 
 // The shared workspace. In host code this name only stands for the device
 // array; its device address comes from cudaGetSymbolAddress below.
@@ -94,8 +92,8 @@ extern "C" int b64_decode_batch_noalloc(const uint8_t* src, const int64_t* src_o
     cudaError_t e = workspace_address(&ws);
     if (e != cudaSuccess)
         return set_error(B64_ERR_CUDA, "%s: workspace address: %s", fn, cudaGetErrorString(e));
-    // The prep kernel writes every workspace word this call reads (the tile
-    // scan and the n error words), so nothing left by an earlier call leaks in.
+    // The call sets all n error words before the tile kernel reads them, so
+    // nothing left by an earlier call leaks in.
     BatchArgs a{src, src_off, n, dst, dst_off, alph_id, results};
     e = launch_batch(true, a, tabs, tile_units, ws, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return set_error(B64_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));

@@ -157,6 +157,35 @@ def test_batch_single_and_empty(b64, orc, tables):
                      torch.zeros(1, dtype=torch.uint8, device="cuda"), z, tables[0])
 
 
+def test_batch_tiny_strings_and_offset_origin(b64, orc, tables):
+    """20,000 strings of 0..9 bytes (far fewer bytes than the grid has warps,
+    so most warps' byte ranges are empty or end inside a string's first
+    group), with src_off starting past 0 (bytes before the first string are
+    not part of the batch); then the same for decode, where strings of 0..13
+    characters are mostly tail (handled by the finalize kernel)."""
+    g = wl.rng(50)
+    lengths = g.integers(0, 10, 20_000).astype(np.int64)
+    origin = 37
+    off = wl.offsets_from_lengths(lengths) + origin
+    data = wl.random_bytes(int(off[-1]), 51)
+    aid = wl.bernoulli(lengths.size, 52).astype(np.uint8)
+    padded = (aid == 0).astype(np.int32)
+    want, eoff, wres = oracle_encode(orc, tables, data, off, aid, padded)
+    for units in (1, 8):
+        got, goff, gres = gpu_encode(b64, tables, data, off, aid, units)
+        assert np.array_equal(gres, wres)
+        assert np.array_equal(goff - goff[0], eoff - eoff[0])
+        assert np.array_equal(got, want)
+    text = np.concatenate([wl.random_bytes(origin, 53), want])
+    toff = eoff + origin
+    for units in (2, 4):
+        dec, doff, dres = gpu_decode(b64, tables, text, toff, aid, units)
+        want_dec, want_res = orc.decode_batch(text, toff, doff, tables[1], aid.astype(np.int32),
+                                              padded, int(doff[-1]))
+        assert np.array_equal(want_res, lengths)
+        check_decoded(dec, doff, dres, want_res, want_dec)
+
+
 def test_batch_config3_full_size(b64, orc, tables):
     """100,000 strings, lognormal lengths (median 1 KiB, sigma 1.5, 1 B..1 MiB),
     all three residues mod 3, 50/50 standard-padded / url-unpadded, 1% of the

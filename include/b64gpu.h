@@ -203,6 +203,46 @@ int b64_batch_offsets(const int64_t* src_off, int64_t n, const b64_alphabet* con
                       int n_alphabets, const uint8_t* alph_id, int decode, int64_t* dst_off,
                       void* stream);
 
+/* ---------------------------------------------------------------- host buffers
+ * Encode or strictly decode a buffer that lives in host memory (not in the
+ * paper, which codes buffers already in the processor's memory). The codec
+ * owns n_streams streams and, per stream, one device piece buffer for input
+ * and one for output, allocated once here; a call copies consecutive pieces
+ * of piece_bytes to the device, codes them and copies the results back, the
+ * three steps of different pieces overlapping on the streams. Host buffers
+ * that are page-locked (cudaHostAlloc / cudaHostRegister, torch
+ * pin_memory) give full overlap; pageable ones work, with copies the driver
+ * stages itself. Results are those of b64_encode / b64_decode on the whole
+ * buffer: decode pieces after the first are offset-shifted, inner pieces
+ * treat every '=' as an error and the last piece always holds the last two
+ * characters, so the padding and length rules apply to the whole input
+ * (Sec. 2). A codec serves one call at a time (calls from several threads
+ * take turns) and stays on the device that was current when it was made. */
+typedef struct b64_host_codec b64_host_codec;
+
+/* piece_bytes: input bytes per piece, rounded down to a multiple of 12
+ * (0 picks 48 MiB); n_streams: 1..8 (0 picks 3). Device memory used:
+ * b64_host_codec_device_bytes. Returns NULL on failure (b64_last_error). */
+b64_host_codec* b64_host_codec_create(size_t piece_bytes, int n_streams);
+
+size_t b64_host_codec_device_bytes(const b64_host_codec* c);
+
+/* Host src (len bytes) -> host dst (b64_encoded_length(len, padded) bytes).
+ * Blocks until the output is in dst. Returns the output length, B64_E_INVAL
+ * or B64_E_CUDA. */
+int64_t b64_host_encode(b64_host_codec* c, const uint8_t* src, size_t len, uint8_t* dst,
+                        const b64_alphabet* a);
+
+/* Host src (len characters) -> host dst (b64_decoded_max_length(len) bytes,
+ * contents past an error unspecified). Blocks until done. Returns the decoded
+ * length, -(offset+1) of the first invalid character, B64_E_TIMEOUT,
+ * B64_E_INVAL or B64_E_CUDA. */
+int64_t b64_host_decode(b64_host_codec* c, const uint8_t* src, size_t len, uint8_t* dst,
+                        const b64_alphabet* a);
+
+/* Waits for the codec's streams, then frees it. */
+void b64_host_codec_destroy(b64_host_codec* c);
+
 /* ---------------------------------------------------------------- serving
  * A request engine with continuous batching (not in the paper; it drives the
  * codec above). The server owns a device arena of budget_bytes and a pinned

@@ -52,6 +52,11 @@ SIGNATURES = {
     "b64_server_outstanding": (_I, [_P]),
     "b64_server_batches": (ctypes.c_uint64, [_P]),
     "b64_server_destroy": (None, [_P]),
+    "b64_host_codec_create": (_P, [_SZ, _I]),
+    "b64_host_codec_device_bytes": (_SZ, [_P]),
+    "b64_host_encode": (_I64, [_P, _P, _SZ, _P, _P]),
+    "b64_host_decode": (_I64, [_P, _P, _SZ, _P, _P]),
+    "b64_host_codec_destroy": (None, [_P]),
     "b64_last_error": (ctypes.c_char_p, []),
     "b64_device_fault_flag": (_I, [_I]),
     "b64_version": (_I, []),
@@ -323,3 +328,70 @@ def mime_decode(src: torch.Tensor, alphabet: Alphabet | None = None, dst=None, w
     if r == B64_E_TIMEOUT:
         raise B64Error("a device wait ran out of time (see device_fault_flag)")
     return r, dst[: max(r, 0)]
+
+
+def _host_u8(t, name: str) -> int:
+    """Address of a contiguous uint8 host buffer (CPU tensor or numpy array)."""
+    if isinstance(t, torch.Tensor):
+        if t.device.type != "cpu" or t.dtype != torch.uint8 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous uint8 CPU tensor")
+        return t.data_ptr()
+    import numpy as np
+    if not isinstance(t, np.ndarray) or t.dtype != np.uint8 or not t.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{name} must be a contiguous uint8 array")
+    return t.ctypes.data
+
+
+class HostCodec:
+    """Encode / strict decode of host buffers, pieces of piece_bytes copied in,
+    coded and copied out with the steps of consecutive pieces overlapped on
+    n_streams streams. Page-locked buffers (torch pin_memory) overlap fully."""
+
+    def __init__(self, piece_bytes: int = 0, n_streams: int = 0):
+        self._lib = lib()
+        self.handle = self._lib.b64_host_codec_create(piece_bytes, n_streams)
+        if not self.handle:
+            raise B64Error(last_error())
+
+    def device_bytes(self) -> int:
+        return int(self._lib.b64_host_codec_device_bytes(self.handle))
+
+    def encode(self, src, dst, alphabet: Alphabet | None = None) -> int:
+        a = alphabet or Alphabet.standard()
+        n = src.numel() if isinstance(src, torch.Tensor) else src.size
+        need = encoded_length(n, a.padded)
+        cap = dst.numel() if isinstance(dst, torch.Tensor) else dst.size
+        if cap < need:
+            raise ValueError(f"dst holds {cap} bytes, needs {need}")
+        r = self._lib.b64_host_encode(self.handle, _host_u8(src, "src"), n,
+                                      _host_u8(dst, "dst"), a.handle)
+        if r < 0:
+            raise B64Error(last_error())
+        return int(r)
+
+    def decode(self, src, dst, alphabet: Alphabet | None = None) -> int:
+        """Returns the decoded length or -(offset+1) of the first bad character."""
+        a = alphabet or Alphabet.standard()
+        m = src.numel() if isinstance(src, torch.Tensor) else src.size
+        need = decoded_max_length(m)
+        cap = dst.numel() if isinstance(dst, torch.Tensor) else dst.size
+        if cap < need:
+            raise ValueError(f"dst holds {cap} bytes, needs {need}")
+        r = self._lib.b64_host_decode(self.handle, _host_u8(src, "src"), m,
+                                      _host_u8(dst, "dst"), a.handle)
+        if r in (B64_E_INVAL, B64_E_CUDA):
+            raise B64Error(last_error())
+        if r == B64_E_TIMEOUT:
+            raise B64Error("a device wait ran out of time (see device_fault_flag)")
+        return int(r)
+
+    def close(self):
+        if self.handle:
+            self._lib.b64_host_codec_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -131,9 +131,11 @@ int64_t b64_decode(const uint8_t* src, size_t len, uint8_t* dst, const b64_alpha
  * Sec. 1). The remaining characters are decoded exactly as b64_decode_async
  * decodes them (Sec. 2, Sec. 3.2, and the rules at the top of this file);
  * error offsets are offsets into the original input, and a bad length is
- * reported at offset len. One pass over the input (tiles publish running
- * counts of data characters to their successors), then a one-thread kernel
- * writes *d_result: the decoded length, -(offset+1), or B64_E_TIMEOUT.
+ * reported at offset len. Four kernels on `stream`: a count of the data
+ * characters of every 4 KiB segment, a scan of those counts, the decode of
+ * every segment at its known output offset, and a one-thread kernel that
+ * writes *d_result: the decoded length, -(offset+1), or B64_E_TIMEOUT (a
+ * bounded wait ran out).
  * workspace: device memory of b64_mime_workspace_size(len) bytes, 8-byte
  * aligned, caller-owned, busy until the work completes (one call at a time per
  * workspace). dst needs b64_decoded_max_length(len) bytes. */
@@ -144,8 +146,9 @@ int b64_mime_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b6
                           void* stream);
 
 /* ---------------------------------------------------------------- batches
- * Many independent strings in one launch sequence (prep kernel, one
- * persistent tile kernel, and for decode a per-string finalize kernel), all
+ * Many independent strings in one launch sequence (a per-string results
+ * kernel or error-word memset, one persistent tile kernel, and for decode a
+ * per-string finalize kernel), all
  * on `stream`, so it can be recorded in a CUDA graph. Batching is not in the
  * paper; each string is coded exactly as the single-buffer calls code it.
  *
@@ -297,15 +300,13 @@ const char* b64_last_error(void);
  * clears it if clear != 0. Synchronises the device. Negative on CUDA error. */
 int b64_device_fault_flag(int clear);
 
-/* Self-test of the bounded device waits: runs b64_mime_decode_async on the
- * given input (at least 8193 bytes) with its first tile never claimed, so the
- * other tiles' waits for it run out after wait_limit_ns nanoseconds.
- * *d_result then becomes B64_E_TIMEOUT and b64_device_fault_flag reports the
- * timeout; no wait lasts longer than the limit and the context stays usable.
- * Returns B64_SUCCESS if the work was enqueued. */
-int b64_selftest_wait_timeout(const uint8_t* src, size_t len, uint8_t* dst,
-                              const b64_alphabet* a, int64_t* d_result, void* workspace,
-                              size_t workspace_bytes, uint64_t wait_limit_ns, void* stream);
+/* Self-test of the bounded device waits: runs the wait the kernels use for
+ * their bulk (TMA) copies on a barrier armed for a copy that is never issued,
+ * giving up after wait_limit_ns (1 .. 2e9). *d_result then becomes
+ * B64_E_TIMEOUT and b64_device_fault_flag reports the timeout; the wait lasts
+ * no longer than the limit and the context stays usable. Returns B64_SUCCESS
+ * if the work was enqueued. */
+int b64_selftest_wait_timeout(int64_t* d_result, uint64_t wait_limit_ns, void* stream);
 
 /* Library version: major*10000 + minor*100 + patch. */
 int b64_version(void);

@@ -45,7 +45,7 @@ SIGNATURES = {
     "b64_decode_batch_noalloc": (_I, [_P, _P, _I64, _P, _P, _P, _I, _P, _P, _I, _P]),
     "b64_mime_workspace_size": (_SZ, [_SZ]),
     "b64_mime_decode_async": (_I, [_P, _SZ, _P, _P, _P, _P, _SZ, _P]),
-    "b64_selftest_wait_timeout": (_I, [_P, _SZ, _P, _P, _P, _P, _SZ, ctypes.c_uint64, _P]),
+    "b64_selftest_wait_timeout": (_I, [_P, ctypes.c_uint64, _P]),
     "b64_server_create": (_P, [_SZ, _I, _SZ, _P, _I]),
     "b64_server_submit": (_I, [_P, ctypes.c_uint64, _I, _I, _P, _SZ, _P, _SZ]),
     "b64_server_poll": (_I, [_P, _P, _I]),

@@ -308,7 +308,7 @@ size_t b64_mime_workspace_size(size_t len) { return mime_workspace_bytes(len); }
 
 static int mime_common(const char* fn, const uint8_t* src, size_t len, uint8_t* dst,
                        const b64_alphabet* a, int64_t* d_result, void* workspace,
-                       size_t workspace_bytes, uint64_t skip, uint64_t limit_ns, void* stream) {
+                       size_t workspace_bytes, uint64_t limit_ns, void* stream) {
     if (!a || !d_result || !workspace)
         return set_error(B64_ERR_INVALID_ARGUMENT, "%s: NULL alphabet, d_result or workspace", fn);
     if ((reinterpret_cast<uintptr_t>(d_result) | reinterpret_cast<uintptr_t>(workspace)) & 7u)
@@ -322,7 +322,7 @@ static int mime_common(const char* fn, const uint8_t* src, size_t len, uint8_t* 
     if (overlaps(src, len, dst, b64_decoded_max_length(len)))
         return set_error(B64_ERR_INVALID_ARGUMENT, "%s: src and dst overlap", fn);
     const cudaError_t e = launch_mime_decode(src, len, dst, a->dec, a->padded, d_result, workspace,
-                                             skip, limit_ns, static_cast<cudaStream_t>(stream));
+                                             limit_ns, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return set_error(B64_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     return B64_SUCCESS;
 }
@@ -331,17 +331,21 @@ int b64_mime_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b6
                           int64_t* d_result, void* workspace, size_t workspace_bytes,
                           void* stream) {
     return mime_common("b64_mime_decode_async", src, len, dst, a, d_result, workspace,
-                       workspace_bytes, 0, kWaitLimitNs, stream);
+                       workspace_bytes, kWaitLimitNs, stream);
 }
 
-int b64_selftest_wait_timeout(const uint8_t* src, size_t len, uint8_t* dst,
-                              const b64_alphabet* a, int64_t* d_result, void* workspace,
-                              size_t workspace_bytes, uint64_t wait_limit_ns, void* stream) {
-    if (len <= 8192)
+int b64_selftest_wait_timeout(int64_t* d_result, uint64_t wait_limit_ns, void* stream) {
+    if (!d_result || (reinterpret_cast<uintptr_t>(d_result) & 7u))
         return set_error(B64_ERR_INVALID_ARGUMENT,
-                         "b64_selftest_wait_timeout: needs more than one tile (8192 bytes)");
-    return mime_common("b64_selftest_wait_timeout", src, len, dst, a, d_result, workspace,
-                       workspace_bytes, 1, wait_limit_ns, stream);
+                         "b64_selftest_wait_timeout: d_result NULL or not 8-byte aligned");
+    if (wait_limit_ns == 0 || wait_limit_ns > kWaitLimitNs)
+        return set_error(B64_ERR_INVALID_ARGUMENT,
+                         "b64_selftest_wait_timeout: wait_limit_ns must be 1..%llu",
+                         (unsigned long long)kWaitLimitNs);
+    const cudaError_t e = launch_selftest_wait(d_result, wait_limit_ns, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return set_error(B64_ERR_CUDA, "b64_selftest_wait_timeout: %s", cudaGetErrorString(e));
+    return B64_SUCCESS;
 }
 
 const char* b64_last_error(void) { return t_last_error.c_str(); }

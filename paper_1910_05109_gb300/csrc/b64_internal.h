@@ -83,12 +83,13 @@ cudaError_t launch_batch_offsets(bool decode, const int64_t* src_off, int64_t n,
 
 // ---- MIME decode (b64_mime.cu)
 size_t mime_workspace_bytes(uint64_t m);
-// Enqueues the whitespace-skipping strict decode; skip_tiles > 0 leaves the
-// first tiles unclaimed (self-test of the bounded look-back waits).
+// Enqueues the whitespace-skipping strict decode; its bulk-copy waits give
+// up after wait_limit_ns.
 cudaError_t launch_mime_decode(const uint8_t* src, uint64_t m, uint8_t* dst,
                                const DecodeTable& tab, int padded, int64_t* d_result,
-                               void* workspace, uint64_t skip_tiles, uint64_t wait_limit_ns,
-                               cudaStream_t stream);
+                               void* workspace, uint64_t wait_limit_ns, cudaStream_t stream);
+// Self-test of the bounded wait: a barrier armed for a copy that never comes.
+cudaError_t launch_selftest_wait(int64_t* d_result, uint64_t wait_limit_ns, cudaStream_t stream);
 uint32_t mime_fault_flag(bool clear);
 
 }  // namespace b64

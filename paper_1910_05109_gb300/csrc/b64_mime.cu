@@ -4,25 +4,31 @@
 // original input. The paper cites MIME only as motivation (Sec. 1); the
 // whitespace removal and this single-pass design are this library's.
 //
-// One pass over the input with decoupled look-back:
-//   - CTAs claim tiles of kTile raw bytes in arrival order from an atomic
-//     counter (so every tile's predecessors are already running);
-//   - each thread classifies its 32 bytes; a warp/block scan gives every data
-//     character its index within the tile;
-//   - the tile publishes its aggregate (data characters, last data byte),
-//     walks back over its predecessors' published states until it meets an
-//     inclusive prefix, and publishes its own inclusive prefix; the prefix
-//     tells it the global index of its first data character and the last data
-//     byte before it (so the group of four that straddles the tile start can
-//     be finished here);
-//   - the tile compacts its characters' 6-bit values in shared memory and
-//     writes exactly the output bytes whose second character it holds, up to
-//     its first '=' or bad byte;
-//   - bad bytes and the first '=' are folded into status words with atomic
-//     minima; a one-thread kernel then applies the padding and length rules
-//     on the compacted stream and writes the result.
-// Every wait on a predecessor is bounded; a tile that gives up publishes a
-// "poisoned" state so its successors stop at once, and the result becomes
+// Three kernels, no waits on other blocks:
+//   1. count: every block takes 64 consecutive 4 KiB segments (rows of 32
+//      lanes x 16 bytes; exact word-parallel tests for CR, LF and space),
+//      counts each segment's data characters and last data byte, and writes
+//      for each segment the prefix within its block, and the block's total;
+//   2. scan (one block): block totals become block prefixes (plus the whole
+//      input's count and last data byte), so a segment's global prefix is its
+//      block's prefix plus its own: the index P of its first data character
+//      and the last data byte before it (the group of four that straddles a
+//      segment start is finished by the segment holding its second
+//      character);
+//   3. decode: every warp takes segments, each one's bulk (TMA) copy started
+//      before the previous segment is worked on. Row by row it translates a
+//      lane's 16 bytes through the table (6-bit value, bad = 0x80, whitespace
+//      = 0xC0), counts the data characters from the class bits, scans the
+//      counts over the warp and stores the values at their index with
+//      predicated byte stores, in place (an index never exceeds its raw
+//      position); it then decodes whole groups in place and writes exactly
+//      the output bytes whose second character it holds, up to its first '='
+//      or bad byte. Bad bytes and the first '=' are folded into status words
+//      by atomic minima.
+//   4. finalize (one thread): the padding and length rules on the compacted
+//      stream, and the result.
+// The only waits are on the decode kernel's own bulk copies, each bounded in
+// time; one that runs out sets the timeout word, and the result becomes
 // B64_E_TIMEOUT.
 #include <mutex>
 
@@ -31,354 +37,448 @@
 namespace b64 {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kChunks = 4;                              // rounds of 32 bytes per thread
-constexpr uint32_t kChunk = kThreads * 32;              // 8 KiB
-constexpr uint32_t kTile = kChunk * kChunks;            // raw bytes per tile (32 KiB)
+constexpr int kWarps = 4;                               // warps per CTA, decode kernel
+constexpr int kThreads = 32 * kWarps;
+constexpr int kCountThreads = 256;                     // 8 warps
+constexpr int kSegsPerBlock = 64;                       // segments per count block
+constexpr int kScanThreads = 1024;
+constexpr int kRows = 8;                                // rows of 32 lanes x 16 bytes
+constexpr uint32_t kRow = 512;
+constexpr uint32_t kSeg = kRow * kRows;                 // raw bytes per segment (4 KiB)
+constexpr uint32_t kLead = 16;                          // buffer bytes before the segment
+constexpr uint32_t kBuf = kLead + kSeg + 48;            // + room for shifted 16-byte reads
 constexpr uint32_t kSpace = 0xC0u;                      // table class of CR, LF, space
 
-// Tile state word: [flag:2][last data byte:8][data characters:54].
-constexpr int kFlagShift = 62;
+// Segment state word: [flag:2][last data byte:8][data characters:54]. After
+// the count kernel: flag 1 if the segment holds a data character, its last
+// one, and its count. After the scan: the same fields for everything before
+// the segment.
 constexpr uint64_t kCountMask = (uint64_t(1) << 54) - 1;
-constexpr uint64_t kFlagAggregate = 1, kFlagPrefix = 2, kFlagPoison = 3;
 
 __device__ uint32_t g_fault;
 
 __host__ __device__ __forceinline__ uint64_t make_state(uint64_t flag, uint32_t last,
                                                         uint64_t count) {
-    return (flag << kFlagShift) | (uint64_t(last & 0xFFu) << 54) | (count & kCountMask);
+    return (flag << 62) | (uint64_t(last & 0xFFu) << 54) | (count & kCountMask);
 }
-__host__ __device__ __forceinline__ uint64_t st_flag(uint64_t s) { return s >> kFlagShift; }
+__host__ __device__ __forceinline__ uint64_t st_flag(uint64_t s) { return s >> 62; }
 __host__ __device__ __forceinline__ uint32_t st_last(uint64_t s) {
     return uint32_t(s >> 54) & 0xFFu;
 }
 __host__ __device__ __forceinline__ uint64_t st_count(uint64_t s) { return s & kCountMask; }
 
-__device__ __forceinline__ uint64_t ld_relaxed(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed(unsigned long long* p, uint64_t v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"((unsigned long long)v)
-                 : "memory");
-}
-
 // Four already-translated 6-bit values (one per byte, first in the low byte)
 // -> their 24-bit value a<<18 | b<<12 | c<<6 | d. Each byte is masked to six
 // bits first, so that a byte holding anything larger (a value past the end of
-// the valid data: stale shared memory) cannot carry into the output bytes of
-// the other values.
+// the valid data: a raw byte or an earlier segment's value) cannot carry
+// into the output bytes of the other values.
 __device__ __forceinline__ uint32_t decode4_values(uint32_t w) {
     w &= 0x3F3F3F3Fu;
     const uint32_t a = w & 0xFFu, b = (w >> 8) & 0xFFu, c = (w >> 16) & 0xFFu, d = w >> 24;
     return ((a * 64u + b) * 64u + c) * 64u + d;
 }
 
+// Output bytes of the first j data characters.
 __host__ __device__ __forceinline__ uint64_t bytes_for(uint64_t j) {
     const uint64_t r = j & 3;
     return 3 * (j >> 2) + (r ? r - 1 : 0);
 }
 
-// Dynamic shared memory: raw[kTile] (the tile; later the output bytes) then
-// vals[kTile + 32] (compacted values at (P & 3) + index).
-constexpr size_t kDynSmem = 2 * size_t(kTile) + 32;
-
-struct TileShared {
-    uint8_t lut[256];                       // 0..63, 0x80 (bad or '='), kSpace
-    unsigned long long warp_tot[kThreads / 32];
-    unsigned long long tile;
-    unsigned long long excl;
-    uint32_t prev_last;
-    uint32_t poisoned;
-    uint32_t last_key;                      // (raw position + 1) << 8 | byte of the last data byte
-    uint32_t min_bad_raw, min_eq_raw, min_eq_comp, min_stop_comp;
-};
-
-// The tile's predecessors' published states, 32 at a time (warp 0): the data
-// characters before the tile and the last data byte before it. Returns false
-// if a wait ran out or a predecessor was poisoned.
-__device__ bool look_back(const unsigned long long* __restrict__ states, uint64_t tile,
-                          const unsigned long long* timeout, uint64_t wait_limit_ns,
-                          uint64_t* excl_out, uint32_t* prev_last_out, bool* have_prev_out) {
-    const int lane = threadIdx.x & 31;
-    uint64_t excl = 0;
-    uint32_t prev_last = 0;
-    bool have_prev = false;
-    int64_t wend = int64_t(tile);
-    const uint64_t t0 = global_timer_ns();
-    for (;;) {
-        const int64_t t = wend - 1 - lane;
-        uint64_t s = t >= 0 ? ld_relaxed(states + t) : make_state(kFlagPrefix, 0, 0);
-        uint32_t spins = 0;
-        for (;;) {
-            const bool ready = st_flag(s) != 0;
-            if (__all_sync(0xffffffffu, ready)) break;
-            if (!ready) s = ld_relaxed(states + t);
-            if ((++spins & 31) == 0) {
-                const bool give_up =
-                    global_timer_ns() - t0 > wait_limit_ns || ld_relaxed(timeout) != 0;
-                if (__any_sync(0xffffffffu, give_up)) return false;
-            }
-        }
-        if (__any_sync(0xffffffffu, st_flag(s) == kFlagPoison)) return false;
-        const uint32_t pmask = __ballot_sync(0xffffffffu, st_flag(s) == kFlagPrefix);
-        const int pl = pmask ? __ffs(pmask) - 1 : 31;  // nearest inclusive prefix
-        const bool mine = lane <= pl;
-        uint64_t c = mine ? st_count(s) : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        excl += c;
-        if (!have_prev) {
-            const uint32_t lmask = __ballot_sync(0xffffffffu, mine && st_count(s) > 0);
-            if (lmask) {
-                prev_last = __shfl_sync(0xffffffffu, st_last(s), __ffs(lmask) - 1);
-                have_prev = true;
-            }
-        }
-        if (pmask) break;
-        wend -= 32;
-    }
-    *excl_out = excl;
-    *prev_last_out = prev_last;
-    *have_prev_out = have_prev;
-    return true;
+// Bit 7 of each byte of x that equals the byte c (exact: no carries between bytes).
+__device__ __forceinline__ uint32_t eq_bytes(uint32_t x, uint32_t c) {
+    const uint32_t t = x ^ (c * 0x01010101u);
+    return ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t) & 0x80808080u;
+}
+__device__ __forceinline__ uint32_t space_bytes(uint32_t x) {
+    return eq_bytes(x, '\r') | eq_bytes(x, '\n') | eq_bytes(x, ' ');
 }
 
-__global__ void __launch_bounds__(kThreads, 2)
+__device__ __forceinline__ uint32_t byte_of(uint4 w, int k) {
+    const uint32_t x = k < 4 ? w.x : k < 8 ? w.y : k < 12 ? w.z : w.w;
+    return __byte_perm(x, 0, 0x4440u + (k & 3));
+}
+
+// Data characters of a 16-byte chunk (exact: every byte but CR, LF, space)
+// and, if any, the position + 1 (within the segment; off = the chunk's
+// position) and value of the last one, as (pos + 1) << 8 | byte in *key.
+__device__ __forceinline__ uint32_t chunk_count(uint4 w, uint32_t off, uint32_t* key) {
+    const uint32_t d0 = ~space_bytes(w.x) & 0x80808080u, d1 = ~space_bytes(w.y) & 0x80808080u;
+    const uint32_t d2 = ~space_bytes(w.z) & 0x80808080u, d3 = ~space_bytes(w.w) & 0x80808080u;
+    const uint32_t c = __popc(d0) + __popc(d1) + __popc(d2) + __popc(d3);
+    // highest data byte: the top set bit of the four masks laid end to end
+    const uint32_t hi = d3 ? 12 + (31 - __clz(d3)) / 8
+                      : d2 ? 8 + (31 - __clz(d2)) / 8
+                      : d1 ? 4 + (31 - __clz(d1)) / 8
+                      : d0 ? (31 - __clz(d0)) / 8 : 0xFFu;
+    if (hi != 0xFFu) *key = ((off + hi + 1) << 8) | byte_of(w, int(hi));
+    return c;
+}
+
+// Segment bytes [0, len) in registers, row r of this lane in v[r]; bytes past
+// len read as spaces.
+__device__ __forceinline__ void load_rows(const uint8_t* seg_src, uint32_t len, bool aligned,
+                                          int lane, uint4 (&v)[kRows]) {
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const uint32_t off = kRow * r + 16 * lane;
+        if (aligned && off + 16 <= len) {
+            v[r] = *reinterpret_cast<const uint4*>(seg_src + off);
+        } else {
+            uint8_t* b = reinterpret_cast<uint8_t*>(&v[r]);
+            for (int k = 0; k < 16; ++k) b[k] = off + k < len ? seg_src[off + k] : uint8_t(' ');
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t warp_scan_add32(uint32_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+__device__ __forceinline__ uint32_t warp_scan_max32(uint32_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o && u > v) v = u;
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------- 1. count
+// Block b: segments [64 b, 64 b + 64). states[s] = (data characters and last
+// data byte of the segments before s in its block); totals[b] = the block's.
+__global__ void __launch_bounds__(kCountThreads, 4)
+    mime_count_kernel(const uint8_t* __restrict__ src, uint64_t m,
+                      unsigned long long* __restrict__ states,
+                      unsigned long long* __restrict__ totals, uint64_t nseg) {
+    __shared__ uint32_t s_cnt[kSegsPerBlock], s_key[kSegsPerBlock];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool aligned = (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
+    const uint64_t first = uint64_t(blockIdx.x) * kSegsPerBlock;
+    for (int j = warp; j < kSegsPerBlock; j += kCountThreads / 32) {
+        const uint64_t seg = first + j;
+        uint32_t count = 0, key = 0;
+        if (seg < nseg) {
+            const uint64_t base = seg * kSeg;
+            const uint32_t len = uint32_t(m - base < kSeg ? m - base : kSeg);
+            uint4 v[kRows];
+            load_rows(src + base, len, aligned, lane, v);
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) count += chunk_count(v[r], kRow * r + 16 * lane, &key);
+            count = __reduce_add_sync(0xffffffffu, count);
+            key = __reduce_max_sync(0xffffffffu, key);
+        }
+        if (lane == 0) {
+            s_cnt[j] = count;
+            s_key[j] = key ? (uint32_t(j + 1) << 8) | (key & 0xFFu) : 0u;  // block-local order
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {  // two segments per lane
+        const uint32_t c0 = s_cnt[2 * lane], c1 = s_cnt[2 * lane + 1];
+        const uint32_t k0 = s_key[2 * lane], k1 = s_key[2 * lane + 1];
+        const uint32_t incl = warp_scan_add32(c0 + c1, lane);
+        const uint32_t kincl = warp_scan_max32(k0 > k1 ? k0 : k1, lane);
+        uint32_t kex = __shfl_up_sync(0xffffffffu, kincl, 1);
+        if (lane == 0) kex = 0;
+        const uint32_t ex = incl - c0 - c1;
+        const uint64_t s0 = first + 2 * lane;
+        if (s0 < nseg) states[s0] = make_state(kex != 0, kex & 0xFFu, ex);
+        const uint32_t kmid = k0 > kex ? k0 : kex;
+        if (s0 + 1 < nseg) states[s0 + 1] = make_state(kmid != 0, kmid & 0xFFu, ex + c0);
+        if (lane == 31) totals[blockIdx.x] = make_state(kincl != 0, kincl & 0xFFu, incl);
+    }
+}
+
+// ---------------------------------------------------------------- 2. scan
+// One block: totals[b] = (data characters before block b, last data byte
+// before it); status[5] = the whole input's (count, last data byte).
+constexpr int kScanItems = 8;
+
+__global__ void __launch_bounds__(kScanThreads)
+    mime_scan_kernel(unsigned long long* __restrict__ totals, uint64_t nblk,
+                     unsigned long long* __restrict__ status) {
+    __shared__ uint64_t warp_sum[kScanThreads / 32];
+    __shared__ uint64_t warp_key[kScanThreads / 32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint64_t carry = 0, carry_key = 0;  // key: (block + 1) << 8 | last byte, 0 = none
+    for (uint64_t base = 0; base < nblk; base += uint64_t(kScanThreads) * kScanItems) {
+        const uint64_t i0 = base + uint64_t(tid) * kScanItems;
+        uint64_t cnt[kScanItems], keys[kScanItems];
+        uint64_t sum = 0, kmax = 0;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            const uint64_t i = i0 + j;
+            const uint64_t st = i < nblk ? totals[i] : 0;
+            cnt[j] = st_count(st);
+            keys[j] = st_flag(st) ? ((i + 1) << 8) | st_last(st) : 0;
+            sum += cnt[j];
+            kmax = keys[j] > kmax ? keys[j] : kmax;
+        }
+        uint64_t incl = sum, ikey = kmax;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            const uint64_t uk = __shfl_up_sync(0xffffffffu, ikey, o);
+            if (lane >= o) {
+                incl += u;
+                ikey = uk > ikey ? uk : ikey;
+            }
+        }
+        if (lane == 31) {
+            warp_sum[warp] = incl;
+            warp_key[warp] = ikey;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            uint64_t x = warp_sum[lane], xk = warp_key[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t u = __shfl_up_sync(0xffffffffu, x, o);
+                const uint64_t uk = __shfl_up_sync(0xffffffffu, xk, o);
+                if (lane >= o) {
+                    x += u;
+                    xk = uk > xk ? uk : xk;
+                }
+            }
+            warp_sum[lane] = x;
+            warp_key[lane] = xk;
+        }
+        __syncthreads();
+        uint64_t run = carry + (warp ? warp_sum[warp - 1] : 0) + incl - sum;
+        // keys before this thread's items: carried, earlier warps, earlier lanes
+        uint64_t rkey = carry_key;
+        if (warp && warp_key[warp - 1] > rkey) rkey = warp_key[warp - 1];
+        const uint64_t lane_prev = __shfl_up_sync(0xffffffffu, ikey, 1);
+        if (lane && lane_prev > rkey) rkey = lane_prev;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) {
+            if (i0 + j < nblk) totals[i0 + j] = make_state(rkey != 0, uint32_t(rkey & 0xFFu), run);
+            run += cnt[j];
+            rkey = keys[j] > rkey ? keys[j] : rkey;
+        }
+        carry += warp_sum[kScanThreads / 32 - 1];
+        if (warp_key[kScanThreads / 32 - 1] > carry_key) carry_key = warp_key[kScanThreads / 32 - 1];
+        __syncthreads();  // warp_sum / warp_key are rewritten by the next chunk
+    }
+    if (tid == 0) status[5] = make_state(carry_key != 0, uint32_t(carry_key & 0xFFu), carry);
+}
+
+// ---------------------------------------------------------------- 3. decode
+// Bounded wait on a bulk copy's barrier: false after limit_ns.
+__device__ __forceinline__ bool wait_copy(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        for (int i = 0; i < 16; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 6)
     mime_decode_kernel(const uint8_t* __restrict__ src, uint64_t m, uint8_t* __restrict__ dst,
                        const __grid_constant__ DecodeTable tab, int padded,
                        unsigned long long* __restrict__ status,
-                       unsigned long long* __restrict__ states, uint64_t ntiles,
-                       uint64_t skip_tiles, uint64_t wait_limit_ns) {
-    __shared__ TileShared sh;
-    extern __shared__ __align__(16) uint8_t dyn[];
-    uint8_t* raw = dyn;
-    uint8_t* vals = dyn + kTile;
+                       const unsigned long long* __restrict__ states,
+                       const unsigned long long* __restrict__ totals, uint64_t nseg,
+                       uint64_t wait_limit_ns) {
+    __shared__ uint8_t lut[256];  // 0..63, 0x80 (bad or '='), kSpace
+    __shared__ __align__(16) uint8_t bufs[kWarps][2][kBuf];
+    __shared__ uint64_t bars[kWarps][2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < 64) reinterpret_cast<uint32_t*>(sh.lut)[tid] = tab.w[tid];
+    for (int i = tid; i < 64; i += kThreads) reinterpret_cast<uint32_t*>(lut)[i] = tab.w[i];
     __syncthreads();
-    if (tid == 0) sh.lut['\r'] = sh.lut['\n'] = sh.lut[' '] = uint8_t(kSpace);
+    if (tid == 0) lut['\r'] = lut['\n'] = lut[' '] = uint8_t(kSpace);
+    if (lane == 0) {
+        mbar_init(&bars[warp][0], 1);
+        mbar_init(&bars[warp][1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();  // the only block-wide barrier: tables and barriers ready
     const bool aligned = (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
-    unsigned long long* counter = status + 3;
     unsigned long long* timeout = status + 4;
+    const uint64_t GW = uint64_t(gridDim.x) * kWarps;
 
-    for (;;) {
-        __syncthreads();  // every thread is done with the previous tile's shared state
-        if (tid == 0) {
-            sh.tile = atomicAdd(counter, 1ull) + skip_tiles;
-            sh.min_bad_raw = sh.min_eq_raw = sh.min_eq_comp = sh.min_stop_comp = 0xFFFFFFFFu;
-            sh.last_key = 0;
-            sh.poisoned = 0;
+    // Starts the bulk copy of a whole, aligned segment into buffer k; false if
+    // the segment is staged with plain loads instead.
+    auto issue = [&](uint64_t seg, int k) -> bool {
+        const uint64_t base = seg * kSeg;
+        if (!aligned || m - base < kSeg) return false;
+        if (lane == 0) {
+            mbar_arrive_expect_tx(&bars[warp][k], kSeg);
+            bulk_load(bufs[warp][k] + kLead, src + base, kSeg, &bars[warp][k]);
         }
-        __syncthreads();
-        const uint64_t tile = sh.tile;
-        if (tile >= ntiles) break;
-        const uint64_t base = tile * kTile;
-        const uint32_t len = uint32_t(m - base < kTile ? m - base : kTile);
+        return true;
+    };
 
-        // ---- stage the tile (coalesced 16-byte loads; bytes past the end read as spaces)
-#pragma unroll 1
-        for (int half = 0; half < 2; ++half) {
-            constexpr int kLoads = int(kTile / 16 / kThreads) / 2;
-            uint4 v[kLoads];
-#pragma unroll
-            for (int i = 0; i < kLoads; ++i) {
-                const uint32_t off = 16 * (tid + kThreads * (i + kLoads * half));
-                if (aligned && off + 16 <= len) {
-                    v[i] = *reinterpret_cast<const uint4*>(src + base + off);
-                } else {
-                    uint8_t* b = reinterpret_cast<uint8_t*>(&v[i]);
-                    for (int k = 0; k < 16; ++k) b[k] = off + k < len ? src[base + off + k] : 32;
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < kLoads; ++i)
-                *reinterpret_cast<uint4*>(raw + 16 * (tid + kThreads * (i + kLoads * half))) =
-                    v[i];
-        }
-        __syncthreads();
-
-        // ---- count data characters per 32-byte piece; 4 pieces per thread,
-        //      piece c covers raw bytes [c*kChunk + 32*tid, +32)
-        uint64_t cnt = 0;  // four 16-bit counts, piece c in bits 16c..16c+15
-        uint32_t my_last = 0;
-#pragma unroll 1
-        for (int c = 0; c < kChunks; ++c) {
-            const uint32_t p0 = c * kChunk + 32 * tid;
-            const uint4 x = *reinterpret_cast<const uint4*>(raw + p0);
-            const uint4 y = *reinterpret_cast<const uint4*>(raw + p0 + 16);
-            const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
-            uint32_t k = 0;
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const uint32_t ch = __byte_perm(w[q], 0, 0x4440u + i);
-                    if (sh.lut[ch] != kSpace) {
-                        ++k;
-                        my_last = ((p0 + 4 * q + i + 1) << 8) | ch;  // never 0
-                    }
-                }
-            cnt |= uint64_t(k) << (16 * c);
-        }
-        if (my_last) atomicMax(&sh.last_key, my_last);
-        uint64_t incl = cnt;  // scan of the four counts at once (fields never overflow)
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint64_t v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        if (lane == 31) sh.warp_tot[warp] = incl;
-        __syncthreads();
-        uint64_t before = 0, total = 0;
-#pragma unroll
-        for (int q = 0; q < kThreads / 32; ++q) {
-            if (q < warp) before += sh.warp_tot[q];
-            total += sh.warp_tot[q];
-        }
-        const uint64_t excl_fields = before + incl - cnt;
-        // piece c of this thread starts at data index
-        //   (totals of pieces < c) + (this thread's exclusive count in piece c)
-        uint32_t tile_count = 0;
-#pragma unroll
-        for (int c = 0; c < kChunks; ++c) tile_count += uint32_t((total >> (16 * c)) & 0xFFFFu);
-        const uint32_t tile_last = sh.last_key & 0xFFu;
-        const bool tile_has_last = sh.last_key != 0;
-
-        // ---- publish the aggregate, look back, publish the inclusive prefix
-        if (warp == 0) {
-            unsigned long long* my = states + tile;
-            uint64_t excl = 0;
-            uint32_t prev_last = 0;
-            bool have_prev = false, ok = true;
-            if (tile == 0) {
-                if (lane == 0) st_relaxed(my, make_state(kFlagPrefix, tile_last, tile_count));
-            } else {
-                if (lane == 0) st_relaxed(my, make_state(kFlagAggregate, tile_last, tile_count));
-                ok = look_back(states, tile, timeout, wait_limit_ns, &excl, &prev_last,
-                               &have_prev);
+    uint32_t phases = 0;
+    uint64_t seg = uint64_t(blockIdx.x) * kWarps + warp;
+    int k = 0;
+    bool by_copy = seg < nseg ? issue(seg, 0) : false;
+    for (; seg < nseg; seg += GW, k ^= 1) {
+        const uint64_t next = seg + GW;
+        fence_proxy_async_smem();  // this lane's accesses to buffer k^1 before the copy below
+        __syncwarp();
+        const bool next_by_copy = next < nseg ? issue(next, k ^ 1) : false;
+        uint8_t* buf = bufs[warp][k];
+        const uint64_t base = seg * kSeg;
+        const uint32_t len = uint32_t(m - base < kSeg ? m - base : kSeg);
+        if (by_copy) {
+            const bool ok =
+                __all_sync(0xffffffffu, wait_copy(&bars[warp][k], (phases >> k) & 1u, wait_limit_ns));
+            phases ^= 1u << k;
+            if (!ok) {
+                if (next_by_copy)  // let the copy in flight land before the block can exit
+                    wait_copy(&bars[warp][k ^ 1], (phases >> (k ^ 1)) & 1u, wait_limit_ns);
                 if (lane == 0) {
-                    if (ok) {
-                        st_relaxed(my, make_state(kFlagPrefix,
-                                                  tile_has_last ? tile_last : prev_last,
-                                                  excl + tile_count));
-                    } else {
-                        st_relaxed(my, make_state(kFlagPoison, 0, 0));
-                        atomicExch(timeout, 1ull);
-                        atomicOr(&g_fault, 1u);
-                    }
+                    atomicExch(timeout, 1ull);
+                    atomicOr(&g_fault, 1u);
                 }
+                return;
             }
-            if (lane == 0) {
-                sh.excl = excl;
-                sh.prev_last = have_prev ? prev_last : 0u;
-                sh.poisoned = ok ? 0u : 1u;
-            }
+        } else {
+            uint4 v[kRows];
+            load_rows(src + base, len, aligned, lane, v);
+#pragma unroll
+            for (int r = 0; r < kRows; ++r)
+                *reinterpret_cast<uint4*>(buf + kLead + kRow * r + 16 * lane) = v[r];
+            __syncwarp();
         }
-        __syncthreads();
-        if (sh.poisoned) continue;  // uniform: the whole block skips this tile
-        const uint64_t P = sh.excl;
-        const uint32_t shift = uint32_t(P & 3);
+        const uint64_t pre = states[seg], blk = totals[seg / kSegsPerBlock];
+        const uint64_t P = st_count(blk) + st_count(pre);
+        const uint32_t prev_last = st_flag(pre) ? st_last(pre) : st_flag(blk) ? st_last(blk) : 0u;
 
-        // ---- compact the 6-bit values to vals[shift + index]; note errors
-        if (tid == 0 && shift) vals[shift - 1] = sh.lut[sh.prev_last];
+        // ---- row by row: translate, count, scan, store the values at their
+        //      index (buf[kLead + index]); note the first bad byte and '='
         uint32_t bad_raw = 0xFFFFFFFFu, eq_raw = 0xFFFFFFFFu, eq_comp = 0xFFFFFFFFu,
                  stop = 0xFFFFFFFFu;
+        uint32_t rowbase = 0;
 #pragma unroll 1
-        for (int c = 0; c < kChunks; ++c) {
-            const uint32_t p0 = c * kChunk + 32 * tid;
-            uint32_t pos = uint32_t((excl_fields >> (16 * c)) & 0xFFFFu);
-            for (int c2 = 0; c2 < c; ++c2) pos += uint32_t((total >> (16 * c2)) & 0xFFFFu);
-            const uint4 x = *reinterpret_cast<const uint4*>(raw + p0);
-            const uint4 y = *reinterpret_cast<const uint4*>(raw + p0 + 16);
-            const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+        for (int r = 0; r < kRows; ++r) {
+            const uint32_t off = kRow * r + 16 * lane;
+            const uint4 w = *reinterpret_cast<const uint4*>(buf + kLead + off);
+            const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+            uint32_t T[4], dm[4], badm = 0;
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t t0 = lut[x[q] & 0xFFu], t1 = lut[(x[q] >> 8) & 0xFFu];
+                const uint32_t t2 = lut[(x[q] >> 16) & 0xFFu], t3 = lut[x[q] >> 24];
+                T[q] = t0 | (t1 << 8) | (t2 << 16) | (t3 << 24);
+                const uint32_t b7 = T[q] & 0x80808080u, b6 = (T[q] << 1) & 0x80808080u;
+                dm[q] = ~(b7 & b6) & 0x80808080u;  // not whitespace (0xC0)
+                badm |= b7 & ~b6;                  // bad or '=' (0x80)
+            }
+            const uint32_t c = __popc(dm[0]) + __popc(dm[1]) + __popc(dm[2]) + __popc(dm[3]);
+            const uint32_t incl = warp_scan_add32(c, lane);
+            const uint32_t pos = rowbase + incl - c;
+            rowbase += __shfl_sync(0xffffffffu, incl, 31);
+            __syncwarp();  // the row is read everywhere before any lane writes into it
+            uint8_t* out = buf + kLead + pos;
+            uint32_t q = 0;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const uint32_t ch = __byte_perm(w[q], 0, 0x4440u + i);
-                    const uint32_t v = sh.lut[ch];
-                    if (v != kSpace) {
-                        vals[shift + pos] = uint8_t(v);
-                        if (v & kBad) {
-                            if (stop == 0xFFFFFFFFu) stop = pos;
-                            const uint32_t raw = p0 + 4 * q + i;
-                            if (ch == '=' && padded) {
-                                if (eq_raw == 0xFFFFFFFFu) {
-                                    eq_raw = raw;
-                                    eq_comp = pos;
-                                }
-                            } else if (bad_raw == 0xFFFFFFFFu) {
-                                bad_raw = raw;
+            for (int i = 0; i < 16; ++i) {
+                const uint32_t d = (dm[i >> 2] >> (8 * (i & 3) + 7)) & 1u;
+                if (d) out[q] = uint8_t(T[i >> 2] >> (8 * (i & 3)));
+                q += d;
+            }
+            if (badm) {  // rare: locate the chunk's first bad byte and first '='
+                uint32_t qq = 0;
+                for (int i = 0; i < 16; ++i) {
+                    const uint32_t v = (T[i >> 2] >> (8 * (i & 3))) & 0xFFu;
+                    if (v == kSpace) continue;
+                    if (v & kBad) {
+                        const uint32_t ch = byte_of(w, i);
+                        if (stop == 0xFFFFFFFFu) stop = pos + qq;
+                        if (ch == '=' && padded) {
+                            if (eq_raw == 0xFFFFFFFFu) {
+                                eq_raw = off + i;
+                                eq_comp = pos + qq;
                             }
+                        } else if (bad_raw == 0xFFFFFFFFu) {
+                            bad_raw = off + i;
                         }
-                        ++pos;
                     }
+                    ++qq;
                 }
-        }
-        if (stop != 0xFFFFFFFFu) {
-            atomicMin(&sh.min_stop_comp, stop);
-            if (bad_raw != 0xFFFFFFFFu) atomicMin(&sh.min_bad_raw, bad_raw);
-            if (eq_raw != 0xFFFFFFFFu) {
-                atomicMin(&sh.min_eq_raw, eq_raw);
-                atomicMin(&sh.min_eq_comp, eq_comp);
             }
         }
-        __syncthreads();
-        if (tid == 0) {
-            if (sh.min_bad_raw != 0xFFFFFFFFu) atomicMin(status + 0, base + sh.min_bad_raw);
-            if (sh.min_eq_raw != 0xFFFFFFFFu) {
-                atomicMin(status + 1, base + sh.min_eq_raw);
-                atomicMin(status + 2, P + sh.min_eq_comp);
+        const uint32_t count = rowbase;
+        stop = __reduce_min_sync(0xffffffffu, stop);
+        if (stop != 0xFFFFFFFFu) {
+            bad_raw = __reduce_min_sync(0xffffffffu, bad_raw);
+            eq_raw = __reduce_min_sync(0xffffffffu, eq_raw);
+            eq_comp = __reduce_min_sync(0xffffffffu, eq_comp);
+            if (lane == 0) {
+                if (bad_raw != 0xFFFFFFFFu) atomicMin(status + 0, base + bad_raw);
+                if (eq_raw != 0xFFFFFFFFu) {
+                    atomicMin(status + 1, base + eq_raw);
+                    atomicMin(status + 2, P + eq_comp);
+                }
             }
         }
 
-        // ---- whole quads, four per thread: 16 values -> 12 bytes into the raw
-        //      buffer (free now); quad Q's values sit at vals[4 * (Q - P/4)]
-        const uint32_t jend = sh.min_stop_comp < tile_count ? sh.min_stop_comp : tile_count;
+        // ---- whole groups in place: 16 values -> 12 bytes; the value of data
+        //      character P + i sits at buf[kLead + i], the one before P at
+        //      buf[kLead - 1], so the group holding P starts at buf[kLead - s]
+        const uint32_t s = uint32_t(P & 3);
+        if (lane == 0 && s) buf[kLead - 1] = lut[prev_last];
+        __syncwarp();
+        const uint32_t jend = stop < count ? stop : count;
         const uint64_t ob = bytes_for(P), oe = bytes_for(P + jend);
         const uint32_t nout = uint32_t(oe > ob ? oe - ob : 0);
-        const uint32_t skip = shift ? shift - 1 : 0;    // bytes of the first quad not ours
-        const uint32_t ngroups = (shift + jend + 15) / 16;
-        uint8_t* out = raw;
-        for (uint32_t g = tid; g < ngroups; g += kThreads) {
-            const uint4 c = *reinterpret_cast<const uint4*>(vals + 16 * g);
-            const uint3 o = pack4x24(decode4_values(c.x), decode4_values(c.y),
-                                     decode4_values(c.z), decode4_values(c.w));
-            uint32_t* ow = reinterpret_cast<uint32_t*>(out + 12 * g);
-            ow[0] = o.x;
-            ow[1] = o.y;
-            ow[2] = o.z;
+        const uint32_t skip = s ? s - 1 : 0;  // bytes of the first group written before P
+        const uint32_t ngroups = (s + jend + 15) / 16;
+        const uint32_t first = kLead - s, sh = first & 3;
+#pragma unroll 1
+        for (uint32_t g0 = 0; g0 < ngroups; g0 += 32) {
+            const uint32_t g = g0 + lane;
+            uint3 o = make_uint3(0, 0, 0);
+            if (g < ngroups) {
+                const uint4 c = load16_shifted(buf, first + 16 * g, sh);
+                o = pack4x24(decode4_values(c.x), decode4_values(c.y), decode4_values(c.z),
+                             decode4_values(c.w));
+            }
+            __syncwarp();  // this round's values are read before any lane overwrites them
+            if (g < ngroups) {
+                uint32_t* ow = reinterpret_cast<uint32_t*>(buf + 12 * g);
+                ow[0] = o.x;
+                ow[1] = o.y;
+                ow[2] = o.z;
+            }
         }
-        __syncthreads();
-        // copy out: aligned 16-byte stores for the middle, bytes at the edges
+        __syncwarp();
+        // copy out buf[skip .. skip + nout): aligned 16-byte stores, bytes at the edges
         uint8_t* q = dst + ob;
         const uint32_t head = uint32_t((16 - (reinterpret_cast<uintptr_t>(q) & 15)) & 15);
         const uint32_t h = head < nout ? head : nout;
-        if (tid < int(h)) q[tid] = out[skip + tid];
+        if (lane < int(h)) q[lane] = buf[skip + lane];
         const uint32_t body = (nout - h) & ~15u;
-        for (uint32_t k = tid; k < body / 16; k += kThreads) {
-            const uint32_t off = skip + h + 16 * k;
-            *reinterpret_cast<uint4*>(q + h + 16 * k) = load16_shifted(out, off, off & 3);
+        for (uint32_t i = lane; i < body / 16; i += 32) {
+            const uint32_t off = skip + h + 16 * i;
+            *reinterpret_cast<uint4*>(q + h + 16 * i) = load16_shifted(buf, off, off & 3);
         }
-        for (uint32_t i = h + body + tid; i < nout; i += kThreads) q[i] = out[skip + i];
+        for (uint32_t i = h + body + lane; i < nout; i += 32) q[i] = buf[skip + i];
+        by_copy = next_by_copy;
     }
 }
 
+// ---------------------------------------------------------------- 4. finalize
 // One thread: the padding and length rules on the compacted stream.
 __global__ void mime_finalize_kernel(uint64_t m, int padded,
                                      const unsigned long long* __restrict__ status,
-                                     const unsigned long long* __restrict__ states,
-                                     uint64_t ntiles, int64_t* __restrict__ d_result) {
+                                     int64_t* __restrict__ d_result) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (status[4]) {
         *d_result = B64_E_TIMEOUT;
         return;
     }
-    const uint64_t last_state = ntiles ? states[ntiles - 1] : make_state(kFlagPrefix, 0, 0);
-    const uint64_t mc = st_count(last_state);           // data characters
-    const uint32_t last = st_last(last_state);
+    const uint64_t whole = status[5];
+    const uint64_t mc = st_count(whole);  // data characters
+    const uint32_t last = st_last(whole);
     uint64_t err = status[0];
     uint64_t pads = 0;
     if (padded && status[2] != kNoError) {
@@ -391,56 +491,84 @@ __global__ void mime_finalize_kernel(uint64_t m, int padded,
     *d_result = err != kNoError ? -int64_t(err) - 1 : int64_t(bytes_for(mc - pads));
 }
 
+// The bounded wait of the decode kernel on a bulk copy that is never issued:
+// one thread arms a barrier for 16 bytes that never arrive and waits.
+__global__ void selftest_wait_kernel(int64_t* __restrict__ d_result, uint64_t wait_limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&bar, 16);
+    if (!wait_copy(&bar, 0, wait_limit_ns)) {
+        atomicOr(&g_fault, 1u);
+        *d_result = B64_E_TIMEOUT;
+    } else {
+        *d_result = 0;
+    }
+}
+
 struct Occ {
     std::once_flag once;
-    cudaError_t err = cudaSuccess;
     int ctas = 1;
 };
 Occ g_occ[64];
 
+template <class K>
+int occupancy(K kernel, int threads, Occ& occ) {
+    std::call_once(occ.once, [&] {
+        int c = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, kernel, threads, 0) != cudaSuccess)
+            c = 1;
+        occ.ctas = c > 0 ? c : 1;
+    });
+    return occ.ctas;
+}
+
 }  // namespace
 
 size_t mime_workspace_bytes(uint64_t m) {
-    const uint64_t ntiles = (m + kTile - 1) / kTile;
-    return 64 + 8 * size_t(ntiles);
+    const uint64_t nseg = (m + kSeg - 1) / kSeg;
+    const uint64_t nblk = (nseg + kSegsPerBlock - 1) / kSegsPerBlock;
+    return 64 + 8 * size_t(nseg + nblk);
 }
 
 cudaError_t launch_mime_decode(const uint8_t* src, uint64_t m, uint8_t* dst,
                                const DecodeTable& tab, int padded, int64_t* d_result,
-                               void* workspace, uint64_t skip_tiles, uint64_t wait_limit_ns,
-                               cudaStream_t st) {
-    const uint64_t ntiles = (m + kTile - 1) / kTile;
+                               void* workspace, uint64_t wait_limit_ns, cudaStream_t st) {
+    const uint64_t nseg = (m + kSeg - 1) / kSeg;
+    const uint64_t nblk = (nseg + kSegsPerBlock - 1) / kSegsPerBlock;
     unsigned long long* status = static_cast<unsigned long long*>(workspace);
     unsigned long long* states = status + 8;
-    // status[0..2] (first bad byte, first '=' raw and compacted) start at "none";
-    // the tile counter, the timeout word and every tile state start at zero.
+    unsigned long long* totals = states + nseg;
+    // status[0..2] (first bad byte, first '=' raw and compacted) start at
+    // "none"; status[3..7] (status[4]: the timeout word; status[5]: the whole
+    // input's state) at zero.
     cudaError_t e = cudaMemsetAsync(status, 0xFF, 3 * sizeof(uint64_t), st);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(status + 3, 0, (5 + ntiles) * sizeof(uint64_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status + 3, 0, 5 * sizeof(uint64_t), st);
     if (e != cudaSuccess) return e;
-    if (ntiles) {
+    if (nseg) {
         const DeviceInfo& di = device_info();
-        Occ& occ = g_occ[di.device & 63];
-        std::call_once(occ.once, [&] {
-            int c = 1;
-            occ.err = cudaFuncSetAttribute(mime_decode_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           int(kDynSmem));
-            if (occ.err == cudaSuccess &&
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, mime_decode_kernel, kThreads,
-                                                              kDynSmem) != cudaSuccess)
-                c = 1;
-            occ.ctas = c > 0 ? c : 1;
-        });
-        if (occ.err != cudaSuccess) return occ.err;
-        uint64_t grid = uint64_t(di.sm_count) * occ.ctas;
-        if (ntiles < grid) grid = ntiles;
-        mime_decode_kernel<<<unsigned(grid), kThreads, kDynSmem, st>>>(
-            src, m, dst, tab, padded, status, states, ntiles, skip_tiles, wait_limit_ns);
+        mime_count_kernel<<<unsigned(nblk), kCountThreads, 0, st>>>(src, m, states, totals, nseg);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        mime_scan_kernel<<<1, kScanThreads, 0, st>>>(totals, nblk, status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        uint64_t grid = uint64_t(di.sm_count) *
+                        occupancy(mime_decode_kernel, kThreads, g_occ[di.device & 63]);
+        const uint64_t need = (nseg + kWarps - 1) / kWarps;
+        if (need < grid) grid = need;
+        mime_decode_kernel<<<unsigned(grid), kThreads, 0, st>>>(
+            src, m, dst, tab, padded, status, states, totals, nseg, wait_limit_ns);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    mime_finalize_kernel<<<1, 32, 0, st>>>(m, padded, status, states, ntiles, d_result);
+    mime_finalize_kernel<<<1, 32, 0, st>>>(m, padded, status, d_result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_selftest_wait(int64_t* d_result, uint64_t wait_limit_ns, cudaStream_t st) {
+    selftest_wait_kernel<<<1, 32, 0, st>>>(d_result, wait_limit_ns);
     return cudaGetLastError();
 }
 

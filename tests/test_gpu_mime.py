@@ -15,7 +15,7 @@ from paper_1910_05109_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-TILE = 32768
+TILE = 4096  # raw bytes per segment of the decode kernel
 
 
 @pytest.fixture(scope="module")
@@ -81,7 +81,7 @@ def test_padding_across_tile_edges(b64, orc):
             # place the padding right at a tile boundary, with whitespace around it
             k = int((body[-2:] == ord("=")).sum())
             head, pad = body[:body.size - k], body[body.size - k:]
-            filler = np.full(max(0, TILE - head.size - gap), 10, np.uint8)
+            filler = np.full((TILE - (head.size + gap) % TILE) % TILE, 10, np.uint8)
             text = np.concatenate([head, filler, np.full(gap, 13, np.uint8), pad,
                                    np.full(gap, 32, np.uint8)])
             check(b64, orc, text, std, orc.standard_alphabet(), True)
@@ -137,20 +137,14 @@ def test_config4_documents_with_stray_bytes(b64, orc):
 
 
 def test_bounded_wait_timeout_selftest(b64, orc):
-    """A look-back wait that nothing will satisfy: the call reports
-    B64_E_TIMEOUT within the limit, the fault flag is raised, and the context
-    keeps working."""
+    """The wait the kernels use for their bulk copies, on a barrier armed for a
+    copy that is never issued: the call reports B64_E_TIMEOUT within the
+    limit, the fault flag is raised, and the context keeps working."""
     import ctypes
     import time
-    text = wl.mime_wrap(orc.encode(wl.random_bytes(60_000, 800)))
-    src = torch.from_numpy(text).cuda()
-    dst = torch.empty(b64.decoded_max_length(text.size), dtype=torch.uint8, device="cuda")
     res = torch.zeros(1, dtype=torch.int64, device="cuda")
-    ws = b64.mime_workspace(text.size)
     t0 = time.time()
-    rc = b64.lib().b64_selftest_wait_timeout(src.data_ptr(), text.size, dst.data_ptr(),
-                                             b64.Alphabet.standard().handle, res.data_ptr(),
-                                             ws.data_ptr(), ws.numel(), ctypes.c_uint64(50_000_000),
+    rc = b64.lib().b64_selftest_wait_timeout(res.data_ptr(), ctypes.c_uint64(50_000_000),
                                              torch.cuda.current_stream().cuda_stream)
     assert rc == b64.B64_SUCCESS, b64.last_error()
     torch.cuda.synchronize()
@@ -158,7 +152,10 @@ def test_bounded_wait_timeout_selftest(b64, orc):
     assert int(res.item()) == b64.B64_E_TIMEOUT
     assert b64.device_fault_flag(clear=True) != 0
     assert b64.device_fault_flag() == 0
-    r, got = b64.mime_decode(src, b64.Alphabet.standard())
+    rc = b64.lib().b64_selftest_wait_timeout(res.data_ptr(), ctypes.c_uint64(0), None)
+    assert rc == b64.B64_ERR_INVALID_ARGUMENT
+    text = wl.mime_wrap(orc.encode(wl.random_bytes(60_000, 800)))
+    r, got = b64.mime_decode(torch.from_numpy(text).cuda(), b64.Alphabet.standard())
     assert r == 60_000
 
 

@@ -352,59 +352,85 @@ __global__ void __launch_bounds__(kThreads, 6)
         const uint64_t P = st_count(blk) + st_count(pre);
         const uint32_t prev_last = st_flag(pre) ? st_last(pre) : st_flag(blk) ? st_last(blk) : 0u;
 
-        // ---- row by row: translate, count, scan, store the values at their
-        //      index (buf[kLead + index]); note the first bad byte and '='
+        // ---- row by row (512 bytes = four sub-rows of 128; lane L takes word L
+        //      of each): translate, count, scan, and store each value at
+        //      buf[kLead + s + index], s = P mod 4, so that whole groups of four
+        //      start on 16-byte boundaries. A value's position never passes its
+        //      raw byte by more than 3, so the next row is read before any lane
+        //      writes (the only raw bytes a row's stores can reach).
+        const uint32_t s = uint32_t(P & 3);
+        const uint32_t* raw32 = reinterpret_cast<const uint32_t*>(buf + kLead);
         uint32_t bad_raw = 0xFFFFFFFFu, eq_raw = 0xFFFFFFFFu, eq_comp = 0xFFFFFFFFu,
                  stop = 0xFFFFFFFFu;
         uint32_t rowbase = 0;
+        uint32_t xr[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) xr[j] = raw32[32 * j + lane];
 #pragma unroll 1
         for (int r = 0; r < kRows; ++r) {
-            const uint32_t off = kRow * r + 16 * lane;
-            const uint4 w = *reinterpret_cast<const uint4*>(buf + kLead + off);
-            const uint32_t x[4] = {w.x, w.y, w.z, w.w};
-            uint32_t T[4], dm[4], badm = 0;
+            uint32_t xn[4] = {0u, 0u, 0u, 0u};
+            if (r + 1 < kRows) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint32_t t0 = lut[x[q] & 0xFFu], t1 = lut[(x[q] >> 8) & 0xFFu];
-                const uint32_t t2 = lut[(x[q] >> 16) & 0xFFu], t3 = lut[x[q] >> 24];
-                T[q] = t0 | (t1 << 8) | (t2 << 16) | (t3 << 24);
-                const uint32_t b7 = T[q] & 0x80808080u, b6 = (T[q] << 1) & 0x80808080u;
-                dm[q] = ~(b7 & b6) & 0x80808080u;  // not whitespace (0xC0)
-                badm |= b7 & ~b6;                  // bad or '=' (0x80)
+                for (int j = 0; j < 4; ++j) xn[j] = raw32[128 * (r + 1) + 32 * j + lane];
             }
-            const uint32_t c = __popc(dm[0]) + __popc(dm[1]) + __popc(dm[2]) + __popc(dm[3]);
-            const uint32_t incl = warp_scan_add32(c, lane);
-            const uint32_t pos = rowbase + incl - c;
-            rowbase += __shfl_sync(0xffffffffu, incl, 31);
-            __syncwarp();  // the row is read everywhere before any lane writes into it
-            uint8_t* out = buf + kLead + pos;
-            uint32_t q = 0;
+            uint32_t T[4], dm[4], badm[4], C = 0;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const uint32_t d = (dm[i >> 2] >> (8 * (i & 3) + 7)) & 1u;
-                if (d) out[q] = uint8_t(T[i >> 2] >> (8 * (i & 3)));
-                q += d;
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t x = xr[j];
+                const uint32_t t0 = lut[x & 0xFFu], t1 = lut[(x >> 8) & 0xFFu];
+                const uint32_t t2 = lut[(x >> 16) & 0xFFu], t3 = lut[x >> 24];
+                T[j] = t0 | (t1 << 8) | (t2 << 16) | (t3 << 24);
+                const uint32_t b7 = T[j] & 0x80808080u, b6 = (T[j] << 1) & 0x80808080u;
+                dm[j] = ~(b7 & b6) & 0x80808080u;  // not whitespace (0xC0)
+                badm[j] = b7 & ~b6;                // bad or '=' (0x80)
+                C |= uint32_t(__popc(dm[j])) << (8 * j);
             }
-            if (badm) {  // rare: locate the chunk's first bad byte and first '='
-                uint32_t qq = 0;
-                for (int i = 0; i < 16; ++i) {
-                    const uint32_t v = (T[i >> 2] >> (8 * (i & 3))) & 0xFFu;
-                    if (v == kSpace) continue;
-                    if (v & kBad) {
-                        const uint32_t ch = byte_of(w, i);
-                        if (stop == 0xFFFFFFFFu) stop = pos + qq;
-                        if (ch == '=' && padded) {
-                            if (eq_raw == 0xFFFFFFFFu) {
-                                eq_raw = off + i;
-                                eq_comp = pos + qq;
-                            }
-                        } else if (bad_raw == 0xFFFFFFFFu) {
-                            bad_raw = off + i;
-                        }
+            // four 8-bit counts scanned at once (a sub-row holds at most 128)
+            const uint32_t incl = warp_scan_add32(C, lane);
+            const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t ex = incl - C;
+            __syncwarp();  // row r and row r + 1 are read everywhere before any lane writes
+            uint32_t base = rowbase;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t idx = base + ((ex >> (8 * j)) & 0xFFu);
+                uint8_t* out = buf + kLead + s + idx;
+                uint32_t q = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t v = (T[j] >> (8 * i)) & 0xFFu;
+                    if (v < kSpace) {
+                        out[q] = uint8_t(v);
+                        ++q;
                     }
-                    ++qq;
                 }
+                if (badm[j]) {  // rare: the word's first bad byte and first '='
+                    uint32_t qq = 0;
+                    for (int i = 0; i < 4; ++i) {
+                        const uint32_t v = (T[j] >> (8 * i)) & 0xFFu;
+                        if (v == kSpace) continue;
+                        if (v & kBad) {
+                            const uint32_t ch = (xr[j] >> (8 * i)) & 0xFFu;
+                            const uint32_t rawpos = kRow * r + 128 * j + 4 * lane + i;
+                            if (stop == 0xFFFFFFFFu || idx + qq < stop) stop = idx + qq;
+                            if (ch == '=' && padded) {
+                                if (eq_raw == 0xFFFFFFFFu || rawpos < eq_raw) {
+                                    eq_raw = rawpos;
+                                    eq_comp = idx + qq;
+                                }
+                            } else if (bad_raw == 0xFFFFFFFFu || rawpos < bad_raw) {
+                                bad_raw = rawpos;
+                            }
+                            break;
+                        }
+                        ++qq;
+                    }
+                }
+                base += (tot >> (8 * j)) & 0xFFu;
             }
+            rowbase = base;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) xr[j] = xn[j];
         }
         const uint32_t count = rowbase;
         stop = __reduce_min_sync(0xffffffffu, stop);
@@ -421,24 +447,23 @@ __global__ void __launch_bounds__(kThreads, 6)
             }
         }
 
-        // ---- whole groups in place: 16 values -> 12 bytes; the value of data
-        //      character P + i sits at buf[kLead + i], the one before P at
-        //      buf[kLead - 1], so the group holding P starts at buf[kLead - s]
-        const uint32_t s = uint32_t(P & 3);
-        if (lane == 0 && s) buf[kLead - 1] = lut[prev_last];
+        // ---- whole groups in place: 16 values -> 12 bytes. The value of data
+        //      character P + i sits at buf[kLead + s + i], so the group holding P
+        //      starts at buf[kLead] and group g at buf[kLead + 16 g]; the value
+        //      before P goes to buf[kLead + s - 1]
+        if (lane == 0 && s) buf[kLead + s - 1] = lut[prev_last];
         __syncwarp();
         const uint32_t jend = stop < count ? stop : count;
         const uint64_t ob = bytes_for(P), oe = bytes_for(P + jend);
         const uint32_t nout = uint32_t(oe > ob ? oe - ob : 0);
         const uint32_t skip = s ? s - 1 : 0;  // bytes of the first group written before P
         const uint32_t ngroups = (s + jend + 15) / 16;
-        const uint32_t first = kLead - s, sh = first & 3;
 #pragma unroll 1
         for (uint32_t g0 = 0; g0 < ngroups; g0 += 32) {
             const uint32_t g = g0 + lane;
             uint3 o = make_uint3(0, 0, 0);
             if (g < ngroups) {
-                const uint4 c = load16_shifted(buf, first + 16 * g, sh);
+                const uint4 c = *reinterpret_cast<const uint4*>(buf + kLead + 16 * g);
                 o = pack4x24(decode4_values(c.x), decode4_values(c.y), decode4_values(c.z),
                              decode4_values(c.w));
             }
@@ -451,15 +476,26 @@ __global__ void __launch_bounds__(kThreads, 6)
             }
         }
         __syncwarp();
-        // copy out buf[skip .. skip + nout): aligned 16-byte stores, bytes at the edges
+        // copy out buf[skip .. skip + nout): 16-byte stores at aligned addresses,
+        // each built from two aligned 16-byte shared loads; bytes at the edges
         uint8_t* q = dst + ob;
         const uint32_t head = uint32_t((16 - (reinterpret_cast<uintptr_t>(q) & 15)) & 15);
         const uint32_t h = head < nout ? head : nout;
         if (lane < int(h)) q[lane] = buf[skip + lane];
         const uint32_t body = (nout - h) & ~15u;
+        const uint32_t o0 = skip + h, sw = (o0 & 15) >> 2, sb = 8 * (o0 & 3);
         for (uint32_t i = lane; i < body / 16; i += 32) {
-            const uint32_t off = skip + h + 16 * i;
-            *reinterpret_cast<uint4*>(q + h + 16 * i) = load16_shifted(buf, off, off & 3);
+            const uint32_t A = (o0 & ~15u) + 16 * i;
+            const uint4 a = *reinterpret_cast<const uint4*>(buf + A);
+            const uint4 b = *reinterpret_cast<const uint4*>(buf + A + 16);
+            const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            uint32_t v[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k)  // words sw .. sw + 4 (sw is the same in every lane)
+                v[k] = sw == 0 ? w[k] : sw == 1 ? w[k + 1] : sw == 2 ? w[k + 2] : w[(k + 3) & 7];
+            *reinterpret_cast<uint4*>(q + h + 16 * i) =
+                make_uint4(__funnelshift_r(v[0], v[1], sb), __funnelshift_r(v[1], v[2], sb),
+                           __funnelshift_r(v[2], v[3], sb), __funnelshift_r(v[3], v[4], sb));
         }
         for (uint32_t i = h + body + lane; i < nout; i += 32) q[i] = buf[skip + i];
         by_copy = next_by_copy;

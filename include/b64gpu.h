@@ -258,7 +258,9 @@ void b64_host_codec_destroy(b64_host_codec* c);
  * MiB) as one batched encode and/or one batched decode: a host-to-device
  * copy, the batched kernels, device-to-host copies. Batches on different
  * streams overlap, and requests that arrive while others run join the next
- * batch. A server is used by one thread at a time. */
+ * batch. Host copies into and out of the staging area are spread over up to
+ * eight worker threads the server starts (half the hardware threads). A
+ * server is used by one thread at a time. */
 typedef struct b64_server b64_server;
 
 typedef struct {

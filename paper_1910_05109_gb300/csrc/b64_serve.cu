@@ -16,9 +16,15 @@
 // Batches on different streams overlap (copies of one with kernels of
 // another); requests that arrive while batches run are admitted as soon as a
 // stream and ring space are free. One thread at a time may use a server.
+#include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "b64_internal.h"
@@ -63,6 +69,105 @@ private:
     std::deque<std::pair<size_t, size_t>> blocks_;
 };
 
+// Host copies of one poll (packing payloads into staging, unpacking
+// results into the callers' buffers) spread over worker threads: the tasks
+// are cut into pieces of at most kPiece bytes and taken from a shared index
+// by the workers and the calling thread. Each run is its own job object, so
+// a worker that wakes late only ever sees a finished job. Small jobs run on
+// the caller alone.
+class CopyPool {
+public:
+    struct Task {
+        void* dst;
+        const void* src;
+        size_t len;
+    };
+    static constexpr size_t kPiece = size_t(1) << 20;
+    static constexpr size_t kInline = size_t(512) << 10;
+
+    explicit CopyPool(int threads) {
+        for (int i = 0; i < threads; ++i) workers_.emplace_back([this] { work(); });
+    }
+    ~CopyPool() {
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto& t : workers_) t.join();
+    }
+
+    void run(const std::vector<Task>& tasks) {
+        size_t total = 0;
+        for (const auto& t : tasks) total += t.len;
+        if (workers_.empty() || total <= kInline) {
+            for (const auto& t : tasks)
+                if (t.len) memcpy(t.dst, t.src, t.len);
+            return;
+        }
+        auto job = std::make_shared<Job>();
+        for (const auto& t : tasks)
+            for (size_t o = 0; o < t.len; o += kPiece)
+                job->pieces.push_back({static_cast<uint8_t*>(t.dst) + o,
+                                       static_cast<const uint8_t*>(t.src) + o,
+                                       std::min(kPiece, t.len - o)});
+        job->left.store(job->pieces.size());
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            job_ = job;
+            ++generation_;
+        }
+        cv_.notify_all();
+        drain(*job);
+        std::unique_lock<std::mutex> g(mu_);
+        done_cv_.wait(g, [&] { return job->left.load() == 0; });
+    }
+
+private:
+    struct Job {
+        std::vector<Task> pieces;
+        std::atomic<size_t> next{0}, left{0};
+    };
+    void drain(Job& j) {
+        for (;;) {
+            const size_t i = j.next.fetch_add(1);
+            if (i >= j.pieces.size()) return;
+            memcpy(j.pieces[i].dst, j.pieces[i].src, j.pieces[i].len);
+            if (j.left.fetch_sub(1) == 1) {
+                std::lock_guard<std::mutex> g(mu_);
+                done_cv_.notify_all();
+            }
+        }
+    }
+    void work() {
+        uint64_t seen = 0;
+        for (;;) {
+            std::shared_ptr<Job> job;
+            {
+                std::unique_lock<std::mutex> g(mu_);
+                cv_.wait(g, [&] { return stop_ || generation_ != seen; });
+                if (stop_) return;
+                seen = generation_;
+                job = job_;
+            }
+            drain(*job);
+        }
+    }
+
+    std::vector<std::thread> workers_;
+    std::shared_ptr<Job> job_;
+    std::mutex mu_;
+    std::condition_variable cv_, done_cv_;
+    uint64_t generation_ = 0;
+    bool stop_ = false;
+};
+
+int default_copy_threads() {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int n = hw > 2 ? int(hw / 2) : 0;
+    return n > 8 ? 8 : n;
+}
+
 }  // namespace
 
 struct b64_server_req {
@@ -82,7 +187,7 @@ struct b64_server_batch {
     int stream = 0;
     std::vector<b64_server_req> reqs;
     size_t off = 0, bytes = 0;  // ring block
-    size_t o_out = 0, o_meta = 0, o_res = 0, o_ws = 0, meta_bytes = 0;
+    size_t o_in = 0, o_out = 0, o_meta = 0, o_res = 0, o_ws = 0, meta_bytes = 0;
     std::vector<int64_t> dst_off;
     cudaEvent_t done = nullptr;
     bool ready = false;     // event fired; results are in staging
@@ -103,6 +208,8 @@ struct b64_server {
     std::deque<b64_server_batch> inflight;
     int device = 0;
     uint64_t launched_batches = 0;
+    CopyPool* copies = nullptr;
+    std::vector<CopyPool::Task> tasks;  // scratch of one poll
 };
 
 namespace {
@@ -111,14 +218,17 @@ size_t out_capacity(const b64_server* s, int op, int alph, size_t len) {
     return op == 0 ? b64_encoded_length(len, s->padded[alph]) : b64_decoded_max_length(len);
 }
 
-// Layout of a batch block: [payload][outputs][src_off n+1][dst_off n+1][ids n]
-// [results n][workspace], sections 256-byte aligned.
+// Layout of a batch block: [src_off n+1][dst_off n+1][ids n][payload]
+// [outputs][results n][workspace], sections 256-byte aligned, so that one
+// host-to-device copy moves the offsets and the payload, and one
+// device-to-host copy the outputs and the results.
 size_t batch_layout(b64_server_batch& b, size_t in_bytes, size_t out_bytes) {
     const size_t n = b.reqs.size();
-    b.o_out = align_up(in_bytes);
-    b.o_meta = b.o_out + align_up(out_bytes);
+    b.o_meta = 0;
     b.meta_bytes = align_up(2 * (n + 1) * sizeof(int64_t) + n);
-    b.o_res = b.o_meta + b.meta_bytes;
+    b.o_in = b.meta_bytes;
+    b.o_out = b.o_in + align_up(in_bytes);
+    b.o_res = b.o_out + align_up(out_bytes);
     b.o_ws = b.o_res + align_up(n * sizeof(int64_t));
     return b.o_ws + align_up(b64::batch_workspace_bytes(int64_t(n)));
 }
@@ -144,10 +254,11 @@ int launch(b64_server* s, b64_server_batch& b) {
     int64_t* h_dst_off = h_src_off + (n + 1);
     uint8_t* h_ids = reinterpret_cast<uint8_t*>(h_dst_off + (n + 1));
     b.dst_off.resize(n + 1);
+    s->tasks.clear();
     size_t pi = 0, po = 0;
     for (size_t i = 0; i < n; ++i) {
         const auto& r = b.reqs[i];
-        if (r.len) memcpy(h + pi, r.in, r.len);
+        if (r.len) s->tasks.push_back({h + b.o_in + pi, r.in, r.len});
         h_src_off[i] = int64_t(pi);
         h_dst_off[i] = int64_t(po);
         b.dst_off[i] = int64_t(po);
@@ -158,22 +269,18 @@ int launch(b64_server* s, b64_server_batch& b) {
     h_src_off[n] = int64_t(pi);
     h_dst_off[n] = int64_t(po);
     b.dst_off[n] = int64_t(po);
+    s->copies->run(s->tasks);
     cudaStream_t st = s->streams[b.stream];
-    cudaError_t e = cudaSuccess;
-    if (in_bytes) e = cudaMemcpyAsync(d, h, in_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d + b.o_meta, h + b.o_meta, b.meta_bytes, cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(d, h, b.o_in + in_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return -1;
-    b64::BatchArgs a{d, reinterpret_cast<const int64_t*>(d + b.o_meta), int64_t(n), d + b.o_out,
-                     reinterpret_cast<const int64_t*>(d + b.o_meta) + (n + 1),
+    b64::BatchArgs a{d + b.o_in, reinterpret_cast<const int64_t*>(d + b.o_meta), int64_t(n),
+                     d + b.o_out, reinterpret_cast<const int64_t*>(d + b.o_meta) + (n + 1),
                      d + b.o_meta + 2 * (n + 1) * sizeof(int64_t),
                      reinterpret_cast<int64_t*>(d + b.o_res)};
     e = b64::launch_batch(b.op == 1, a, s->tabs, 4, d + b.o_ws, st);
-    if (e == cudaSuccess && out_bytes)
-        e = cudaMemcpyAsync(h + b.o_out, d + b.o_out, out_bytes, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h + b.o_res, d + b.o_res, n * sizeof(int64_t), cudaMemcpyDeviceToHost,
-                            st);
+    if (e == cudaSuccess)  // outputs and results in one copy
+        e = cudaMemcpyAsync(h + b.o_out, d + b.o_out, b.o_res - b.o_out + n * sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaEventRecord(b.done, st);
     return e == cudaSuccess ? 0 : -1;
 }
@@ -208,6 +315,7 @@ b64_server* b64_server_create(size_t budget_bytes, int n_streams, size_t max_bat
         if (e == cudaSuccess) s->streams.push_back(st);
     }
     s->busy.assign(s->streams.size(), 0);
+    s->copies = new CopyPool(default_copy_threads());
     if (e != cudaSuccess) {
         set_error(0, "b64_server_create: %s", cudaGetErrorString(e));
         b64_server_destroy(s);
@@ -249,16 +357,20 @@ int b64_server_poll(b64_server* s, b64_completion* out, int max_out) {
         const uint8_t* h = s->h_stage + b.off;
         const int64_t* res = reinterpret_cast<const int64_t*>(h + b.o_res);
         const auto now = Clock::now();
-        while (b.reported < b.reqs.size() && nout < max_out) {
-            const size_t i = b.reported++;
+        const size_t first = b.reported;
+        const size_t take = std::min(b.reqs.size() - first, size_t(max_out - nout));
+        s->tasks.clear();
+        for (size_t i = first; i < first + take; ++i)
+            if (res[i] > 0) s->tasks.push_back({b.reqs[i].out, h + b.o_out + b.dst_off[i], size_t(res[i])});
+        s->copies->run(s->tasks);
+        for (size_t i = first; i < first + take; ++i) {
             const auto& r = b.reqs[i];
-            const int64_t v = res[i];
-            if (v > 0) memcpy(r.out, h + b.o_out + b.dst_off[i], size_t(v));
             out[nout].tag = r.tag;
-            out[nout].result = v;
+            out[nout].result = res[i];
             out[nout].latency_us = std::chrono::duration<double, std::micro>(now - r.t0).count();
             ++nout;
         }
+        b.reported = first + take;
         if (b.reported == b.reqs.size()) {
             b.finished = true;
             s->busy[b.stream] -= 1;
@@ -332,6 +444,7 @@ void b64_server_destroy(b64_server* s) {
     for (auto st : s->streams) cudaStreamDestroy(st);
     if (s->d_arena) cudaFree(s->d_arena);
     if (s->h_stage) cudaFreeHost(s->h_stage);
+    delete s->copies;
     delete s;
 }
 

@@ -621,6 +621,79 @@ def run_mime(args):
           "gpu_launches": 2 * args.steps})
 
 
+# ---------------------------------------------------------------- Table 2 sizes
+
+def run_table2(args):
+    """Decode (and encode) at the sizes of the paper's Table 2 files (141,020;
+    247,222; 2,357; 34,904,444 bytes of binary data; random bytes stand in,
+    as the codec is content-insensitive). Per size: the base64 text of the
+    data is decoded from device memory, one call at a time (eager launches)
+    and as 100 calls recorded in a CUDA graph; GB/s counts base64 bytes, the
+    paper's unit, beside a D2D memcpy of the same text. Everything fits in
+    L2 except the largest size."""
+    import torch
+    from paper_1910_05109_gb300 import binding as b64
+    from paper_1910_05109_gb300 import build as gpu_build
+    from paper_1910_05109_gb300 import workloads as wl
+
+    gpu_build.build()
+    torch.cuda.set_device(0)
+    std = b64.Alphabet.standard()
+    stream = torch.cuda.Stream()
+    rows = []
+    launches = 0
+    for name, n in (("lena.jpg", 141_020), ("mandril.jpg", 247_222), ("google logo png", 2_357),
+                    ("large.zip", 34_904_444)):
+        data = torch.from_numpy(wl.random_bytes(n, 2)).cuda()
+        text = b64.encode(data, std)
+        torch.cuda.synchronize()
+        m = text.numel()
+        dst = torch.empty(b64.decoded_max_length(m), dtype=torch.uint8, device="cuda")
+        enc = torch.empty_like(text)
+        res = torch.zeros(1, dtype=torch.int64, device="cuda")
+        reps = 200 if n < (1 << 20) else 50
+
+        def timed(fn, k):
+            with torch.cuda.stream(stream):
+                for _ in range(5):
+                    fn()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(k):
+                    fn()
+                e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / k
+
+        dec_ms = timed(lambda: b64.decode_async(text, dst, res, std, stream), reps)
+        enc_ms = timed(lambda: b64.encode(data, std, enc, stream), reps)
+        assert int(res.item()) == n and torch.equal(dst[:n], data) and torch.equal(enc, text)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            b64.decode_async(text, dst, res, std, stream)
+            stream.synchronize()
+            with torch.cuda.graph(g, stream=stream):
+                for _ in range(100):
+                    b64.decode_async(text, dst, res, std, stream)
+        graph_ms = timed(g.replay, max(2, reps // 100)) / 100
+        cp = torch.empty_like(text)
+        mc_ms = timed(lambda: cp.copy_(text), reps)
+        launches += 3 * (reps + 5) * 2 + 300 * (max(2, reps // 100) + 5)
+        rows.append({"file": name, "bytes": n, "base64_bytes": m,
+                     "decode_gbps": m / (dec_ms / 1e3) / 1e9,
+                     "decode_graph_gbps": m / (graph_ms / 1e3) / 1e9,
+                     "encode_gbps": m / (enc_ms / 1e3) / 1e9,
+                     "memcpy_gbps": m / (mc_ms / 1e3) / 1e9,
+                     "decode_us": dec_ms * 1e3, "decode_graph_us": graph_ms * 1e3})
+    big = rows[-1]
+    emit({"metric": METRIC, "workload": "paper Table 2 sizes", "value": big["decode_gbps"],
+          "unit": "GB/s (base64 bytes, decode, 34,904,444-byte case)", "n_gpus": 1, "steps": 0,
+          "warmup": 5, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+          "vs_baseline": None, "dtype": "u8", "data": "synthetic (random bytes at the files' sizes)",
+          "config": {"workload": "Table 2 sizes", "l2": "all but the largest case fit in L2"},
+          "sizes": rows, "gpu_launches": launches})
+
+
 # ---------------------------------------------------------------- serving workload
 
 def run_serve(args):
@@ -682,7 +755,7 @@ def main():
                     help="host codec streams for the e2e leg (0 = library default)")
     ap.add_argument("--bytes", type=int, default=N_BYTES,
                     help="input size (default 1 GiB; smaller sizes are for profiling)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "mime"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "mime", "table2"],
                     help="single: the 1 GiB single-buffer step (default); batch: 100,000 "
                          "strings in one launch sequence vs one launch per string; serve: "
                          "Poisson request stream through the continuous-batching engine")
@@ -704,6 +777,8 @@ def main():
         run_serve(args)
     elif args.workload == "mime":
         run_mime(args)
+    elif args.workload == "table2":
+        run_table2(args)
     else:
         run_gpu(args)
 

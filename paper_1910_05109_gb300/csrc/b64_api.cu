@@ -209,8 +209,7 @@ int b64_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b64_alp
     if (overlaps(src, len, dst, b64_decoded_max_length(len)))
         return set_error(B64_ERR_INVALID_ARGUMENT, "b64_decode_async: src and dst overlap");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(d_result, 0xFF, sizeof(int64_t), s);
-    if (e == cudaSuccess) e = launch_decode(src, len, dst, a->dec, a->padded, d_result, s);
+    const cudaError_t e = launch_decode(src, len, dst, a->dec, a->padded, d_result, s);
     if (e != cudaSuccess)
         return set_error(B64_ERR_CUDA, "b64_decode_async: %s", cudaGetErrorString(e));
     return B64_SUCCESS;

@@ -26,6 +26,8 @@
 // result.
 #include <mutex>
 
+#include <cooperative_groups.h>
+
 #include "b64_internal.h"
 
 #ifndef B64_DEC_WARPS
@@ -216,14 +218,13 @@ __device__ __forceinline__ uint32_t table_at(const DecodeTable& tab, uint32_t c)
     return (tab.w[c >> 2] >> (8 * (c & 3))) & 0xFFu;
 }
 
-// One thread: the padding and length rules on the tail [body, m), the
-// tail's bytes, and the call's result (length, or -(first error + 1)).
-__global__ void decode_finalize_kernel(const uint8_t* __restrict__ src, uint64_t m,
-                                       uint8_t* __restrict__ dst, const __grid_constant__ DecodeTable tab, int padded,
-                                       int64_t* d_result) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// The padding and length rules on the tail [body, m) (one thread), given the
+// smallest bad offset found in the body (kNoError if none): writes the
+// tail's bytes and returns the call's result (length, or -(first error + 1)).
+__device__ int64_t tail_result(const uint8_t* __restrict__ src, uint64_t m,
+                               uint8_t* __restrict__ dst, const DecodeTable& tab, int padded,
+                               uint64_t err) {
     const uint64_t body = body_length(m);
-    uint64_t err = *reinterpret_cast<unsigned long long*>(d_result);
     const uint32_t last = m >= 1 ? src[m - 1] : 0u;
     uint32_t pads = 0;
     if (padded && m >= 1 && last == '=') pads = (m >= 2 && src[m - 2] == '=') ? 2 : 1;
@@ -244,10 +245,7 @@ __global__ void decode_finalize_kernel(const uint8_t* __restrict__ src, uint64_t
         }
     }
     if (padded ? (m % 4 != 0) : (m % 4 == 1)) err = m < err ? m : err;
-    if (err != kNoError) {
-        *d_result = -int64_t(err) - 1;
-        return;
-    }
+    if (err != kNoError) return -int64_t(err) - 1;
     // Decode the tail's data characters: groups of four, then a short group
     // of k characters giving k-1 bytes (missing values taken as zero).
     const uint32_t d = tail - pads;
@@ -260,7 +258,93 @@ __global__ void decode_finalize_kernel(const uint8_t* __restrict__ src, uint64_t
         const uint32_t nb = k == 4 ? 3u : k - 1;
         for (uint32_t t = 0; t < nb; ++t) dst[o++] = uint8_t(w >> (16 - 8 * t));
     }
-    *d_result = int64_t(o);
+    return int64_t(o);
+}
+
+// One thread: the tail rules after the body kernels have folded their first
+// bad offset into *d_result.
+__global__ void decode_finalize_kernel(const uint8_t* __restrict__ src, uint64_t m,
+                                       uint8_t* __restrict__ dst, const __grid_constant__ DecodeTable tab, int padded,
+                                       int64_t* d_result) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const uint64_t err = *reinterpret_cast<unsigned long long*>(d_result);
+    *d_result = tail_result(src, m, dst, tab, padded, err);
+}
+
+// Inputs of at most kSmallMax characters: the whole strict decode in one
+// launch of one cluster of up to kSmallCtas blocks (no result
+// initialisation, no separate tail kernel). Every thread loads all of its
+// groups before decoding any of them; each block folds its first bad offset
+// into its shared memory, and after a cluster barrier block 0 reads the
+// others' through distributed shared memory and applies the tail rules.
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallPer = 16;                                   // groups per thread
+constexpr int kSmallCtas = 8;                                   // portable cluster size
+constexpr uint64_t kSmallPerCta = uint64_t(kSmallThreads) * kSmallPer * 4;  // 64 KiB
+constexpr uint64_t kSmallMax = kSmallPerCta * kSmallCtas;                   // 512 KiB
+
+template <bool kCluster>
+__global__ void __launch_bounds__(kSmallThreads)
+    decode_small_kernel(const uint8_t* __restrict__ src, uint64_t m, uint8_t* __restrict__ dst,
+                        const __grid_constant__ DecodeTable tab, int padded, int64_t* d_result) {
+    namespace cg = cooperative_groups;
+    __shared__ __align__(16) uint8_t lut[256];
+    __shared__ unsigned long long s_err;
+    const int tid = threadIdx.x;
+    const uint32_t rank = kCluster ? cg::this_cluster().block_rank() : 0u;
+    const uint32_t nblocks = kCluster ? cg::this_cluster().num_blocks() : 1u;
+    if (tid < 64) reinterpret_cast<uint32_t*>(lut)[tid] = tab.w[tid];
+    if (tid == 0) s_err = kNoError;
+    __syncthreads();
+    const uint64_t quads = body_length(m) / 4;
+    const bool al4 = (reinterpret_cast<uintptr_t>(src) & 3u) == 0;
+    const uint64_t g = uint64_t(rank) * kSmallThreads + tid, stride = uint64_t(nblocks) * kSmallThreads;
+    uint32_t w[kSmallPer];
+#pragma unroll
+    for (int k = 0; k < kSmallPer; ++k) {
+        const uint64_t q = g + uint64_t(k) * stride;
+        w[k] = q < quads ? load4(src + 4 * q, al4) : 0x41414141u;  // "AAAA": valid filler
+    }
+    uint64_t first = kNoError;
+#pragma unroll
+    for (int k = 0; k < kSmallPer; ++k) {
+        const uint64_t q = g + uint64_t(k) * stride;
+        if (q >= quads) break;
+        uint32_t err = 0;
+        const uint32_t v = decode4(w[k], lut, err);
+        if (err & kBad) {
+            for (int i = 0; i < 4; ++i) {
+                if (lut[(w[k] >> (8 * i)) & 0xFFu] & kBad) {
+                    const uint64_t pos = 4 * q + i;
+                    first = pos < first ? pos : first;
+                    break;
+                }
+            }
+        } else {
+            uint8_t* o = dst + 3 * q;
+            o[0] = uint8_t(v >> 16);
+            o[1] = uint8_t(v >> 8);
+            o[2] = uint8_t(v);
+        }
+    }
+    const uint64_t wmin = warp_min_u64(first);
+    if ((tid & 31) == 0 && wmin != kNoError) atomicMin(&s_err, (unsigned long long)wmin);
+    if (!kCluster) {
+        __syncthreads();
+        if (tid == 0) *d_result = tail_result(src, m, dst, tab, padded, s_err);
+        return;
+    }
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.sync();  // every block's minimum (and bytes) are final
+    if (rank == 0 && tid == 0) {
+        uint64_t err = kNoError;
+        for (uint32_t r = 0; r < nblocks; ++r) {
+            const uint64_t e = *cluster.map_shared_rank(&s_err, r);
+            err = e < err ? e : err;
+        }
+        *d_result = tail_result(src, m, dst, tab, padded, err);
+    }
+    cluster.sync();  // no block leaves while block 0 may still read its shared memory
 }
 
 struct KernelSetup {
@@ -274,9 +358,33 @@ KernelSetup g_setup[64];
 
 cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const DecodeTable& tab,
                           int padded, int64_t* d_result, cudaStream_t stream) {
+    if (m <= kSmallMax) {
+        const unsigned ctas = unsigned(m <= kSmallPerCta ? 1 : (m + kSmallPerCta - 1) / kSmallPerCta);
+        if (ctas == 1) {
+            decode_small_kernel<false><<<1, kSmallThreads, 0, stream>>>(src, m, dst, tab, padded,
+                                                                        d_result);
+            return cudaGetLastError();
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(ctas);
+        cfg.blockDim = dim3(kSmallThreads);
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = ctas;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, decode_small_kernel<true>, src, m, dst, tab, padded,
+                                  d_result);
+    }
     const DeviceInfo& di = device_info();
     const uint64_t body = body_length(m);
     unsigned long long* d_err = reinterpret_cast<unsigned long long*>(d_result);
+    // the body kernels fold their first bad offsets into *d_result: start at "none"
+    const cudaError_t e0 = cudaMemsetAsync(d_result, 0xFF, sizeof(int64_t), stream);
+    if (e0 != cudaSuccess) return e0;
     if (body > 0) {
         const bool aligned =
             ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0;

@@ -40,7 +40,9 @@ uint32_t encode_fault_flag(bool clear);
 
 // ---- decode (b64_decode.cu)
 // Enqueues the strict decode of m characters; *d_result receives the length
-// or -(offset+1). d_result must already hold ~0 (no error) if m > 0.
+// or -(offset+1). Up to 512 KiB of input takes one launch (one cluster of
+// up to 8 blocks); larger inputs
+// start with a memset of *d_result, then the body kernel and the tail kernel.
 cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const DecodeTable& tab,
                           int padded, int64_t* d_result, cudaStream_t stream);
 

@@ -108,6 +108,7 @@ class Alphabet:
     def __init__(self, handle: int, owned: bool):
         self.handle = handle
         self._owned = owned
+        self._padded = None  # alphabets are immutable: read once
 
     @classmethod
     def standard(cls) -> "Alphabet":
@@ -132,7 +133,9 @@ class Alphabet:
 
     @property
     def padded(self) -> bool:
-        return self.chars()[1]
+        if self._padded is None:
+            self._padded = self.chars()[1]
+        return self._padded
 
     def __del__(self):
         if getattr(self, "_owned", False) and self.handle and _lib is not None:

@@ -458,6 +458,19 @@ def run_batch(args):
             src, src_off = texts
         codec = BatchCodec(op, n, src.numel(), alphs, dev)
         cap = codec.load(src, src_off, d_aid)
+        # output offsets (b64_batch_offsets), timed on their own
+        with torch.cuda.stream(codec.stream):
+            for _ in range(3):
+                b64.batch_offsets(codec.src_off, alphs, codec.alph_id[:n], decode=op == "decode",
+                                  stream=codec.stream)
+            o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            o0.record(codec.stream)
+            for _ in range(10):
+                b64.batch_offsets(codec.src_off, alphs, codec.alph_id[:n], decode=op == "decode",
+                                  stream=codec.stream)
+            o1.record(codec.stream)
+        o1.synchronize()
+        offsets_ms = o0.elapsed_time(o1) / 10
         if args.tile_units:
             units, timings = args.tile_units, {}
         else:
@@ -485,7 +498,7 @@ def run_batch(args):
 
         if args.no_per_string:
             out[op] = {"batch_ms": batch_ms, "input_gbps": in_bytes / (batch_ms / 1e3) / 1e9,
-                       "tile_units": units, "autotune_ms": timings}
+                       "tile_units": units, "autotune_ms": timings, "offsets_ms": offsets_ms, "offsets_ms": offsets_ms}
             continue
         # One launch per string through the single-buffer calls.
         hoff = codec.src_off.cpu().numpy()
@@ -545,7 +558,7 @@ def run_batch(args):
                     break
         del g
         out[op] = {"batch_ms": batch_ms, "input_gbps": in_bytes / (batch_ms / 1e3) / 1e9,
-                   "tile_units": units, "autotune_ms": timings,
+                   "tile_units": units, "autotune_ms": timings, "offsets_ms": offsets_ms,
                    "per_string_eager_ms": eager_ms, "per_string_graph_ms": graph_ms,
                    "speedup_vs_eager": eager_ms / batch_ms,
                    "speedup_vs_graph": graph_ms / batch_ms, "identical_output": identical,

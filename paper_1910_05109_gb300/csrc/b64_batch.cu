@@ -34,7 +34,6 @@
 namespace b64 {
 namespace {
 
-constexpr int kScanThreads = 1024;
 
 // Warps per block of the tile kernels: the per-warp staging buffers are
 // static shared memory, which must stay under 48 KiB per block.
@@ -555,57 +554,91 @@ __device__ __forceinline__ int64_t warp_inclusive_scan(int64_t v, int lane) {
     return v;
 }
 
-// dst_off = exclusive scan of per-string output capacities. One block walks
-// the strings in chunks of kScanThreads x kScanItems (each thread takes
-// kScanItems consecutive strings), scanning each chunk with warp shuffles and
-// carrying the running total.
+// dst_off = exclusive scan of per-string output capacities, in three
+// launches and no workspace:
+//   1. block b scans its kOffItems strings (kOffThreads threads x kScanItems
+//      each) and writes their block-local exclusive offsets, except that the
+//      block's first slot (local offset 0) receives the block's total;
+//   2. one block turns those totals into block prefixes in place (and writes
+//      dst_off[n], the grand total);
+//   3. block b adds its prefix (its first slot, now final) to its other slots.
 constexpr int kScanItems = 8;
+constexpr int kOffThreads = 256;
+constexpr int64_t kOffItems = int64_t(kOffThreads) * kScanItems;  // strings per block
 
 template <bool kDecode>
-__global__ void __launch_bounds__(kScanThreads)
-    batch_offsets_kernel(const int64_t* __restrict__ src_off, int64_t n,
+__device__ __forceinline__ int64_t capacity(const int64_t* __restrict__ src_off, int64_t i,
+                                            const BatchTables& tabs,
+                                            const uint8_t* __restrict__ alph_id) {
+    const uint64_t len = uint64_t(src_off[i + 1] - src_off[i]);
+    if (kDecode) return int64_t((len + 3) / 4 * 3);
+    const int al = alph_id ? (alph_id[i] & (kMaxAlphabets - 1)) : 0;
+    return int64_t(enc_length(len, tabs.padded[al]));
+}
+
+template <bool kDecode>
+__global__ void __launch_bounds__(kOffThreads)
+    offsets_local_kernel(const int64_t* __restrict__ src_off, int64_t n,
                          const __grid_constant__ BatchTables tabs,
                          const uint8_t* __restrict__ alph_id, int64_t* __restrict__ dst_off) {
-    __shared__ int64_t warp_sum[kScanThreads / 32];
+    __shared__ int64_t warp_sum[kOffThreads / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    int64_t carry = 0;
-    for (int64_t base = 0; base < n; base += int64_t(kScanThreads) * kScanItems) {
-        const int64_t i0 = base + int64_t(tid) * kScanItems;
-        int64_t cap[kScanItems];
-        int64_t sum = 0;
-        int64_t prev = i0 < n ? src_off[i0] : 0;
+    const int64_t first = int64_t(blockIdx.x) * kOffItems;
+    const int64_t i0 = first + int64_t(tid) * kScanItems;
+    int64_t cap[kScanItems], sum = 0;
 #pragma unroll
-        for (int j = 0; j < kScanItems; ++j) {
-            const int64_t i = i0 + j;
-            cap[j] = 0;
-            if (i < n) {
-                const int64_t next = src_off[i + 1];
-                const uint64_t len = uint64_t(next - prev);
-                prev = next;
-                if (kDecode) {
-                    cap[j] = int64_t((len + 3) / 4 * 3);
-                } else {
-                    const int al = alph_id ? (alph_id[i] & (kMaxAlphabets - 1)) : 0;
-                    cap[j] = int64_t(enc_length(len, tabs.padded[al]));
-                }
-            }
-            sum += cap[j];
-        }
-        const int64_t incl = warp_inclusive_scan(sum, lane);
+    for (int j = 0; j < kScanItems; ++j) {
+        cap[j] = i0 + j < n ? capacity<kDecode>(src_off, i0 + j, tabs, alph_id) : 0;
+        sum += cap[j];
+    }
+    const int64_t incl = warp_inclusive_scan(sum, lane);
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    int64_t before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kOffThreads / 32; ++w) {
+        before += w < warp ? warp_sum[w] : 0;
+        total += warp_sum[w];
+    }
+    int64_t run = before + incl - sum;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (i0 + j < n) dst_off[i0 + j] = (i0 + j == first) ? total : run;
+        run += cap[j];
+    }
+}
+
+// One block: dst_off[b * kOffItems] (block totals) -> block prefixes; dst_off[n].
+__global__ void __launch_bounds__(1024)
+    offsets_blocks_kernel(int64_t n, int64_t* __restrict__ dst_off) {
+    __shared__ int64_t warp_sum[32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t nblk = (n + kOffItems - 1) / kOffItems;
+    int64_t carry = 0;
+    for (int64_t base = 0; base < nblk; base += 1024) {
+        const int64_t b = base + tid;
+        const int64_t t = b < nblk ? dst_off[b * kOffItems] : 0;
+        const int64_t incl = warp_inclusive_scan(t, lane);
         if (lane == 31) warp_sum[warp] = incl;
         __syncthreads();
-        if (warp == 0) warp_sum[lane] = warp_inclusive_scan(warp_sum[lane], lane);
-        __syncthreads();
-        int64_t run = carry + (warp ? warp_sum[warp - 1] : 0) + incl - sum;
-#pragma unroll
-        for (int j = 0; j < kScanItems; ++j) {
-            if (i0 + j < n) dst_off[i0 + j] = run;
-            run += cap[j];
+        int64_t before = 0, total = 0;
+        for (int w = 0; w < 32; ++w) {
+            before += w < warp ? warp_sum[w] : 0;
+            total += warp_sum[w];
         }
-        carry += warp_sum[kScanThreads / 32 - 1];
-        __syncthreads();  // warp_sum is rewritten by the next chunk
+        if (b < nblk) dst_off[b * kOffItems] = carry + before + incl - t;
+        carry += total;
+        __syncthreads();  // warp_sum is rewritten by the next round
     }
     if (tid == 0) dst_off[n] = carry;
+}
+
+__global__ void __launch_bounds__(kOffThreads)
+    offsets_fix_kernel(int64_t n, int64_t* __restrict__ dst_off) {
+    const int64_t first = int64_t(blockIdx.x) * kOffItems;
+    const int64_t prefix = dst_off[first];
+    for (int64_t i = first + 1 + threadIdx.x; i < first + kOffItems && i < n; i += kOffThreads)
+        dst_off[i] += prefix;
 }
 
 }  // namespace
@@ -662,10 +695,21 @@ namespace b64 {
 cudaError_t launch_batch_offsets(bool decode, const int64_t* src_off, int64_t n,
                                  const BatchTables& tabs, const uint8_t* alph_id,
                                  int64_t* dst_off, cudaStream_t st) {
-    if (decode)
-        batch_offsets_kernel<true><<<1, kScanThreads, 0, st>>>(src_off, n, tabs, alph_id, dst_off);
-    else
-        batch_offsets_kernel<false><<<1, kScanThreads, 0, st>>>(src_off, n, tabs, alph_id, dst_off);
+    const unsigned nblk = unsigned((n + kOffItems - 1) / kOffItems);
+    if (nblk) {
+        if (decode)
+            offsets_local_kernel<true><<<nblk, kOffThreads, 0, st>>>(src_off, n, tabs, alph_id,
+                                                                     dst_off);
+        else
+            offsets_local_kernel<false><<<nblk, kOffThreads, 0, st>>>(src_off, n, tabs, alph_id,
+                                                                      dst_off);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    offsets_blocks_kernel<<<1, 1024, 0, st>>>(n, dst_off);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || nblk == 0) return e;
+    offsets_fix_kernel<<<nblk, kOffThreads, 0, st>>>(n, dst_off);
     return cudaGetLastError();
 }
 

@@ -166,16 +166,49 @@ __device__ __forceinline__ int64_t round_boundary(const int64_t* __restrict__ sr
     return s0 + (r < lim ? r : lim);
 }
 
+// The per-string metadata of strings [w0, w0 + 32), one string per lane
+// (loaded with one coalesced round, read back by shuffles).
+struct Window {
+    int64_t w0 = INT64_MIN / 2;     // no string loaded yet
+    int64_t lo = 0, hi = 0, d = 0;  // src_off[i], src_off[i + 1], dst_off[i]
+    uint32_t id = 0;                // alphabet of string i
+    __device__ __forceinline__ void load(int64_t s, const int64_t* __restrict__ src_off,
+                                         const int64_t* __restrict__ dst_off,
+                                         const uint8_t* __restrict__ alph_id, int64_t n,
+                                         int lane) {
+        w0 = s;
+        const int64_t i = s + lane;
+        lo = i < n ? src_off[i] : 0;
+        hi = i < n ? src_off[i + 1] : 0;
+        d = i < n ? dst_off[i] : 0;
+        id = (i < n && alph_id) ? uint32_t(alph_id[i] & (kMaxAlphabets - 1)) : 0u;
+    }
+};
+
+// One tile: bytes [a, b) of string s, with the string's metadata.
+struct Tile {
+    int64_t s = 0, a = 0, b = 0, s0 = 0, s1 = 0, d0 = 0;
+    uint32_t id = 0;
+};
+
 // The warp's walk over its range [pos, end): strings in order, tiles of at
 // most T bytes, each starting on a group boundary of its string.
+// Warp-collective (every lane holds the same state).
 template <bool kDecode>
 struct Cursor {
     int64_t s, pos, end;
-    __device__ __forceinline__ bool next(const int64_t* __restrict__ src_off, int64_t n, int64_t T,
-                                         int64_t* ts, int64_t* ta, int64_t* tb) {
+    Window win;
+    __device__ __forceinline__ bool next(const int64_t* __restrict__ src_off,
+                                         const int64_t* __restrict__ dst_off,
+                                         const uint8_t* __restrict__ alph_id, int64_t n, int64_t T,
+                                         int lane, Tile* t) {
         for (;;) {
             if (pos >= end || s >= n) return false;
-            const int64_t s0 = src_off[s], len = src_off[s + 1] - s0;
+            if (s < win.w0 || s >= win.w0 + 32) win.load(s, src_off, dst_off, alph_id, n, lane);
+            const int k = int(s - win.w0);
+            const int64_t s0 = __shfl_sync(0xffffffffu, win.lo, k);
+            const int64_t s1 = __shfl_sync(0xffffffffu, win.hi, k);
+            const int64_t len = s1 - s0;
             const int64_t lim = s0 + (kDecode ? int64_t(dec_body_length(uint64_t(len))) : len);
             if (pos < s0) pos = s0;
             if (pos >= end) return false;
@@ -186,9 +219,13 @@ struct Cursor {
             int64_t b = pos + T;
             if (b > lim) b = lim;
             if (b > end) b = end;
-            *ts = s;
-            *ta = pos;
-            *tb = b;
+            t->s = s;
+            t->a = pos;
+            t->b = b;
+            t->s0 = s0;
+            t->s1 = s1;
+            t->d0 = __shfl_sync(0xffffffffu, win.d, k);
+            t->id = __shfl_sync(0xffffffffu, win.id, k);
             pos = b;
             return true;
         }
@@ -247,33 +284,34 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
 
     // The tile after the current one is described and its bulk copy started
     // before the current one is coded (two staging buffers per warp).
-    int64_t cs, ns = 0, ia, ib, na = 0, nb = 0;
-    if (!cur.next(src_off, n, T, &cs, &ia, &ib)) return;
-    uint64_t a = uint64_t(ia), b = uint64_t(ib);
+    Tile t, nt;
+    if (!cur.next(src_off, dst_off, alph_id, n, T, lane, &t)) return;
     bool by_copy = false, n_by_copy = false;
-    if (lane == 0) by_copy = issue_tile_load(sin_all[warp][0], src, a, b, src_end, &bars[warp][0]);
+    if (lane == 0)
+        by_copy = issue_tile_load(sin_all[warp][0], src, uint64_t(t.a), uint64_t(t.b), src_end,
+                                  &bars[warp][0]);
     by_copy = __shfl_sync(0xffffffffu, by_copy, 0);
     uint32_t phases = 0;
 
-    for (int64_t t = 0;; ++t) {
-        const int k = int(t & 1);
+    for (int64_t it = 0;; ++it) {
+        const int k = int(it & 1);
         fence_proxy_async_smem();  // this lane's reads of tile t - 1 before the copy below
         __syncwarp();              // every lane is done with the other buffer
-        const bool more = cur.next(src_off, n, T, &ns, &na, &nb);
+        const bool more = cur.next(src_off, dst_off, alph_id, n, T, lane, &nt);
         if (more) {
             if (lane == 0)
-                n_by_copy = issue_tile_load(sin_all[warp][k ^ 1], src, uint64_t(na),
-                                            uint64_t(nb), src_end, &bars[warp][k ^ 1]);
+                n_by_copy = issue_tile_load(sin_all[warp][k ^ 1], src, uint64_t(nt.a),
+                                            uint64_t(nt.b), src_end, &bars[warp][k ^ 1]);
             n_by_copy = __shfl_sync(0xffffffffu, n_by_copy, 0);
         }
         uint8_t* sin = sin_all[warp][k];
+        const uint64_t a = uint64_t(t.a), b = uint64_t(t.b);
         if (!tile_ready(by_copy, sin, &bars[warp][k], phases, k, src, a, b, src_end, lane)) {
             if (lane == 0) atomicOr(&g_fault, 1u);
             return;
         }
-        const uint64_t s1 = uint64_t(src_off[cs + 1]);
-        const bool last = b == s1;
-        const int ai = alph_id ? (alph_id[cs] & (kMaxAlphabets - 1)) : 0;
+        const bool last = t.b == t.s1;
+        const int ai = int(t.id);
         const uint8_t* lut = luts[ai];
         const uint32_t nbytes = uint32_t(b - a);
         const uint32_t triples = nbytes / 3;
@@ -312,11 +350,12 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
             nout += tabs.padded[ai] ? 4 : r + 1;
         }
         __syncwarp();
-        const uint64_t rel = a - uint64_t(src_off[cs]);  // a multiple of 3
-        warp_stage_out(dst + dst_off[cs] + rel / 3 * 4, sout, nout, lane);
+        const uint64_t rel = a - uint64_t(t.s0);  // a multiple of 3
+        warp_stage_out(dst + t.d0 + rel / 3 * 4, sout, nout, lane);
         __syncwarp();  // sout is rewritten by the next tile
         if (!more) break;
-        a = uint64_t(na); b = uint64_t(nb); cs = ns; by_copy = n_by_copy;
+        t = nt;
+        by_copy = n_by_copy;
     }
 }
 
@@ -355,38 +394,40 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
     if (bytes <= 0) return;
     const int64_t x0 = origin + bytes * gw / GW, x1 = origin + bytes * (gw + 1) / GW;
     Cursor<true> cur{0, round_boundary<true>(src_off, n, x0, lane),
-                      gw + 1 == GW ? src_off[n] : round_boundary<true>(src_off, n, x1, lane)};
+                     gw + 1 == GW ? src_off[n] : round_boundary<true>(src_off, n, x1, lane)};
     if (cur.pos >= cur.end) return;
     cur.s = cur.pos < src_off[n] ? warp_find_string(src_off, n, cur.pos, lane) : n;
     const uint64_t src_end = uint64_t(src_off[n]);
 
     // The tile after the current one is described and its bulk copy started
     // before the current one is coded (two staging buffers per warp).
-    int64_t cs, ns = 0, ia, ib, na = 0, nb = 0;
-    if (!cur.next(src_off, n, T, &cs, &ia, &ib)) return;
-    uint64_t a = uint64_t(ia), b = uint64_t(ib);
+    Tile t, nt;
+    if (!cur.next(src_off, dst_off, alph_id, n, T, lane, &t)) return;
     bool by_copy = false, n_by_copy = false;
-    if (lane == 0) by_copy = issue_tile_load(sin_all[warp][0], src, a, b, src_end, &bars[warp][0]);
+    if (lane == 0)
+        by_copy = issue_tile_load(sin_all[warp][0], src, uint64_t(t.a), uint64_t(t.b), src_end,
+                                  &bars[warp][0]);
     by_copy = __shfl_sync(0xffffffffu, by_copy, 0);
     uint32_t phases = 0;
 
-    for (int64_t t = 0;; ++t) {
-        const int k = int(t & 1);
+    for (int64_t it = 0;; ++it) {
+        const int k = int(it & 1);
         fence_proxy_async_smem();  // this lane's reads of tile t - 1 before the copy below
         __syncwarp();              // every lane is done with the other buffer
-        const bool more = cur.next(src_off, n, T, &ns, &na, &nb);
+        const bool more = cur.next(src_off, dst_off, alph_id, n, T, lane, &nt);
         if (more) {
             if (lane == 0)
-                n_by_copy = issue_tile_load(sin_all[warp][k ^ 1], src, uint64_t(na),
-                                            uint64_t(nb), src_end, &bars[warp][k ^ 1]);
+                n_by_copy = issue_tile_load(sin_all[warp][k ^ 1], src, uint64_t(nt.a),
+                                            uint64_t(nt.b), src_end, &bars[warp][k ^ 1]);
             n_by_copy = __shfl_sync(0xffffffffu, n_by_copy, 0);
         }
         uint8_t* sin = sin_all[warp][k];
+        const uint64_t a = uint64_t(t.a), b = uint64_t(t.b);
         if (!tile_ready(by_copy, sin, &bars[warp][k], phases, k, src, a, b, src_end, lane)) {
             if (lane == 0) atomicOr(&g_fault, 1u);
             return;
         }
-        const uint8_t* lut = luts[alph_id ? (alph_id[cs] & (kMaxAlphabets - 1)) : 0];
+        const uint8_t* lut = luts[t.id];
         const uint32_t nchars = uint32_t(b - a);  // a multiple of 4
         const uint32_t delta = uint32_t((reinterpret_cast<uintptr_t>(src + a)) & 15);
         const uint32_t sh = delta & 3;
@@ -406,7 +447,7 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
                 if (e & kBad) {
                     for (uint32_t i = 0; i < 16; ++i) {
                         if (lut[sin[delta + 16 * j + i]] & kBad) {
-                            const uint64_t off = a - uint64_t(src_off[cs]) + 16 * j + i;
+                            const uint64_t off = a - uint64_t(t.s0) + 16 * j + i;
                             first = off < first ? off : first;
                             break;
                         }
@@ -425,7 +466,7 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
                     if (e & kBad) {
                         for (uint32_t i = 0; i < 4; ++i) {
                             if (lut[sin[p + i]] & kBad) {
-                                const uint64_t off = a - uint64_t(src_off[cs]) + 4 * q + i;
+                                const uint64_t off = a - uint64_t(t.s0) + 4 * q + i;
                                 first = off < first ? off : first;
                                 break;
                             }
@@ -435,13 +476,14 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
             }
         }
         const uint64_t wmin = warp_min_u64(first);
-        if (lane == 0 && wmin != kNoError) atomicMin(&err[cs], (unsigned long long)wmin);
+        if (lane == 0 && wmin != kNoError) atomicMin(&err[t.s], (unsigned long long)wmin);
         __syncwarp();
-        const uint64_t rel = a - uint64_t(src_off[cs]);  // a multiple of 4
-        warp_stage_out(dst + dst_off[cs] + rel / 4 * 3, sout, nchars / 4 * 3, lane);
+        const uint64_t rel = a - uint64_t(t.s0);  // a multiple of 4
+        warp_stage_out(dst + t.d0 + rel / 4 * 3, sout, nchars / 4 * 3, lane);
         __syncwarp();  // sout is rewritten by the next tile
         if (!more) break;
-        a = uint64_t(na); b = uint64_t(nb); cs = ns; by_copy = n_by_copy;
+        t = nt;
+        by_copy = n_by_copy;
     }
 }
 

@@ -107,14 +107,15 @@ def encode(data, alphabet: bytes | None = None, padded: bool = True) -> np.ndarr
 
 
 def decode(text, alphabet: bytes | None = None, padded: bool = True,
-           mime: bool = False) -> tuple[int, np.ndarray]:
+           mime: bool = False, canonical: bool = False) -> tuple[int, np.ndarray]:
     """Strict decode. Returns (result, bytes): result is the decoded length
-    (>= 0) or -(offset+1) of the first error; bytes is empty on error."""
+    (>= 0) or -(offset+1) of the first error; bytes is empty on error.
+    canonical: also reject non-zero unused bits in a partial final group."""
     src = _u8(text)
     alph = _u8(alphabet if alphabet is not None else standard_alphabet())
     out = np.zeros(max(1, 3 * ((src.size + 3) // 4)), np.uint8)
-    r = _load().oracle_decode(_ptr(src), src.size, _ptr(out), _ptr(alph), int(padded),
-                              int(mime))
+    flags = int(bool(padded)) | (int(bool(canonical)) << 1)
+    r = _load().oracle_decode(_ptr(src), src.size, _ptr(out), _ptr(alph), flags, int(mime))
     return int(r), (out[:r] if r >= 0 else out[:0])
 
 
@@ -138,6 +139,7 @@ def encode_batch(src: np.ndarray, src_off: np.ndarray, dst_off: np.ndarray,
 def decode_batch(src: np.ndarray, src_off: np.ndarray, dst_off: np.ndarray,
                  alphabets: bytes, alph_id: np.ndarray, padded: np.ndarray,
                  dst_size: int, mime: bool = False) -> tuple[np.ndarray, np.ndarray]:
+    """Per string: padded[i] carries its flags (bit 0 padded, bit 1 canonical)."""
     src = _u8(src)
     src_off = np.ascontiguousarray(src_off, np.int64)
     dst_off = np.ascontiguousarray(dst_off, np.int64)

@@ -40,6 +40,16 @@
  *       with zero 6-bit values and yields k-1 bytes; a partial final group of
  *       encoder input (1 or 2 bytes) is completed with zero bytes (RFC 4648
  *       Sec. 4, the standard the paper cites for base64url).
+ *   R7  Canonical mode (optional, flag bit 1; RFC 4648 Sec. 3.5 lets a decoder
+ *       reject what an encoder never emits): R3 is replaced by this rule. When
+ *       the final group is partial (k = 2 or 3 data characters once the
+ *       padding is removed), the bits of its last data character that reach
+ *       no output byte (the low 4 bits for k = 2, the low 2 bits for k = 3)
+ *       must be zero; otherwise that character is an error at its own index.
+ *       It competes with the length error of R2 under R4.
+ *
+ * The decoders' `padded` argument carries flags: bit 0 = padded (R2),
+ * bit 1 = canonical (R7).
  *
  * Return values: encode returns the number of characters written; decode
  * returns the number of bytes written (>= 0) or -(offset+1) for the first
@@ -125,7 +135,8 @@ static int oracle_is_mime_space(uint8_t c) {
 }
 
 int64_t oracle_decode(const uint8_t* src, size_t m, uint8_t* dst,
-                      const uint8_t alph[64], int padded, int mime) {
+                      const uint8_t alph[64], int flags, int mime) {
+    const int padded = flags & 1, canonical = (flags >> 1) & 1;
     int inv[256];
     oracle_inverse(alph, inv);
 
@@ -158,21 +169,29 @@ int64_t oracle_decode(const uint8_t* src, size_t m, uint8_t* dst,
         }
         if (!pad_ok) { has_err = 1; err = POS(j); break; }
     }
-    if (!has_err) {
-        if (padded && mc % 4 != 0) { has_err = 1; err = m; }
-        if (!padded && mc % 4 == 1) { has_err = 1; err = m; }
-    }
-    if (has_err) {
-        free(pos);
-        return -(int64_t)err - 1;
-    }
-
     size_t pads = 0;
     if (padded) {
         if (mc >= 1 && src[POS(mc - 1)] == '=') pads = 1;
         if (mc >= 2 && src[POS(mc - 2)] == '=') pads = 2;
     }
     size_t d = mc - pads;
+    if (!has_err) {
+        if (padded && mc % 4 != 0) { has_err = 1; err = m; }
+        if (!padded && mc % 4 == 1) { has_err = 1; err = m; }
+        /* R7: the unused low bits of a partial final group's last character */
+        if (canonical && (d % 4 == 2 || d % 4 == 3)) {
+            unsigned low = d % 4 == 2 ? 15u : 3u;
+            size_t at = POS(d - 1);
+            if (((unsigned)inv[src[at]] & low) != 0 && (!has_err || at < err)) {
+                has_err = 1;
+                err = at;
+            }
+        }
+    }
+    if (has_err) {
+        free(pos);
+        return -(int64_t)err - 1;
+    }
 
     /* Sec. 2: four 6-bit values a,b,c,d -> three bytes; a short final group
      * is completed with zero values and emits one byte fewer than it has
@@ -196,7 +215,8 @@ int64_t oracle_decode(const uint8_t* src, size_t m, uint8_t* dst,
 
 /* Batched forms: string i occupies src[src_off[i] .. src_off[i+1]) and is
  * written at dst + dst_off[i]; alph_id[i] selects one of the alphabets
- * (64 bytes each, contiguous in alphs) and padded[i] its padding mode.
+ * (64 bytes each, contiguous in alphs) and padded[i] its flags (bit 0
+ * padded, bit 1 canonical; encode reads bit 0 only).
  * results[i] gets what the single-string call returns. */
 void oracle_encode_batch(const uint8_t* src, const int64_t* src_off, uint8_t* dst,
                          const int64_t* dst_off, const uint8_t* alphs,
@@ -204,7 +224,7 @@ void oracle_encode_batch(const uint8_t* src, const int64_t* src_off, uint8_t* ds
                          int64_t* results) {
     for (int64_t i = 0; i < n; ++i) {
         results[i] = oracle_encode(src + src_off[i], (size_t)(src_off[i + 1] - src_off[i]),
-                                   dst + dst_off[i], alphs + 64 * alph_id[i], padded[i]);
+                                   dst + dst_off[i], alphs + 64 * alph_id[i], padded[i] & 1);
     }
 }
 

@@ -20,7 +20,12 @@
  *     index; a length that is not a multiple of 4 is an error at offset len;
  *   - unpadded alphabets: every '=' is an error; a length of 1 mod 4 is an
  *     error at offset len;
- *   - bits of the last character that reach no output byte are ignored;
+ *   - bits of the last character that reach no output byte are ignored,
+ *     unless the alphabet was made with B64_FLAG_CANONICAL: then, when the
+ *     final group is partial (2 or 3 data characters once the padding is
+ *     removed), its last data character must have those bits (the low 4 for
+ *     2 characters, the low 2 for 3) at zero, else it is an error at its own
+ *     offset (RFC 4648 Sec. 3.5, canonical encoding);
  *   - MIME mode (b64_mime_decode*): CR, LF and space are skipped first, the
  *     rules above apply to the rest, and offsets are in the original input.
  *
@@ -75,6 +80,19 @@ typedef struct b64_alphabet b64_alphabet;
  * requires it; 0 = no padding. Returns NULL (and sets b64_last_error) if chars
  * is invalid. Free with b64_alphabet_destroy. */
 b64_alphabet* b64_alphabet_create(const uint8_t chars[64], int padded);
+
+/* Alphabet flags: B64_FLAG_PADDED ('=' emitted by encode and required by
+ * decode) and B64_FLAG_CANONICAL (decode rejects non-zero unused bits in a
+ * partial final group, as stated at the top of this file). Not in the paper;
+ * b64_alphabet_create(chars, padded) is the same as flags = padded ?
+ * B64_FLAG_PADDED : 0. Returns NULL on invalid characters or unknown flag
+ * bits (b64_last_error). */
+#define B64_FLAG_PADDED 1
+#define B64_FLAG_CANONICAL 2
+b64_alphabet* b64_alphabet_create_flags(const uint8_t chars[64], int flags);
+
+/* The alphabet's flags, or B64_ERR_INVALID_ARGUMENT for NULL. */
+int b64_alphabet_flags(const b64_alphabet* a);
 
 /* Table 1 (A-Z a-z 0-9 + /), padded. Static; never destroy. */
 const b64_alphabet* b64_alphabet_standard(void);

@@ -29,6 +29,8 @@ _lib = None
 _P, _SZ, _I, _I64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int64
 SIGNATURES = {
     "b64_alphabet_create": (_P, [_P, _I]),
+    "b64_alphabet_create_flags": (_P, [_P, _I]),
+    "b64_alphabet_flags": (_I, [_P]),
     "b64_alphabet_standard": (_P, []),
     "b64_alphabet_url": (_P, []),
     "b64_alphabet_destroy": (None, [_P]),
@@ -119,9 +121,10 @@ class Alphabet:
         return cls(lib().b64_alphabet_url(), False)
 
     @classmethod
-    def create(cls, chars: bytes, padded: bool) -> "Alphabet":
+    def create(cls, chars: bytes, padded: bool, canonical: bool = False) -> "Alphabet":
+        """canonical: decode rejects non-zero unused bits in a partial final group."""
         buf = ctypes.create_string_buffer(bytes(chars), 64)
-        h = lib().b64_alphabet_create(buf, int(padded))
+        h = lib().b64_alphabet_create_flags(buf, (1 if padded else 0) | (2 if canonical else 0))
         if not h:
             raise B64Error(last_error())
         return cls(h, True)
@@ -130,6 +133,10 @@ class Alphabet:
         buf = ctypes.create_string_buffer(64)
         padded = lib().b64_alphabet_chars(self.handle, buf)
         return buf.raw, bool(padded)
+
+    @property
+    def canonical(self) -> bool:
+        return bool(lib().b64_alphabet_flags(self.handle) & 2)
 
     @property
     def padded(self) -> bool:

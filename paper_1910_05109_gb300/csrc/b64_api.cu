@@ -58,6 +58,7 @@ b64_alphabet make_builtin(bool url) {
     a.chars[62] = url ? '-' : '+';
     a.chars[63] = url ? '_' : '/';
     a.padded = url ? 0 : 1;
+    a.canonical = 0;
     fill_tables(&a);
     return a;
 }
@@ -134,6 +135,7 @@ int batch_tables(const char* fn, const b64_alphabet* const* alphabets, int n_alp
         t->enc[k] = a->enc;
         t->dec[k] = a->dec;
         t->padded[k] = a->padded;
+        t->canonical[k] = a->canonical;
     }
     return B64_SUCCESS;
 }
@@ -142,9 +144,13 @@ int batch_tables(const char* fn, const b64_alphabet* const* alphabets, int n_alp
 
 extern "C" {
 
-b64_alphabet* b64_alphabet_create(const uint8_t chars[64], int padded) {
+b64_alphabet* b64_alphabet_create_flags(const uint8_t chars[64], int flags) {
     if (!chars) {
         set_error(0, "b64_alphabet_create: chars is NULL");
+        return nullptr;
+    }
+    if (flags & ~(B64_FLAG_PADDED | B64_FLAG_CANONICAL)) {
+        set_error(0, "b64_alphabet_create_flags: unknown flag bits 0x%x", flags);
         return nullptr;
     }
     char why[160];
@@ -154,9 +160,19 @@ b64_alphabet* b64_alphabet_create(const uint8_t chars[64], int padded) {
     }
     b64_alphabet* a = new b64_alphabet;
     memcpy(a->chars, chars, 64);
-    a->padded = padded ? 1 : 0;
+    a->padded = (flags & B64_FLAG_PADDED) ? 1 : 0;
+    a->canonical = (flags & B64_FLAG_CANONICAL) ? 1 : 0;
     fill_tables(a);
     return a;
+}
+
+b64_alphabet* b64_alphabet_create(const uint8_t chars[64], int padded) {
+    return b64_alphabet_create_flags(chars, padded ? B64_FLAG_PADDED : 0);
+}
+
+int b64_alphabet_flags(const b64_alphabet* a) {
+    if (!a) return set_error(B64_ERR_INVALID_ARGUMENT, "b64_alphabet_flags: NULL alphabet");
+    return (a->padded ? B64_FLAG_PADDED : 0) | (a->canonical ? B64_FLAG_CANONICAL : 0);
 }
 
 const b64_alphabet* b64_alphabet_standard(void) { return &g_standard; }
@@ -209,7 +225,7 @@ int b64_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b64_alp
     if (overlaps(src, len, dst, b64_decoded_max_length(len)))
         return set_error(B64_ERR_INVALID_ARGUMENT, "b64_decode_async: src and dst overlap");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const cudaError_t e = launch_decode(src, len, dst, a->dec, a->padded, d_result, s);
+    const cudaError_t e = launch_decode(src, len, dst, a->dec, decode_flags(a), d_result, s);
     if (e != cudaSuccess)
         return set_error(B64_ERR_CUDA, "b64_decode_async: %s", cudaGetErrorString(e));
     return B64_SUCCESS;
@@ -320,8 +336,8 @@ static int mime_common(const char* fn, const uint8_t* src, size_t len, uint8_t* 
                          workspace_bytes, mime_workspace_bytes(len));
     if (overlaps(src, len, dst, b64_decoded_max_length(len)))
         return set_error(B64_ERR_INVALID_ARGUMENT, "%s: src and dst overlap", fn);
-    const cudaError_t e = launch_mime_decode(src, len, dst, a->dec, a->padded, d_result, workspace,
-                                             limit_ns, static_cast<cudaStream_t>(stream));
+    const cudaError_t e = launch_mime_decode(src, len, dst, a->dec, decode_flags(a), d_result,
+                                             workspace, limit_ns, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return set_error(B64_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
     return B64_SUCCESS;
 }

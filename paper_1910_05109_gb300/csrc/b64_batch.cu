@@ -525,11 +525,17 @@ __global__ void decode_batch_finalize_kernel(const uint8_t* __restrict__ src,
         }
     }
     if (padded ? (m % 4 != 0) : (m % 4 == 1)) e = m < e ? m : e;
+    const uint32_t d = tail - pads;
+    if (tabs.canonical[ai] && (d % 4 == 2 || d % 4 == 3)) {
+        // the last data character's bits that reach no output byte must be zero
+        const uint32_t last_v = v[d - 1], low = d % 4 == 2 ? 15u : 3u;
+        const uint64_t pos = body + d - 1;
+        if (!(last_v & kBad) && (last_v & low)) e = pos < e ? pos : e;
+    }
     if (e != kNoError) {
         results[i] = -int64_t(e) - 1;
         return;
     }
-    const uint32_t d = tail - pads;
     uint8_t* q = dst + dst_off[i];
     uint64_t o = body / 4 * 3;
     for (uint32_t j = 0; j < d; j += 4) {

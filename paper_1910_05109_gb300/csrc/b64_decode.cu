@@ -222,8 +222,9 @@ __device__ __forceinline__ uint32_t table_at(const DecodeTable& tab, uint32_t c)
 // smallest bad offset found in the body (kNoError if none): writes the
 // tail's bytes and returns the call's result (length, or -(first error + 1)).
 __device__ int64_t tail_result(const uint8_t* __restrict__ src, uint64_t m,
-                               uint8_t* __restrict__ dst, const DecodeTable& tab, int padded,
+                               uint8_t* __restrict__ dst, const DecodeTable& tab, int flags,
                                uint64_t err) {
+    const bool padded = flags & 1, canonical = flags & 2;
     const uint64_t body = body_length(m);
     const uint32_t last = m >= 1 ? src[m - 1] : 0u;
     uint32_t pads = 0;
@@ -245,10 +246,16 @@ __device__ int64_t tail_result(const uint8_t* __restrict__ src, uint64_t m,
         }
     }
     if (padded ? (m % 4 != 0) : (m % 4 == 1)) err = m < err ? m : err;
+    const uint32_t d = tail - pads;
+    if (canonical && (d % 4 == 2 || d % 4 == 3)) {
+        // the last data character's bits that reach no output byte must be zero
+        const uint32_t last_v = v[d - 1], low = d % 4 == 2 ? 15u : 3u;
+        const uint64_t pos = body + d - 1;
+        if (!(last_v & kBad) && (last_v & low)) err = pos < err ? pos : err;
+    }
     if (err != kNoError) return -int64_t(err) - 1;
     // Decode the tail's data characters: groups of four, then a short group
     // of k characters giving k-1 bytes (missing values taken as zero).
-    const uint32_t d = tail - pads;
     uint64_t o = body / 4 * 3;
     for (uint32_t j = 0; j < d; j += 4) {
         const uint32_t k = d - j < 4 ? d - j : 4;
@@ -264,11 +271,11 @@ __device__ int64_t tail_result(const uint8_t* __restrict__ src, uint64_t m,
 // One thread: the tail rules after the body kernels have folded their first
 // bad offset into *d_result.
 __global__ void decode_finalize_kernel(const uint8_t* __restrict__ src, uint64_t m,
-                                       uint8_t* __restrict__ dst, const __grid_constant__ DecodeTable tab, int padded,
+                                       uint8_t* __restrict__ dst, const __grid_constant__ DecodeTable tab, int flags,
                                        int64_t* d_result) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const uint64_t err = *reinterpret_cast<unsigned long long*>(d_result);
-    *d_result = tail_result(src, m, dst, tab, padded, err);
+    *d_result = tail_result(src, m, dst, tab, flags, err);
 }
 
 // Inputs of at most kSmallMax characters: the whole strict decode in one
@@ -286,7 +293,7 @@ constexpr uint64_t kSmallMax = kSmallPerCta * kSmallCtas;                   // 5
 template <bool kCluster>
 __global__ void __launch_bounds__(kSmallThreads)
     decode_small_kernel(const uint8_t* __restrict__ src, uint64_t m, uint8_t* __restrict__ dst,
-                        const __grid_constant__ DecodeTable tab, int padded, int64_t* d_result) {
+                        const __grid_constant__ DecodeTable tab, int flags, int64_t* d_result) {
     namespace cg = cooperative_groups;
     __shared__ __align__(16) uint8_t lut[256];
     __shared__ unsigned long long s_err;
@@ -331,7 +338,7 @@ __global__ void __launch_bounds__(kSmallThreads)
     if ((tid & 31) == 0 && wmin != kNoError) atomicMin(&s_err, (unsigned long long)wmin);
     if (!kCluster) {
         __syncthreads();
-        if (tid == 0) *d_result = tail_result(src, m, dst, tab, padded, s_err);
+        if (tid == 0) *d_result = tail_result(src, m, dst, tab, flags, s_err);
         return;
     }
     cg::cluster_group cluster = cg::this_cluster();
@@ -342,7 +349,7 @@ __global__ void __launch_bounds__(kSmallThreads)
             const uint64_t e = *cluster.map_shared_rank(&s_err, r);
             err = e < err ? e : err;
         }
-        *d_result = tail_result(src, m, dst, tab, padded, err);
+        *d_result = tail_result(src, m, dst, tab, flags, err);
     }
     cluster.sync();  // no block leaves while block 0 may still read its shared memory
 }
@@ -357,11 +364,11 @@ KernelSetup g_setup[64];
 }  // namespace
 
 cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const DecodeTable& tab,
-                          int padded, int64_t* d_result, cudaStream_t stream) {
+                          int flags, int64_t* d_result, cudaStream_t stream) {
     if (m <= kSmallMax) {
         const unsigned ctas = unsigned(m <= kSmallPerCta ? 1 : (m + kSmallPerCta - 1) / kSmallPerCta);
         if (ctas == 1) {
-            decode_small_kernel<false><<<1, kSmallThreads, 0, stream>>>(src, m, dst, tab, padded,
+            decode_small_kernel<false><<<1, kSmallThreads, 0, stream>>>(src, m, dst, tab, flags,
                                                                         d_result);
             return cudaGetLastError();
         }
@@ -376,7 +383,7 @@ cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const De
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, decode_small_kernel<true>, src, m, dst, tab, padded,
+        return cudaLaunchKernelEx(&cfg, decode_small_kernel<true>, src, m, dst, tab, flags,
                                   d_result);
     }
     const DeviceInfo& di = device_info();
@@ -418,7 +425,7 @@ cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const De
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    decode_finalize_kernel<<<1, 32, 0, stream>>>(src, m, dst, tab, padded, d_result);
+    decode_finalize_kernel<<<1, 32, 0, stream>>>(src, m, dst, tab, flags, d_result);
     return cudaGetLastError();
 }
 

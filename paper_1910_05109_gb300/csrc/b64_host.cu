@@ -207,14 +207,16 @@ int64_t b64_host_decode(b64_host_codec* c, const uint8_t* src, size_t len, uint8
         e = cudaStreamWaitEvent(c->st[s], c->ready, 0);
     b64_alphabet inner_a;
     memcpy(&inner_a, a, sizeof(inner_a));
-    inner_a.padded = 0;
+    inner_a.padded = 0;     // every '=' in an inner piece is an error
+    inner_a.canonical = 0;  // inner pieces hold whole groups only
     for (size_t i = 0; i < pieces && e == cudaSuccess; ++i) {
         const int s = int(i % size_t(c->n_streams));
         const size_t off = i * P, n = i < inner ? P : len - off;
         const b64_alphabet& pa = i < inner ? inner_a : *a;
         e = cudaMemcpyAsync(c->d_in[s], src + off, n, cudaMemcpyHostToDevice, c->st[s]);
         if (e == cudaSuccess)
-            e = launch_decode(c->d_in[s], n, c->d_out[s], pa.dec, pa.padded, c->d_res + i, c->st[s]);
+            e = launch_decode(c->d_in[s], n, c->d_out[s], pa.dec, decode_flags(&pa), c->d_res + i,
+                              c->st[s]);
         // The piece's output is copied whole (its bytes past an error are
         // unspecified, as for the single-buffer decode).
         if (e == cudaSuccess)

@@ -11,10 +11,14 @@
 // The alphabet handle behind the C ABI's opaque pointer.
 struct b64_alphabet {
     uint8_t chars[64];
-    int padded;
+    int padded;     // '=' emitted by encode, required by decode
+    int canonical;  // decode rejects non-zero unused bits in a partial final group
     b64::EncodeTable enc;
     b64::DecodeTable dec;
 };
+
+// The decode kernels' mode word: bit 0 padded, bit 1 canonical.
+inline int decode_flags(const b64_alphabet* a) { return (a->padded ? 1 : 0) | (a->canonical ? 2 : 0); }
 
 namespace b64 {
 
@@ -44,7 +48,7 @@ uint32_t encode_fault_flag(bool clear);
 // up to 8 blocks); larger inputs
 // start with a memset of *d_result, then the body kernel and the tail kernel.
 cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const DecodeTable& tab,
-                          int padded, int64_t* d_result, cudaStream_t stream);
+                          int flags, int64_t* d_result, cudaStream_t stream);
 
 // ---- batches (b64_batch.cu)
 constexpr int kMaxAlphabets = 4;
@@ -56,6 +60,7 @@ struct BatchTables {
     EncodeTable enc[kMaxAlphabets];
     DecodeTable dec[kMaxAlphabets];
     int padded[kMaxAlphabets];
+    int canonical[kMaxAlphabets];
 };
 
 struct BatchArgs {
@@ -88,7 +93,7 @@ size_t mime_workspace_bytes(uint64_t m);
 // Enqueues the whitespace-skipping strict decode; its bulk-copy waits give
 // up after wait_limit_ns.
 cudaError_t launch_mime_decode(const uint8_t* src, uint64_t m, uint8_t* dst,
-                               const DecodeTable& tab, int padded, int64_t* d_result,
+                               const DecodeTable& tab, int flags, int64_t* d_result,
                                void* workspace, uint64_t wait_limit_ns, cudaStream_t stream);
 // Self-test of the bounded wait: a barrier armed for a copy that never comes.
 cudaError_t launch_selftest_wait(int64_t* d_result, uint64_t wait_limit_ns, cudaStream_t stream);

@@ -281,7 +281,7 @@ __device__ __forceinline__ bool wait_copy(uint64_t* bar, uint32_t parity, uint64
 
 __global__ void __launch_bounds__(kThreads, 6)
     mime_decode_kernel(const uint8_t* __restrict__ src, uint64_t m, uint8_t* __restrict__ dst,
-                       const __grid_constant__ DecodeTable tab, int padded,
+                       const __grid_constant__ DecodeTable tab, int flags,
                        unsigned long long* __restrict__ status,
                        const unsigned long long* __restrict__ states,
                        const unsigned long long* __restrict__ totals, uint64_t nseg,
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, 6)
                             const uint32_t ch = (xr[j] >> (8 * i)) & 0xFFu;
                             const uint32_t rawpos = kRow * r + 128 * j + 4 * lane + i;
                             if (stop == 0xFFFFFFFFu || idx + qq < stop) stop = idx + qq;
-                            if (ch == '=' && padded) {
+                            if (ch == '=' && (flags & 1)) {
                                 if (eq_raw == 0xFFFFFFFFu || rawpos < eq_raw) {
                                     eq_raw = rawpos;
                                     eq_comp = idx + qq;
@@ -503,11 +503,15 @@ __global__ void __launch_bounds__(kThreads, 6)
 }
 
 // ---------------------------------------------------------------- 4. finalize
-// One thread: the padding and length rules on the compacted stream.
-__global__ void mime_finalize_kernel(uint64_t m, int padded,
+// One thread: the padding and length rules on the compacted stream (and, in
+// canonical mode, the unused bits of a partial final group's last data
+// character, found by walking back over the trailing whitespace and padding).
+__global__ void mime_finalize_kernel(const uint8_t* __restrict__ src, uint64_t m, int flags,
+                                     const __grid_constant__ DecodeTable tab,
                                      const unsigned long long* __restrict__ status,
                                      int64_t* __restrict__ d_result) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const bool padded = flags & 1, canonical = flags & 2;
     if (status[4]) {
         *d_result = B64_E_TIMEOUT;
         return;
@@ -524,6 +528,20 @@ __global__ void mime_finalize_kernel(uint64_t m, int padded,
         else err = status[1] < err ? status[1] : err;
     }
     if (padded ? (mc % 4 != 0) : (mc % 4 == 1)) err = m < err ? m : err;
+    const uint64_t d = mc - pads;
+    if (canonical && (d % 4 == 2 || d % 4 == 3)) {
+        // raw position of data character d - 1: the (pads + 1)-th data
+        // character from the end
+        uint64_t p = m, seen = 0;
+        while (p > 0) {
+            const uint32_t ch = src[--p];
+            if (ch == '\r' || ch == '\n' || ch == ' ') continue;
+            if (++seen == pads + 1) break;
+        }
+        const uint32_t v = (tab.w[src[p] >> 2] >> (8 * (src[p] & 3))) & 0xFFu;
+        const uint32_t low = d % 4 == 2 ? 15u : 3u;
+        if (!(v & kBad) && (v & low)) err = p < err ? p : err;
+    }
     *d_result = err != kNoError ? -int64_t(err) - 1 : int64_t(bytes_for(mc - pads));
 }
 
@@ -569,7 +587,7 @@ size_t mime_workspace_bytes(uint64_t m) {
 }
 
 cudaError_t launch_mime_decode(const uint8_t* src, uint64_t m, uint8_t* dst,
-                               const DecodeTable& tab, int padded, int64_t* d_result,
+                               const DecodeTable& tab, int flags, int64_t* d_result,
                                void* workspace, uint64_t wait_limit_ns, cudaStream_t st) {
     const uint64_t nseg = (m + kSeg - 1) / kSeg;
     const uint64_t nblk = (nseg + kSegsPerBlock - 1) / kSegsPerBlock;
@@ -595,11 +613,11 @@ cudaError_t launch_mime_decode(const uint8_t* src, uint64_t m, uint8_t* dst,
         const uint64_t need = (nseg + kWarps - 1) / kWarps;
         if (need < grid) grid = need;
         mime_decode_kernel<<<unsigned(grid), kThreads, 0, st>>>(
-            src, m, dst, tab, padded, status, states, totals, nseg, wait_limit_ns);
+            src, m, dst, tab, flags, status, states, totals, nseg, wait_limit_ns);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    mime_finalize_kernel<<<1, 32, 0, st>>>(m, padded, status, d_result);
+    mime_finalize_kernel<<<1, 32, 0, st>>>(src, m, flags, tab, status, d_result);
     return cudaGetLastError();
 }
 

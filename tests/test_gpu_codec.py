@@ -126,7 +126,9 @@ def test_config1_single_buffer(b64, orc, alphabets):
 @pytest.mark.parametrize("dst_off", [0, 1, 4, 13])
 def test_alignment_classes(b64, orc, alphabets, src_off, dst_off):
     alph, chars, padded = alphabets["std"]
-    for i, n in enumerate((0, 1, 2, 5, 1000, 3 * ENC_CHUNK + 2, 50_001)):
+    # up to 512 KiB of characters decode in one launch; 600,001 bytes take the
+    # three-launch path (the generic kernel when src or dst is unaligned)
+    for i, n in enumerate((0, 1, 2, 5, 1000, 3 * ENC_CHUNK + 2, 50_001, 600_001)):
         data = wl.random_bytes(n, seed=2000 + i)
         want = orc.encode(data, chars, padded)
         assert np.array_equal(gpu_encode(b64, data, alph, src_off, dst_off), want), n
@@ -150,12 +152,14 @@ def test_injected_invalid_byte_offsets(b64, orc, alphabets):
             assert want == -(off + 1)
 
 
-def test_invalid_bytes_at_chunk_edges(b64, orc, alphabets):
+@pytest.mark.parametrize("chunks", [4, 200])  # one-launch decode / body kernel + tail kernel
+def test_invalid_bytes_at_chunk_edges(b64, orc, alphabets, chunks):
     alph, chars, padded = alphabets["std"]
-    text = orc.encode(wl.random_bytes(3 * DEC_CHUNK, seed=12), chars, padded)  # 4*DEC_CHUNK chars
+    text = orc.encode(wl.random_bytes(chunks // 4 * 3 * DEC_CHUNK, seed=12), chars, padded)
     m = text.size
     positions = [0, 1, 15, 16, DEC_CHUNK - 1, DEC_CHUNK, DEC_CHUNK + 1, 2 * DEC_CHUNK - 5,
-                 3 * DEC_CHUNK + 7, m - 7, m - 6, m - 5, m - 4, m - 3, m - 2, m - 1]
+                 3 * DEC_CHUNK + 7, m - DEC_CHUNK - 1, m - DEC_CHUNK, m - 7, m - 6, m - 5,
+                 m - 4, m - 3, m - 2, m - 1]
     values = [0x00, 0x0A, 0x20, 0x2D, 0x3D, 0x5F, 0x7F, 0x80, 0xC3, 0xFF]
     for p in positions:
         for v in values:

@@ -163,6 +163,26 @@ int b64_mime_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b6
                           int64_t* d_result, void* workspace, size_t workspace_bytes,
                           void* stream);
 
+/* Many MIME documents in one launch sequence (not in the paper): document i
+ * is src[src_off[i] .. src_off[i+1]) (device int64[n+1], any alignment),
+ * decoded exactly as b64_mime_decode_async decodes it, to dst + dst_off[i]
+ * (room for b64_decoded_max_length of its length, e.g. from
+ * b64_batch_offsets with decode != 0), with alphabets[alph_id[i]] (alph_id
+ * NULL: alphabet 0); results[i] receives its length or -(offset+1), offset
+ * within the document. workspace: device memory of
+ * b64_mime_batch_workspace_size(n, src_off[n] - src_off[0]) bytes, 8-byte
+ * aligned; if the documents' total turns out larger than the size was
+ * computed for, every results[i] becomes B64_E_INVAL and nothing else is
+ * written. Five launches on `stream` (a memset, count, per-document scan,
+ * decode, result), no waits between blocks. Returns B64_SUCCESS or an error
+ * code; n == 0 enqueues nothing. */
+size_t b64_mime_batch_workspace_size(int64_t n, uint64_t total_bytes);
+
+int b64_mime_decode_batch(const uint8_t* src, const int64_t* src_off, int64_t n, uint8_t* dst,
+                          const int64_t* dst_off, const b64_alphabet* const* alphabets,
+                          int n_alphabets, const uint8_t* alph_id, int64_t* results,
+                          void* workspace, size_t workspace_bytes, void* stream);
+
 /* ---------------------------------------------------------------- batches
  * Many independent strings in one launch sequence (a per-string results
  * kernel or error-word memset, one persistent tile kernel, and for decode a

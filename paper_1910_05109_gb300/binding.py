@@ -47,6 +47,8 @@ SIGNATURES = {
     "b64_decode_batch_noalloc": (_I, [_P, _P, _I64, _P, _P, _P, _I, _P, _P, _I, _P]),
     "b64_mime_workspace_size": (_SZ, [_SZ]),
     "b64_mime_decode_async": (_I, [_P, _SZ, _P, _P, _P, _P, _SZ, _P]),
+    "b64_mime_batch_workspace_size": (_SZ, [_I64, ctypes.c_uint64]),
+    "b64_mime_decode_batch": (_I, [_P, _P, _I64, _P, _P, _P, _I, _P, _P, _P, _SZ, _P]),
     "b64_selftest_wait_timeout": (_I, [_P, ctypes.c_uint64, _P]),
     "b64_server_create": (_P, [_SZ, _I, _SZ, _P, _I]),
     "b64_server_submit": (_I, [_P, ctypes.c_uint64, _I, _I, _P, _SZ, _P, _SZ]),
@@ -405,3 +407,30 @@ class HostCodec:
             self.close()
         except Exception:
             pass
+
+
+def mime_decode_batch(src: torch.Tensor, src_off: torch.Tensor, dst: torch.Tensor,
+                      dst_off: torch.Tensor, alphabets, alph_id: torch.Tensor | None = None,
+                      results: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """Enqueues the whitespace-skipping strict decode of every document;
+    returns the device int64 results."""
+    src_off = _dev(src_off, torch.int64, "src_off")
+    dst_off = _dev(dst_off, torch.int64, "dst_off")
+    n = src_off.numel() - 1
+    arr, na = _alphabet_array(alphabets)
+    if results is None:
+        results = torch.empty(max(n, 1), dtype=torch.int64, device=src_off.device)
+    if workspace is None and n > 0:
+        total = int((src_off[-1] - src_off[0]).item())
+        size = lib().b64_mime_batch_workspace_size(n, total)
+        workspace = torch.empty(max(size, 8), dtype=torch.uint8, device=src_off.device)
+    aid = 0 if alph_id is None else _dev(alph_id, torch.uint8, "alph_id").data_ptr()
+    rc = lib().b64_mime_decode_batch(
+        src.data_ptr() if src.numel() else 0, src_off.data_ptr(), n,
+        dst.data_ptr() if dst.numel() else 0, dst_off.data_ptr(), arr, na, aid,
+        results.data_ptr(), workspace.data_ptr() if workspace is not None else 0,
+        workspace.numel() if workspace is not None else 0, _stream_ptr(stream))
+    if rc != B64_SUCCESS:
+        raise B64Error(last_error())
+    return results[:n]

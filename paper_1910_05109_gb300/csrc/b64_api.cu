@@ -349,6 +349,34 @@ int b64_mime_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b6
                        workspace_bytes, kWaitLimitNs, stream);
 }
 
+size_t b64_mime_batch_workspace_size(int64_t n, uint64_t total_bytes) {
+    return n > 0 ? mime_batch_workspace_bytes(n, total_bytes) : 0;
+}
+
+int b64_mime_decode_batch(const uint8_t* src, const int64_t* src_off, int64_t n, uint8_t* dst,
+                          const int64_t* dst_off, const b64_alphabet* const* alphabets,
+                          int n_alphabets, const uint8_t* alph_id, int64_t* results,
+                          void* workspace, size_t workspace_bytes, void* stream) {
+    const char* fn = "b64_mime_decode_batch";
+    if (n < 0) return set_error(B64_ERR_INVALID_ARGUMENT, "%s: n < 0", fn);
+    BatchTables tabs;
+    const int rc = batch_tables(fn, alphabets, n_alphabets, &tabs);
+    if (rc != B64_SUCCESS) return rc;
+    if (n == 0) return B64_SUCCESS;
+    if (!src_off || !dst_off || !results || !workspace)
+        return set_error(B64_ERR_INVALID_ARGUMENT, "%s: NULL pointer argument", fn);
+    if (reinterpret_cast<uintptr_t>(workspace) & 7u)
+        return set_error(B64_ERR_INVALID_ARGUMENT, "%s: workspace not 8-byte aligned", fn);
+    if (workspace_bytes < mime_batch_workspace_bytes(n, 0))
+        return set_error(B64_ERR_INVALID_ARGUMENT, "%s: workspace holds %zu bytes, at least %zu needed",
+                         fn, workspace_bytes, mime_batch_workspace_bytes(n, 0));
+    BatchArgs a{src, src_off, n, dst, dst_off, alph_id, results};
+    const cudaError_t e = launch_mime_decode_batch(a, tabs, workspace, workspace_bytes,
+                                                   static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return set_error(B64_ERR_CUDA, "%s: %s", fn, cudaGetErrorString(e));
+    return B64_SUCCESS;
+}
+
 int b64_selftest_wait_timeout(int64_t* d_result, uint64_t wait_limit_ns, void* stream) {
     if (!d_result || (reinterpret_cast<uintptr_t>(d_result) & 7u))
         return set_error(B64_ERR_INVALID_ARGUMENT,

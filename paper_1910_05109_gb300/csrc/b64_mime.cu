@@ -279,6 +279,165 @@ __device__ __forceinline__ bool wait_copy(uint64_t* bar, uint32_t parity, uint64
     }
 }
 
+// One staged segment (its bytes at buf[kLead ..], the tail past the document's
+// end reading as spaces), decoded by one warp: the row-by-row compaction of
+// the 6-bit values, the status words (first bad byte and first '=', offsets
+// relative to raw_base / the document), the whole groups and the output bytes
+// whose second character the segment holds. P: data characters before the
+// segment in its document; prev_last: the last data byte before it.
+__device__ __forceinline__ void decode_segment(uint8_t* buf, const uint8_t* lut, int flags,
+                                               int lane, uint64_t P, uint32_t prev_last,
+                                               uint64_t raw_base, uint8_t* __restrict__ out_doc,
+                                               unsigned long long* st3) {
+    const uint64_t base = raw_base;
+    // ---- row by row (512 bytes = four sub-rows of 128; lane L takes word L
+    //      of each): translate, count, scan, and store each value at
+    //      buf[kLead + s + index], s = P mod 4, so that whole groups of four
+    //      start on 16-byte boundaries. A value's position never passes its
+    //      raw byte by more than 3, so the next row is read before any lane
+    //      writes (the only raw bytes a row's stores can reach).
+    const uint32_t s = uint32_t(P & 3);
+    const uint32_t* raw32 = reinterpret_cast<const uint32_t*>(buf + kLead);
+    uint32_t bad_raw = 0xFFFFFFFFu, eq_raw = 0xFFFFFFFFu, eq_comp = 0xFFFFFFFFu,
+             stop = 0xFFFFFFFFu;
+    uint32_t rowbase = 0;
+    uint32_t xr[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) xr[j] = raw32[32 * j + lane];
+#pragma unroll 1
+    for (int r = 0; r < kRows; ++r) {
+        uint32_t xn[4] = {0u, 0u, 0u, 0u};
+        if (r + 1 < kRows) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) xn[j] = raw32[128 * (r + 1) + 32 * j + lane];
+        }
+        uint32_t T[4], dm[4], badm[4], C = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t x = xr[j];
+            const uint32_t t0 = lut[x & 0xFFu], t1 = lut[(x >> 8) & 0xFFu];
+            const uint32_t t2 = lut[(x >> 16) & 0xFFu], t3 = lut[x >> 24];
+            T[j] = t0 | (t1 << 8) | (t2 << 16) | (t3 << 24);
+            const uint32_t b7 = T[j] & 0x80808080u, b6 = (T[j] << 1) & 0x80808080u;
+            dm[j] = ~(b7 & b6) & 0x80808080u;  // not whitespace (0xC0)
+            badm[j] = b7 & ~b6;                // bad or '=' (0x80)
+            C |= uint32_t(__popc(dm[j])) << (8 * j);
+        }
+        // four 8-bit counts scanned at once (a sub-row holds at most 128)
+        const uint32_t incl = warp_scan_add32(C, lane);
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t ex = incl - C;
+        __syncwarp();  // row r and row r + 1 are read everywhere before any lane writes
+        uint32_t base = rowbase;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t idx = base + ((ex >> (8 * j)) & 0xFFu);
+            uint8_t* out = buf + kLead + s + idx;
+            uint32_t q = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t v = (T[j] >> (8 * i)) & 0xFFu;
+                if (v < kSpace) {
+                    out[q] = uint8_t(v);
+                    ++q;
+                }
+            }
+            if (badm[j]) {  // rare: the word's first bad byte and first '='
+                uint32_t qq = 0;
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t v = (T[j] >> (8 * i)) & 0xFFu;
+                    if (v == kSpace) continue;
+                    if (v & kBad) {
+                        const uint32_t ch = (xr[j] >> (8 * i)) & 0xFFu;
+                        const uint32_t rawpos = kRow * r + 128 * j + 4 * lane + i;
+                        if (stop == 0xFFFFFFFFu || idx + qq < stop) stop = idx + qq;
+                        if (ch == '=' && (flags & 1)) {
+                            if (eq_raw == 0xFFFFFFFFu || rawpos < eq_raw) {
+                                eq_raw = rawpos;
+                                eq_comp = idx + qq;
+                            }
+                        } else if (bad_raw == 0xFFFFFFFFu || rawpos < bad_raw) {
+                            bad_raw = rawpos;
+                        }
+                        break;
+                    }
+                    ++qq;
+                }
+            }
+            base += (tot >> (8 * j)) & 0xFFu;
+        }
+        rowbase = base;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) xr[j] = xn[j];
+    }
+    const uint32_t count = rowbase;
+    stop = __reduce_min_sync(0xffffffffu, stop);
+    if (stop != 0xFFFFFFFFu) {
+        bad_raw = __reduce_min_sync(0xffffffffu, bad_raw);
+        eq_raw = __reduce_min_sync(0xffffffffu, eq_raw);
+        eq_comp = __reduce_min_sync(0xffffffffu, eq_comp);
+        if (lane == 0) {
+            if (bad_raw != 0xFFFFFFFFu) atomicMin(st3 + 0, base + bad_raw);
+            if (eq_raw != 0xFFFFFFFFu) {
+                atomicMin(st3 + 1, base + eq_raw);
+                atomicMin(st3 + 2, P + eq_comp);
+            }
+        }
+    }
+
+    // ---- whole groups in place: 16 values -> 12 bytes. The value of data
+    //      character P + i sits at buf[kLead + s + i], so the group holding P
+    //      starts at buf[kLead] and group g at buf[kLead + 16 g]; the value
+    //      before P goes to buf[kLead + s - 1]
+    if (lane == 0 && s) buf[kLead + s - 1] = lut[prev_last];
+    __syncwarp();
+    const uint32_t jend = stop < count ? stop : count;
+    const uint64_t ob = bytes_for(P), oe = bytes_for(P + jend);
+    const uint32_t nout = uint32_t(oe > ob ? oe - ob : 0);
+    const uint32_t skip = s ? s - 1 : 0;  // bytes of the first group written before P
+    const uint32_t ngroups = (s + jend + 15) / 16;
+#pragma unroll 1
+    for (uint32_t g0 = 0; g0 < ngroups; g0 += 32) {
+        const uint32_t g = g0 + lane;
+        uint3 o = make_uint3(0, 0, 0);
+        if (g < ngroups) {
+            const uint4 c = *reinterpret_cast<const uint4*>(buf + kLead + 16 * g);
+            o = pack4x24(decode4_values(c.x), decode4_values(c.y), decode4_values(c.z),
+                         decode4_values(c.w));
+        }
+        __syncwarp();  // this round's values are read before any lane overwrites them
+        if (g < ngroups) {
+            uint32_t* ow = reinterpret_cast<uint32_t*>(buf + 12 * g);
+            ow[0] = o.x;
+            ow[1] = o.y;
+            ow[2] = o.z;
+        }
+    }
+    __syncwarp();
+    // copy out buf[skip .. skip + nout): 16-byte stores at aligned addresses,
+    // each built from two aligned 16-byte shared loads; bytes at the edges
+    uint8_t* q = out_doc + ob;
+    const uint32_t head = uint32_t((16 - (reinterpret_cast<uintptr_t>(q) & 15)) & 15);
+    const uint32_t h = head < nout ? head : nout;
+    if (lane < int(h)) q[lane] = buf[skip + lane];
+    const uint32_t body = (nout - h) & ~15u;
+    const uint32_t o0 = skip + h, sw = (o0 & 15) >> 2, sb = 8 * (o0 & 3);
+    for (uint32_t i = lane; i < body / 16; i += 32) {
+        const uint32_t A = (o0 & ~15u) + 16 * i;
+        const uint4 a = *reinterpret_cast<const uint4*>(buf + A);
+        const uint4 b = *reinterpret_cast<const uint4*>(buf + A + 16);
+        const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        uint32_t v[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k)  // words sw .. sw + 4 (sw is the same in every lane)
+            v[k] = sw == 0 ? w[k] : sw == 1 ? w[k + 1] : sw == 2 ? w[k + 2] : w[(k + 3) & 7];
+        *reinterpret_cast<uint4*>(q + h + 16 * i) =
+            make_uint4(__funnelshift_r(v[0], v[1], sb), __funnelshift_r(v[1], v[2], sb),
+                       __funnelshift_r(v[2], v[3], sb), __funnelshift_r(v[3], v[4], sb));
+    }
+    for (uint32_t i = h + body + lane; i < nout; i += 32) q[i] = buf[skip + i];
+}
+
 __global__ void __launch_bounds__(kThreads, 6)
     mime_decode_kernel(const uint8_t* __restrict__ src, uint64_t m, uint8_t* __restrict__ dst,
                        const __grid_constant__ DecodeTable tab, int flags,
@@ -352,180 +511,30 @@ __global__ void __launch_bounds__(kThreads, 6)
         const uint64_t P = st_count(blk) + st_count(pre);
         const uint32_t prev_last = st_flag(pre) ? st_last(pre) : st_flag(blk) ? st_last(blk) : 0u;
 
-        // ---- row by row (512 bytes = four sub-rows of 128; lane L takes word L
-        //      of each): translate, count, scan, and store each value at
-        //      buf[kLead + s + index], s = P mod 4, so that whole groups of four
-        //      start on 16-byte boundaries. A value's position never passes its
-        //      raw byte by more than 3, so the next row is read before any lane
-        //      writes (the only raw bytes a row's stores can reach).
-        const uint32_t s = uint32_t(P & 3);
-        const uint32_t* raw32 = reinterpret_cast<const uint32_t*>(buf + kLead);
-        uint32_t bad_raw = 0xFFFFFFFFu, eq_raw = 0xFFFFFFFFu, eq_comp = 0xFFFFFFFFu,
-                 stop = 0xFFFFFFFFu;
-        uint32_t rowbase = 0;
-        uint32_t xr[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) xr[j] = raw32[32 * j + lane];
-#pragma unroll 1
-        for (int r = 0; r < kRows; ++r) {
-            uint32_t xn[4] = {0u, 0u, 0u, 0u};
-            if (r + 1 < kRows) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) xn[j] = raw32[128 * (r + 1) + 32 * j + lane];
-            }
-            uint32_t T[4], dm[4], badm[4], C = 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t x = xr[j];
-                const uint32_t t0 = lut[x & 0xFFu], t1 = lut[(x >> 8) & 0xFFu];
-                const uint32_t t2 = lut[(x >> 16) & 0xFFu], t3 = lut[x >> 24];
-                T[j] = t0 | (t1 << 8) | (t2 << 16) | (t3 << 24);
-                const uint32_t b7 = T[j] & 0x80808080u, b6 = (T[j] << 1) & 0x80808080u;
-                dm[j] = ~(b7 & b6) & 0x80808080u;  // not whitespace (0xC0)
-                badm[j] = b7 & ~b6;                // bad or '=' (0x80)
-                C |= uint32_t(__popc(dm[j])) << (8 * j);
-            }
-            // four 8-bit counts scanned at once (a sub-row holds at most 128)
-            const uint32_t incl = warp_scan_add32(C, lane);
-            const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-            const uint32_t ex = incl - C;
-            __syncwarp();  // row r and row r + 1 are read everywhere before any lane writes
-            uint32_t base = rowbase;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t idx = base + ((ex >> (8 * j)) & 0xFFu);
-                uint8_t* out = buf + kLead + s + idx;
-                uint32_t q = 0;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const uint32_t v = (T[j] >> (8 * i)) & 0xFFu;
-                    if (v < kSpace) {
-                        out[q] = uint8_t(v);
-                        ++q;
-                    }
-                }
-                if (badm[j]) {  // rare: the word's first bad byte and first '='
-                    uint32_t qq = 0;
-                    for (int i = 0; i < 4; ++i) {
-                        const uint32_t v = (T[j] >> (8 * i)) & 0xFFu;
-                        if (v == kSpace) continue;
-                        if (v & kBad) {
-                            const uint32_t ch = (xr[j] >> (8 * i)) & 0xFFu;
-                            const uint32_t rawpos = kRow * r + 128 * j + 4 * lane + i;
-                            if (stop == 0xFFFFFFFFu || idx + qq < stop) stop = idx + qq;
-                            if (ch == '=' && (flags & 1)) {
-                                if (eq_raw == 0xFFFFFFFFu || rawpos < eq_raw) {
-                                    eq_raw = rawpos;
-                                    eq_comp = idx + qq;
-                                }
-                            } else if (bad_raw == 0xFFFFFFFFu || rawpos < bad_raw) {
-                                bad_raw = rawpos;
-                            }
-                            break;
-                        }
-                        ++qq;
-                    }
-                }
-                base += (tot >> (8 * j)) & 0xFFu;
-            }
-            rowbase = base;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) xr[j] = xn[j];
-        }
-        const uint32_t count = rowbase;
-        stop = __reduce_min_sync(0xffffffffu, stop);
-        if (stop != 0xFFFFFFFFu) {
-            bad_raw = __reduce_min_sync(0xffffffffu, bad_raw);
-            eq_raw = __reduce_min_sync(0xffffffffu, eq_raw);
-            eq_comp = __reduce_min_sync(0xffffffffu, eq_comp);
-            if (lane == 0) {
-                if (bad_raw != 0xFFFFFFFFu) atomicMin(status + 0, base + bad_raw);
-                if (eq_raw != 0xFFFFFFFFu) {
-                    atomicMin(status + 1, base + eq_raw);
-                    atomicMin(status + 2, P + eq_comp);
-                }
-            }
-        }
-
-        // ---- whole groups in place: 16 values -> 12 bytes. The value of data
-        //      character P + i sits at buf[kLead + s + i], so the group holding P
-        //      starts at buf[kLead] and group g at buf[kLead + 16 g]; the value
-        //      before P goes to buf[kLead + s - 1]
-        if (lane == 0 && s) buf[kLead + s - 1] = lut[prev_last];
-        __syncwarp();
-        const uint32_t jend = stop < count ? stop : count;
-        const uint64_t ob = bytes_for(P), oe = bytes_for(P + jend);
-        const uint32_t nout = uint32_t(oe > ob ? oe - ob : 0);
-        const uint32_t skip = s ? s - 1 : 0;  // bytes of the first group written before P
-        const uint32_t ngroups = (s + jend + 15) / 16;
-#pragma unroll 1
-        for (uint32_t g0 = 0; g0 < ngroups; g0 += 32) {
-            const uint32_t g = g0 + lane;
-            uint3 o = make_uint3(0, 0, 0);
-            if (g < ngroups) {
-                const uint4 c = *reinterpret_cast<const uint4*>(buf + kLead + 16 * g);
-                o = pack4x24(decode4_values(c.x), decode4_values(c.y), decode4_values(c.z),
-                             decode4_values(c.w));
-            }
-            __syncwarp();  // this round's values are read before any lane overwrites them
-            if (g < ngroups) {
-                uint32_t* ow = reinterpret_cast<uint32_t*>(buf + 12 * g);
-                ow[0] = o.x;
-                ow[1] = o.y;
-                ow[2] = o.z;
-            }
-        }
-        __syncwarp();
-        // copy out buf[skip .. skip + nout): 16-byte stores at aligned addresses,
-        // each built from two aligned 16-byte shared loads; bytes at the edges
-        uint8_t* q = dst + ob;
-        const uint32_t head = uint32_t((16 - (reinterpret_cast<uintptr_t>(q) & 15)) & 15);
-        const uint32_t h = head < nout ? head : nout;
-        if (lane < int(h)) q[lane] = buf[skip + lane];
-        const uint32_t body = (nout - h) & ~15u;
-        const uint32_t o0 = skip + h, sw = (o0 & 15) >> 2, sb = 8 * (o0 & 3);
-        for (uint32_t i = lane; i < body / 16; i += 32) {
-            const uint32_t A = (o0 & ~15u) + 16 * i;
-            const uint4 a = *reinterpret_cast<const uint4*>(buf + A);
-            const uint4 b = *reinterpret_cast<const uint4*>(buf + A + 16);
-            const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-            uint32_t v[5];
-#pragma unroll
-            for (int k = 0; k < 5; ++k)  // words sw .. sw + 4 (sw is the same in every lane)
-                v[k] = sw == 0 ? w[k] : sw == 1 ? w[k + 1] : sw == 2 ? w[k + 2] : w[(k + 3) & 7];
-            *reinterpret_cast<uint4*>(q + h + 16 * i) =
-                make_uint4(__funnelshift_r(v[0], v[1], sb), __funnelshift_r(v[1], v[2], sb),
-                           __funnelshift_r(v[2], v[3], sb), __funnelshift_r(v[3], v[4], sb));
-        }
-        for (uint32_t i = h + body + lane; i < nout; i += 32) q[i] = buf[skip + i];
+        decode_segment(buf, lut, flags, lane, P, prev_last, base, dst, status);
         by_copy = next_by_copy;
     }
 }
 
 // ---------------------------------------------------------------- 4. finalize
-// One thread: the padding and length rules on the compacted stream (and, in
+// The padding and length rules on a document's compacted stream (and, in
 // canonical mode, the unused bits of a partial final group's last data
 // character, found by walking back over the trailing whitespace and padding).
-__global__ void mime_finalize_kernel(const uint8_t* __restrict__ src, uint64_t m, int flags,
-                                     const __grid_constant__ DecodeTable tab,
-                                     const unsigned long long* __restrict__ status,
-                                     int64_t* __restrict__ d_result) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// whole: the document's state (data characters, last data byte); st3: its
+// status words (first bad byte, first '=' raw and compacted).
+__device__ int64_t mime_result(const uint8_t* __restrict__ src, uint64_t m, int flags,
+                               const DecodeTable& tab, uint64_t whole,
+                               const unsigned long long* __restrict__ st3) {
     const bool padded = flags & 1, canonical = flags & 2;
-    if (status[4]) {
-        *d_result = B64_E_TIMEOUT;
-        return;
-    }
-    const uint64_t whole = status[5];
     const uint64_t mc = st_count(whole);  // data characters
     const uint32_t last = st_last(whole);
-    uint64_t err = status[0];
+    uint64_t err = st3[0];
     uint64_t pads = 0;
-    if (padded && status[2] != kNoError) {
-        const uint64_t qe = status[2];
+    if (padded && st3[2] != kNoError) {
+        const uint64_t qe = st3[2];
         const bool ok = qe + 1 == mc || (qe + 2 == mc && last == '=');
         if (ok) pads = mc - qe;
-        else err = status[1] < err ? status[1] : err;
+        else err = st3[1] < err ? st3[1] : err;
     }
     if (padded ? (mc % 4 != 0) : (mc % 4 == 1)) err = m < err ? m : err;
     const uint64_t d = mc - pads;
@@ -542,7 +551,236 @@ __global__ void mime_finalize_kernel(const uint8_t* __restrict__ src, uint64_t m
         const uint32_t low = d % 4 == 2 ? 15u : 3u;
         if (!(v & kBad) && (v & low)) err = p < err ? p : err;
     }
-    *d_result = err != kNoError ? -int64_t(err) - 1 : int64_t(bytes_for(mc - pads));
+    return err != kNoError ? -int64_t(err) - 1 : int64_t(bytes_for(mc - pads));
+}
+
+// One thread: the result of the single-document decode.
+__global__ void mime_finalize_kernel(const uint8_t* __restrict__ src, uint64_t m, int flags,
+                                     const __grid_constant__ DecodeTable tab,
+                                     const unsigned long long* __restrict__ status,
+                                     int64_t* __restrict__ d_result) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (status[4]) {
+        *d_result = B64_E_TIMEOUT;
+        return;
+    }
+    *d_result = mime_result(src, m, flags, tab, status[5], status);
+}
+
+// ---------------------------------------------------------------- batched documents
+// Document d is bytes [src_off[d], src_off[d+1]) of src, decoded to
+// dst + dst_off[d] with its own alphabet, exactly as the single-document call
+// decodes it. Its ceil(len / kSeg) segments keep their state words at slots
+// doc_slot(d) + k, doc_slot(d) = (src_off[d] - src_off[0]) / kSeg + d: the
+// slot ranges of consecutive documents never overlap (the next document's
+// first slot lies at least ceil(len / kSeg) further on), so no scan over the
+// documents is needed and a slot's document is found by a search. Launch
+// sequence: memset of the documents' status words, count (all segments), one
+// warp per document scanning its segments, decode (all segments), one thread
+// per document for the result. Documents start anywhere, so segments are
+// staged with aligned loads and a funnel shift (no bulk copies, no waits).
+__device__ __forceinline__ uint64_t doc_slot(const int64_t* __restrict__ src_off, int64_t d) {
+    return uint64_t(src_off[d] - src_off[0]) / kSeg + uint64_t(d);
+}
+
+// Warp-cooperative: the largest d in [0, n) with doc_slot(d) <= g (n >= 1).
+__device__ int64_t warp_find_doc(const int64_t* __restrict__ src_off, int64_t n, uint64_t g,
+                                 int lane) {
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t probe = lo + int64_t(lane) * step;
+        const bool le = probe < hi && doc_slot(src_off, probe) <= g;
+        const uint32_t mask = __ballot_sync(0xffffffffu, le);
+        const int k = 31 - __clz(mask);  // lane 0 always holds (probe = lo)
+        const int64_t nlo = lo + int64_t(k) * step;
+        hi = nlo + step < hi ? nlo + step : hi;
+        lo = nlo;
+    }
+    return lo;
+}
+
+// 16 bytes at p + off (bytes at or past len read as spaces). Aligned 16-byte
+// loads and a funnel shift when both aligned blocks lie inside [lo, hi) (the
+// batch's input); byte loads otherwise.
+__device__ __forceinline__ uint4 load_chunk_any(const uint8_t* p, uint32_t off, uint32_t len,
+                                                const uint8_t* lo, const uint8_t* hi) {
+    const uint8_t* q = p + off;
+    if (off + 16 <= len) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(q);
+        const uint32_t sh = uint32_t(a & 15);
+        if (sh == 0) return *reinterpret_cast<const uint4*>(q);
+        const uint8_t* a0 = reinterpret_cast<const uint8_t*>(a & ~uintptr_t(15));
+        if (a0 >= lo && a0 + 32 <= hi) {
+            const uint4 x = *reinterpret_cast<const uint4*>(a0);
+            const uint4 y = *reinterpret_cast<const uint4*>(a0 + 16);
+            const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+            const uint32_t sw = sh >> 2, sb = 8 * (sh & 3);
+            uint32_t v[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+                v[k] = sw == 0 ? w[k] : sw == 1 ? w[k + 1] : sw == 2 ? w[k + 2] : w[(k + 3) & 7];
+            return make_uint4(__funnelshift_r(v[0], v[1], sb), __funnelshift_r(v[1], v[2], sb),
+                              __funnelshift_r(v[2], v[3], sb), __funnelshift_r(v[3], v[4], sb));
+        }
+    }
+    uint4 v;
+    uint8_t* b = reinterpret_cast<uint8_t*>(&v);
+    for (int k = 0; k < 16; ++k) b[k] = off + k < len ? q[k] : uint8_t(' ');
+    return v;
+}
+
+struct DocSeg {
+    int64_t d;         // document
+    uint64_t k;        // segment within it
+    uint32_t len;      // bytes of the segment
+    const uint8_t* p;  // its first byte
+};
+
+// Slot g's document segment; false for a slot no segment uses.
+__device__ __forceinline__ bool doc_segment(const uint8_t* src, const int64_t* __restrict__ src_off,
+                                            int64_t n, uint64_t g, int lane, DocSeg* ds) {
+    const int64_t d = warp_find_doc(src_off, n, g, lane);
+    const uint64_t k = g - doc_slot(src_off, d);
+    const uint64_t len = uint64_t(src_off[d + 1] - src_off[d]);
+    if (k * kSeg >= len) return false;
+    ds->d = d;
+    ds->k = k;
+    ds->len = uint32_t(len - k * kSeg < kSeg ? len - k * kSeg : kSeg);
+    ds->p = src + src_off[d] + k * kSeg;
+    return true;
+}
+
+__device__ __forceinline__ uint64_t doc_slots(const int64_t* __restrict__ src_off, int64_t n) {
+    return uint64_t(src_off[n] - src_off[0]) / kSeg + uint64_t(n) + 1;
+}
+
+__global__ void __launch_bounds__(kCountThreads)
+    mime_count_docs_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
+                           int64_t n, unsigned long long* __restrict__ states, uint64_t slot_cap) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t nslots = doc_slots(src_off, n);
+    if (nslots > slot_cap) return;  // workspace too small: the results say so
+    const uint64_t gw = (uint64_t(blockIdx.x) * kCountThreads + threadIdx.x) >> 5;
+    const uint64_t GW = (uint64_t(gridDim.x) * kCountThreads) >> 5;
+    const uint8_t* lo = src + src_off[0];
+    const uint8_t* hi = src + src_off[n];
+    for (uint64_t g = gw; g < nslots; g += GW) {
+        DocSeg ds;
+        if (!doc_segment(src, src_off, n, g, lane, &ds)) continue;
+        uint32_t count = 0, key = 0;
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const uint32_t off = kRow * r + 16 * lane;
+            count += chunk_count(load_chunk_any(ds.p, off, ds.len, lo, hi), off, &key);
+        }
+        count = __reduce_add_sync(0xffffffffu, count);
+        key = __reduce_max_sync(0xffffffffu, key);
+        if (lane == 0) states[g] = make_state(key != 0, key & 0xFFu, count);
+    }
+}
+
+// One warp per document: its segments' states become prefixes (data
+// characters and last data byte before the segment, within the document);
+// doc_state[d] = the whole document's.
+__global__ void __launch_bounds__(256)
+    mime_scan_docs_kernel(const int64_t* __restrict__ src_off, int64_t n,
+                          unsigned long long* __restrict__ states,
+                          unsigned long long* __restrict__ doc_state, uint64_t slot_cap) {
+    const int lane = threadIdx.x & 31;
+    if (doc_slots(src_off, n) > slot_cap) return;
+    const int64_t gw = (int64_t(blockIdx.x) * 256 + threadIdx.x) >> 5;
+    const int64_t GW = (int64_t(gridDim.x) * 256) >> 5;
+    for (int64_t d = gw; d < n; d += GW) {
+        const uint64_t first = doc_slot(src_off, d);
+        const uint64_t segs = (uint64_t(src_off[d + 1] - src_off[d]) + kSeg - 1) / kSeg;
+        uint64_t carry = 0, carry_key = 0;  // key: (segment + 1) << 8 | last byte
+        for (uint64_t c = 0; c < segs; c += 32) {
+            const uint64_t k = c + lane;
+            const uint64_t st = k < segs ? states[first + k] : 0;
+            const uint64_t cnt = st_count(st);
+            const uint64_t key = st_flag(st) ? ((k + 1) << 8) | st_last(st) : 0;
+            uint64_t incl = cnt, kincl = key;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                const uint64_t uk = __shfl_up_sync(0xffffffffu, kincl, o);
+                if (lane >= o) {
+                    incl += u;
+                    kincl = uk > kincl ? uk : kincl;
+                }
+            }
+            uint64_t kex = __shfl_up_sync(0xffffffffu, kincl, 1);
+            if (lane == 0) kex = 0;
+            kex = kex > carry_key ? kex : carry_key;
+            if (k < segs) states[first + k] = make_state(kex != 0, uint32_t(kex & 0xFFu), carry + incl - cnt);
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+            const uint64_t top = __shfl_sync(0xffffffffu, kincl, 31);
+            carry_key = top > carry_key ? top : carry_key;
+        }
+        if (lane == 0) doc_state[d] = make_state(carry_key != 0, uint32_t(carry_key & 0xFFu), carry);
+    }
+}
+
+constexpr int kDocWarps = 4;
+
+__global__ void __launch_bounds__(32 * kDocWarps, 6)
+    mime_decode_docs_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
+                            int64_t n, uint8_t* __restrict__ dst,
+                            const int64_t* __restrict__ dst_off,
+                            const __grid_constant__ BatchTables tabs,
+                            const uint8_t* __restrict__ alph_id,
+                            unsigned long long* __restrict__ status_docs,
+                            const unsigned long long* __restrict__ states, uint64_t slot_cap) {
+    __shared__ uint8_t luts[kMaxAlphabets][256];  // 0..63, 0x80, kSpace
+    __shared__ __align__(16) uint8_t bufs[kDocWarps][kBuf];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < kMaxAlphabets * 64; i += 32 * kDocWarps)
+        reinterpret_cast<uint32_t*>(luts)[i] = tabs.dec[i / 64].w[i % 64];
+    __syncthreads();
+    if (tid < kMaxAlphabets) luts[tid]['\r'] = luts[tid]['\n'] = luts[tid][' '] = uint8_t(kSpace);
+    __syncthreads();
+    const uint64_t nslots = doc_slots(src_off, n);
+    if (nslots > slot_cap) return;
+    const uint8_t* lo = src + src_off[0];
+    const uint8_t* hi = src + src_off[n];
+    uint8_t* buf = bufs[warp];
+    const uint64_t GW = uint64_t(gridDim.x) * kDocWarps;
+    for (uint64_t g = uint64_t(blockIdx.x) * kDocWarps + warp; g < nslots; g += GW) {
+        DocSeg ds;
+        if (!doc_segment(src, src_off, n, g, lane, &ds)) continue;
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const uint32_t off = kRow * r + 16 * lane;
+            *reinterpret_cast<uint4*>(buf + kLead + off) = load_chunk_any(ds.p, off, ds.len, lo, hi);
+        }
+        __syncwarp();
+        const uint64_t pre = states[g];
+        const int a = alph_id ? (alph_id[ds.d] & (kMaxAlphabets - 1)) : 0;
+        const int flags = (tabs.padded[a] ? 1 : 0) | (tabs.canonical[a] ? 2 : 0);
+        decode_segment(buf, luts[a], flags, lane, st_count(pre), st_flag(pre) ? st_last(pre) : 0u,
+                       ds.k * kSeg, dst + dst_off[ds.d], status_docs + 3 * ds.d);
+        __syncwarp();  // the buffer is restaged for the next segment
+    }
+}
+
+__global__ void mime_finalize_docs_kernel(const uint8_t* __restrict__ src,
+                                          const int64_t* __restrict__ src_off, int64_t n,
+                                          const __grid_constant__ BatchTables tabs,
+                                          const uint8_t* __restrict__ alph_id,
+                                          const unsigned long long* __restrict__ status_docs,
+                                          const unsigned long long* __restrict__ doc_state,
+                                          uint64_t slot_cap, int64_t* __restrict__ results) {
+    const int64_t d = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (d >= n) return;
+    if (doc_slots(src_off, n) > slot_cap) {
+        results[d] = B64_E_INVAL;
+        return;
+    }
+    const int a = alph_id ? (alph_id[d] & (kMaxAlphabets - 1)) : 0;
+    const int flags = (tabs.padded[a] ? 1 : 0) | (tabs.canonical[a] ? 2 : 0);
+    results[d] = mime_result(src + src_off[d], uint64_t(src_off[d + 1] - src_off[d]), flags,
+                             tabs.dec[a], doc_state[d], status_docs + 3 * d);
 }
 
 // The bounded wait of the decode kernel on a bulk copy that is never issued:
@@ -623,6 +861,41 @@ cudaError_t launch_mime_decode(const uint8_t* src, uint64_t m, uint8_t* dst,
 
 cudaError_t launch_selftest_wait(int64_t* d_result, uint64_t wait_limit_ns, cudaStream_t st) {
     selftest_wait_kernel<<<1, 32, 0, st>>>(d_result, wait_limit_ns);
+    return cudaGetLastError();
+}
+
+size_t mime_batch_workspace_bytes(int64_t n, uint64_t total_bytes) {
+    const uint64_t slots = total_bytes / kSeg + uint64_t(n) + 1;
+    return 8 * (4 * size_t(n) + size_t(slots));
+}
+
+cudaError_t launch_mime_decode_batch(const BatchArgs& a, const BatchTables& tabs, void* workspace,
+                                     size_t workspace_bytes, cudaStream_t st) {
+    if (a.n <= 0) return cudaSuccess;
+    // [status: 3 words per document][document states: n][segment slots]
+    unsigned long long* status_docs = static_cast<unsigned long long*>(workspace);
+    unsigned long long* doc_state = status_docs + 3 * a.n;
+    unsigned long long* states = doc_state + a.n;
+    const uint64_t words = workspace_bytes / 8;
+    const uint64_t slot_cap = words > 4 * uint64_t(a.n) ? words - 4 * uint64_t(a.n) : 0;
+    cudaError_t e = cudaMemsetAsync(status_docs, 0xFF, 3 * size_t(a.n) * sizeof(uint64_t), st);
+    if (e != cudaSuccess) return e;
+    const DeviceInfo& di = device_info();
+    mime_count_docs_kernel<<<unsigned(di.sm_count * 4), kCountThreads, 0, st>>>(a.src, a.src_off, a.n,
+                                                                           states, slot_cap);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const uint64_t scan_blocks = (uint64_t(a.n) + 7) / 8;
+    const unsigned sb = unsigned(scan_blocks < uint64_t(di.sm_count) * 8 ? scan_blocks : di.sm_count * 8);
+    mime_scan_docs_kernel<<<sb, 256, 0, st>>>(a.src_off, a.n, states, doc_state, slot_cap);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    mime_decode_docs_kernel<<<unsigned(di.sm_count * 6), 32 * kDocWarps, 0, st>>>(
+        a.src, a.src_off, a.n, a.dst, a.dst_off, tabs, a.alph_id, status_docs, states, slot_cap);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    mime_finalize_docs_kernel<<<unsigned((a.n + 255) / 256), 256, 0, st>>>(
+        a.src, a.src_off, a.n, tabs, a.alph_id, status_docs, doc_state, slot_cap, a.results);
     return cudaGetLastError();
 }
 

@@ -614,14 +614,17 @@ __device__ __forceinline__ uint4 load_chunk_any(const uint8_t* p, uint32_t off, 
         if (a0 >= lo && a0 + 32 <= hi) {
             const uint4 x = *reinterpret_cast<const uint4*>(a0);
             const uint4 y = *reinterpret_cast<const uint4*>(a0 + 16);
-            const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
-            const uint32_t sw = sh >> 2, sb = 8 * (sh & 3);
-            uint32_t v[5];
-#pragma unroll
-            for (int k = 0; k < 5; ++k)
-                v[k] = sw == 0 ? w[k] : sw == 1 ? w[k + 1] : sw == 2 ? w[k + 2] : w[(k + 3) & 7];
-            return make_uint4(__funnelshift_r(v[0], v[1], sb), __funnelshift_r(v[1], v[2], sb),
-                              __funnelshift_r(v[2], v[3], sb), __funnelshift_r(v[3], v[4], sb));
+            const uint32_t sb = 8 * (sh & 3);
+            auto f = [sb](uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t e) {
+                return make_uint4(__funnelshift_r(a, b, sb), __funnelshift_r(b, c, sb),
+                                  __funnelshift_r(c, d, sb), __funnelshift_r(d, e, sb));
+            };
+            switch (sh >> 2) {  // the same in every lane of the segment
+                case 0: return f(x.x, x.y, x.z, x.w, y.x);
+                case 1: return f(x.y, x.z, x.w, y.x, y.y);
+                case 2: return f(x.z, x.w, y.x, y.y, y.z);
+                default: return f(x.w, y.x, y.y, y.z, y.w);
+            }
         }
     }
     uint4 v;
@@ -655,7 +658,7 @@ __device__ __forceinline__ uint64_t doc_slots(const int64_t* __restrict__ src_of
     return uint64_t(src_off[n] - src_off[0]) / kSeg + uint64_t(n) + 1;
 }
 
-__global__ void __launch_bounds__(kCountThreads)
+__global__ void __launch_bounds__(kCountThreads, 4)
     mime_count_docs_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
                            int64_t n, unsigned long long* __restrict__ states, uint64_t slot_cap) {
     const int lane = threadIdx.x & 31;
@@ -803,7 +806,7 @@ struct Occ {
     std::once_flag once;
     int ctas = 1;
 };
-Occ g_occ[64];
+Occ g_occ[64], g_cd_occ[64], g_dd_occ[64];
 
 template <class K>
 int occupancy(K kernel, int threads, Occ& occ) {
@@ -881,8 +884,9 @@ cudaError_t launch_mime_decode_batch(const BatchArgs& a, const BatchTables& tabs
     cudaError_t e = cudaMemsetAsync(status_docs, 0xFF, 3 * size_t(a.n) * sizeof(uint64_t), st);
     if (e != cudaSuccess) return e;
     const DeviceInfo& di = device_info();
-    mime_count_docs_kernel<<<unsigned(di.sm_count * 4), kCountThreads, 0, st>>>(a.src, a.src_off, a.n,
-                                                                           states, slot_cap);
+    const int cd = occupancy(mime_count_docs_kernel, kCountThreads, g_cd_occ[di.device & 63]);
+    mime_count_docs_kernel<<<unsigned(di.sm_count * cd), kCountThreads, 0, st>>>(
+        a.src, a.src_off, a.n, states, slot_cap);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint64_t scan_blocks = (uint64_t(a.n) + 7) / 8;
@@ -890,7 +894,8 @@ cudaError_t launch_mime_decode_batch(const BatchArgs& a, const BatchTables& tabs
     mime_scan_docs_kernel<<<sb, 256, 0, st>>>(a.src_off, a.n, states, doc_state, slot_cap);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    mime_decode_docs_kernel<<<unsigned(di.sm_count * 6), 32 * kDocWarps, 0, st>>>(
+    const int dd = occupancy(mime_decode_docs_kernel, 32 * kDocWarps, g_dd_occ[di.device & 63]);
+    mime_decode_docs_kernel<<<unsigned(di.sm_count * dd), 32 * kDocWarps, 0, st>>>(
         a.src, a.src_off, a.n, a.dst, a.dst_off, tabs, a.alph_id, status_docs, states, slot_cap);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

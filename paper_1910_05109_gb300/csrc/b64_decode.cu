@@ -108,6 +108,17 @@ __device__ __forceinline__ uint4 load_stream16(const uint8_t* p) {
     return v;
 }
 
+// Programmatic dependent launch: the body and tail kernels may start while
+// the kernel before them finishes; this waits until that kernel has
+// completed and its writes are visible (and makes this kernel's own
+// completion imply it).
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// One thread: *d_err = "no error" before the body kernel folds offsets into it.
+__global__ void result_init_kernel(unsigned long long* d_err) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *d_err = kNoError;
+}
+
 __device__ __forceinline__ int first_bad_in(uint32_t w, const uint8_t* lut) {
     for (int i = 0; i < 4; ++i)
         if (lut[(w >> (8 * i)) & 0xFFu] & kBad) return i;
@@ -124,6 +135,7 @@ __global__ void __launch_bounds__(kThreads)
     uint8_t* sout = smem + size_t(warp) * kStagesOut * kChunkOut;
     if (tid < 64) reinterpret_cast<uint32_t*>(lut)[tid] = tab.w[tid];
     __syncthreads();
+    wait_prior_grid();  // *d_err has been initialised
 
     const uint64_t n_chunks = body / kChunkIn;
     const uint64_t GW = uint64_t(gridDim.x) * kWarps;
@@ -207,6 +219,7 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ __align__(16) uint8_t lut[256];
     if (threadIdx.x < 64) reinterpret_cast<uint32_t*>(lut)[threadIdx.x] = tab.w[threadIdx.x];
     __syncthreads();
+    wait_prior_grid();  // *d_err has been initialised
     const bool al4 = (reinterpret_cast<uintptr_t>(src) & 3u) == 0;
     const uint64_t first =
         decode_quads_plain(src, 0, body / 4, dst, lut, uint64_t(blockIdx.x) * blockDim.x + threadIdx.x,
@@ -273,6 +286,7 @@ __device__ int64_t tail_result(const uint8_t* __restrict__ src, uint64_t m,
 __global__ void decode_finalize_kernel(const uint8_t* __restrict__ src, uint64_t m,
                                        uint8_t* __restrict__ dst, const __grid_constant__ DecodeTable tab, int flags,
                                        int64_t* d_result) {
+    wait_prior_grid();  // the body kernel has folded in its offsets
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const uint64_t err = *reinterpret_cast<unsigned long long*>(d_result);
     *d_result = tail_result(src, m, dst, tab, flags, err);
@@ -354,6 +368,24 @@ __global__ void __launch_bounds__(kSmallThreads)
     cluster.sync();  // no block leaves while block 0 may still read its shared memory
 }
 
+// Launches `kernel` as a programmatic dependent of the previous kernel on
+// the stream (it calls wait_prior_grid before using that kernel's results).
+template <class... KArgs, class... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                             cudaStream_t stream, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 struct KernelSetup {
     std::once_flag once;
     cudaError_t err = cudaSuccess;
@@ -389,8 +421,11 @@ cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const De
     const DeviceInfo& di = device_info();
     const uint64_t body = body_length(m);
     unsigned long long* d_err = reinterpret_cast<unsigned long long*>(d_result);
-    // the body kernels fold their first bad offsets into *d_result: start at "none"
-    const cudaError_t e0 = cudaMemsetAsync(d_result, 0xFF, sizeof(int64_t), stream);
+    // the body kernels fold their first bad offsets into *d_result: start at
+    // "none"; the body and tail kernels are programmatic dependents, so their
+    // launches overlap the kernel before them
+    result_init_kernel<<<1, 32, 0, stream>>>(d_err);
+    const cudaError_t e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
     if (body > 0) {
         const bool aligned =
@@ -411,22 +446,24 @@ cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const De
             const uint64_t want = (n_chunks + kWarps - 1) / kWarps;
             uint64_t grid = uint64_t(di.sm_count) * ks.ctas_per_sm;
             if (want < grid) grid = want > 0 ? want : 1;
-            decode_fast_kernel<<<unsigned(grid), kThreads, kSmem, stream>>>(src, body, dst, tab,
-                                                                             d_err);
+            const cudaError_t e1 = launch_dependent(decode_fast_kernel, unsigned(grid), kThreads,
+                                                    kSmem, stream, src, body, dst, tab, d_err);
+            if (e1 != cudaSuccess) return e1;
         } else {
             const uint64_t quads = body / 4;
             uint64_t grid = (quads + kThreads - 1) / kThreads;
             const uint64_t cap = uint64_t(di.sm_count) * 8;
             if (grid > cap) grid = cap;
             if (grid == 0) grid = 1;
-            decode_generic_kernel<<<unsigned(grid), kThreads, 0, stream>>>(src, body, dst, tab,
-                                                                             d_err);
+            const cudaError_t e1 = launch_dependent(decode_generic_kernel, unsigned(grid), kThreads,
+                                                    0, stream, src, body, dst, tab, d_err);
+            if (e1 != cudaSuccess) return e1;
         }
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    decode_finalize_kernel<<<1, 32, 0, stream>>>(src, m, dst, tab, flags, d_result);
-    return cudaGetLastError();
+    return launch_dependent(decode_finalize_kernel, 1, 32, 0, stream, src, m, dst, tab, flags,
+                            d_result);
 }
 
 

@@ -108,3 +108,54 @@ def test_package_never_imports_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.lower() or f == "workloads.py" and \
                     "import oracle" not in text, f
+
+
+def test_alphabet_flags(L):
+    from paper_1910_05109_gb300 import binding as b
+    std = b.Alphabet.standard().chars()[0]
+    a = b.Alphabet.create(std, True, canonical=True)
+    assert a.padded and a.canonical
+    assert L.b64_alphabet_flags(a.handle) == 3
+    c = b.Alphabet.create(std, False, canonical=True)
+    assert not c.padded and c.canonical and L.b64_alphabet_flags(c.handle) == 2
+    assert L.b64_alphabet_flags(L.b64_alphabet_url()) == 0
+    assert L.b64_alphabet_flags(None) == b.B64_ERR_INVALID_ARGUMENT
+    buf = ctypes.create_string_buffer(std, 64)
+    assert L.b64_alphabet_create_flags(buf, 4) is None      # unknown flag bit
+    assert "flag" in b.last_error()
+    h = L.b64_alphabet_create(buf, 1)                       # same as flags = padded
+    assert L.b64_alphabet_flags(h) == 1
+    L.b64_alphabet_destroy(h)
+
+
+def test_new_entry_points_reject_bad_arguments_without_gpu(L):
+    from paper_1910_05109_gb300 import binding as b
+    std = L.b64_alphabet_standard()
+    arr = (ctypes.c_void_p * 1)(std)
+    # batched MIME: n < 0, no alphabets, NULL pointers, workspace too small or misaligned
+    assert L.b64_mime_decode_batch(None, None, -1, None, None, arr, 1, None, None, None, 0,
+                                   None) == b.B64_ERR_INVALID_ARGUMENT
+    assert L.b64_mime_decode_batch(None, None, 4, None, None, None, 0, None, None, None, 0,
+                                   None) == b.B64_ERR_INVALID_ARGUMENT
+    assert L.b64_mime_decode_batch(None, None, 0, None, None, arr, 1, None, None, None, 0,
+                                   None) == b.B64_SUCCESS          # n == 0: nothing to do
+    assert L.b64_mime_decode_batch(16, None, 4, 16, 64, arr, 1, None, 128, 256, 4096,
+                                   None) == b.B64_ERR_INVALID_ARGUMENT
+    assert L.b64_mime_decode_batch(16, 64, 4, 16, 64, arr, 1, None, 128, 260, 4096,
+                                   None) == b.B64_ERR_INVALID_ARGUMENT
+    assert "aligned" in b.last_error()
+    assert L.b64_mime_decode_batch(16, 64, 4, 16, 64, arr, 1, None, 128, 256, 8,
+                                   None) == b.B64_ERR_INVALID_ARGUMENT
+    assert "workspace" in b.last_error()
+    assert L.b64_mime_batch_workspace_size(0, 1000) == 0
+    assert L.b64_mime_batch_workspace_size(4, 4096 * 10) == 8 * (4 * 4 + 10 + 4 + 1)
+    # bounded-wait self-test: NULL or misaligned result, limit out of range
+    assert L.b64_selftest_wait_timeout(None, 1000, None) == b.B64_ERR_INVALID_ARGUMENT
+    assert L.b64_selftest_wait_timeout(12, 1000, None) == b.B64_ERR_INVALID_ARGUMENT
+    assert L.b64_selftest_wait_timeout(16, 0, None) == b.B64_ERR_INVALID_ARGUMENT
+    assert L.b64_selftest_wait_timeout(16, 3_000_000_000, None) == b.B64_ERR_INVALID_ARGUMENT
+    # host codec: NULL codec or alphabet, NULL buffers
+    assert L.b64_host_encode(None, 16, 10, 16, std) == b.B64_E_INVAL
+    assert L.b64_host_decode(None, 16, 10, 16, std) == b.B64_E_INVAL
+    assert L.b64_host_codec_device_bytes(None) == 0
+    L.b64_host_codec_destroy(None)

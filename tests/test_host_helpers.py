@@ -1,0 +1,59 @@
+"""Host-side helpers that need no GPU: the synthetic input recipes and the
+serving driver's host output ring."""
+import numpy as np
+
+from paper_1910_05109_gb300 import serve
+from paper_1910_05109_gb300 import workloads as wl
+
+
+def test_mime_wrap_lines():
+    text = np.frombuffer(b"A" * 1000, np.uint8)
+    w = wl.mime_wrap(text).tobytes()
+    lines = w.split(b"\r\n")
+    assert all(len(x) == 76 for x in lines[:-1]) and len(lines[-1]) == 1000 - 76 * 13
+    assert not w.endswith(b"\r\n")
+    assert wl.mime_wrap(np.zeros(0, np.uint8)).size == 0
+    assert wl.mime_wrap(np.frombuffer(b"A" * 76, np.uint8)).tobytes() == b"A" * 76
+
+
+def test_insert_spaces_keeps_the_data():
+    text = np.frombuffer(b"QUJDREVG" * 50, np.uint8)
+    w = wl.insert_spaces(text, seed=3, count=100)
+    assert w.size == text.size + 100
+    kept = w[~np.isin(w, np.frombuffer(b"\r\n ", np.uint8))]
+    assert np.array_equal(kept, text)
+
+
+def test_varlen_lengths_recipe():
+    lengths = wl.lognormal_lengths(100_000, 2, 1024, 1.5, 1, 1 << 20)
+    assert lengths.min() >= 1 and lengths.max() <= 1 << 20
+    assert set(np.unique(lengths % 3)) == {0, 1, 2}          # every padding case occurs
+    assert 700 < np.median(lengths) < 1400
+
+
+def test_poisson_requests_recipe():
+    t, ops, sizes, pick = serve.poisson_requests(20_000, 2.0, 4, 5)
+    assert 38_000 < t.size < 42_000 and np.all(np.diff(t) >= 0) and t[-1] <= 2.0
+    assert 0.57 < ops.mean() < 0.63                          # 60% decode
+    assert sizes.min() >= 4 and sizes.max() <= 16 << 20
+    assert np.all(sizes[ops == 1] % 4 == 0)                  # whole groups for decode
+    assert 30_000 < np.median(sizes) < 55_000                # median about 40 KiB
+    assert np.all((pick >= 0) & (pick < 1))
+
+
+def test_host_ring_wraps_and_releases_in_order():
+    ring = serve.HostRing(1000)
+    a = ring.take(0, 300)
+    b = ring.take(1, 300)
+    c = ring.take(2, 300)
+    assert (a, b, c) == (0, 320, 640)
+    assert ring.take(3, 100) is None                         # full
+    ring.release(1)                                          # out of order: nothing freed yet
+    assert ring.take(3, 100) is None
+    ring.release(0)                                          # frees 0 and 1
+    assert ring.take(3, 300) == 0                            # wraps to the front
+    assert ring.take(4, 400) is None
+    ring.release(2)
+    ring.release(3)
+    assert not ring.live and ring.take(5, 960) == 0
+    assert ring.take(6, 2000) is None                        # larger than the ring

@@ -45,6 +45,7 @@ SIZES = [0, 1, 2, 3, 4, 11, 12, 13, P - 1, P, P + 1, P + 2, 2 * P, 5 * P + 7, 17
 
 
 def host_buf(n, pinned):
+    """Page-locked (torch pin_memory) or pageable (numpy) host buffer."""
     if pinned:
         return torch.empty(max(n, 1), dtype=torch.uint8).pin_memory()[:n]
     return np.empty(n, np.uint8)
@@ -54,19 +55,21 @@ def as_np(b):
     return b.numpy() if isinstance(b, torch.Tensor) else b
 
 
-@pytest.mark.parametrize("pinned", [True, False])
+# (input pinned, output pinned): page-locked, pageable and mixed pairs
+@pytest.mark.parametrize("pinned", [(True, True), (False, False), (True, False), (False, True)])
 def test_host_roundtrip_sizes(b64, orc, codecs, pinned):
+    pin_in, pin_out = pinned
     for streams, codec in codecs.items():
         for k, (a, chars, padded) in enumerate(alphabets(b64, orc)):
             for n in SIZES:
                 data = wl.random_bytes(n, 100 + n + k)
-                src = host_buf(n, pinned)
+                src = host_buf(n, pin_in)
                 as_np(src)[:] = data
                 want = orc.encode(data, chars, padded)
-                txt = host_buf(want.size, pinned)
+                txt = host_buf(want.size, pin_out)
                 assert codec.encode(src, txt, a) == want.size
                 assert np.array_equal(as_np(txt), want), (streams, n)
-                out = host_buf(b64.decoded_max_length(want.size), pinned)
+                out = host_buf(b64.decoded_max_length(want.size), pin_in)
                 assert codec.decode(txt, out, a) == n
                 assert np.array_equal(as_np(out)[:n], data), (streams, n)
 
@@ -110,28 +113,33 @@ def test_host_decode_seams_strict(b64, orc, codecs):
     assert checked == 2 * 2 * len(seam_cases()) and errors > checked // 2
 
 
-def test_host_large_default_piece(b64, orc):
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_large_default_piece(b64, orc, pinned):
     """64 MiB + 5 bytes with the default pieces and streams, one bad byte in
-    the decode input at a seeded offset past the first piece."""
+    the decode input at a seeded offset past the first piece; page-locked
+    and pageable buffers."""
     n = (64 << 20) + 5
     codec = b64.HostCodec()
     try:
         assert codec.device_bytes() > 0
         data = wl.random_bytes(n, 3)
-        src = torch.from_numpy(data).pin_memory()
+        src = host_buf(n, pinned)
+        as_np(src)[:] = data
         m = b64.encoded_length(n, True)
-        txt = torch.empty(m, dtype=torch.uint8).pin_memory()
+        txt = host_buf(m, pinned)
         assert codec.encode(src, txt) == m
         want = orc.encode(data)
-        assert np.array_equal(txt.numpy(), want)
-        out = torch.empty(b64.decoded_max_length(m), dtype=torch.uint8).pin_memory()
-        assert codec.decode(txt, out) == n
-        assert torch.equal(out[:n], src)
+        assert np.array_equal(as_np(txt), want)
+        out = host_buf(b64.decoded_max_length(m), pinned)
+        for _ in range(2):  # a second call on the same codec
+            as_np(out)[:] = 0
+            assert codec.decode(txt, out) == n
+            assert np.array_equal(as_np(out)[:n], data)
         g = wl.rng(4)
         pos = int(g.integers(50 << 20, m - 8))
-        txt[pos] = 0xC3
+        as_np(txt)[pos] = 0xC3
         r = codec.decode(txt, out)
-        assert r == -(pos + 1) == orc.decode(txt.numpy())[0]
+        assert r == -(pos + 1) == orc.decode(as_np(txt))[0]
     finally:
         codec.close()
 

@@ -50,7 +50,7 @@ def peaks() -> dict:
 # The source files each profiled kernel is built from.
 KERNEL_SOURCES = {
     "encode_tma_kernel": ("b64_encode.cu", "b64_device.cuh"),
-    "decode_fast_kernel": ("b64_decode.cu", "b64_device.cuh"),
+    "decode_body_kernel": ("b64_decode.cu", "b64_device.cuh"),
 }
 
 
@@ -379,7 +379,7 @@ def finish(args, v):
     dominant = "decode" if dec_avg >= enc_avg else "encode"
     dom_ms = dec_avg if dominant == "decode" else enc_avg
     achieved = (dec_alg if dominant == "decode" else enc_alg) / (dom_ms / 1e3) / 1e9
-    kname = "decode_fast_kernel" if dominant == "decode" else "encode_tma_kernel"
+    kname = "decode_body_kernel" if dominant == "decode" else "encode_tma_kernel"
     tr = profiled_traffic(kname)
     traffic = None
     if tr is not None:
@@ -412,7 +412,8 @@ def finish(args, v):
             "api": "b64_host_encode + b64_host_decode, page-locked host buffers",
             "host_codec": {"piece_bytes": args.piece_bytes or 48 << 20,
                            "streams": args.host_streams or 3}},
-        "gpu_launches": 6 * K,
+        # per step and table: encode; decode = result init, body, tail
+        "gpu_launches": 8 * K,
         "clocks": clocks.summary(),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -727,7 +728,7 @@ def run_table2(args):
         enc_graph_ms = timed(ge.replay, max(2, reps // 100)) / 100
         cp = torch.empty_like(text)
         mc_ms = timed(lambda: cp.copy_(text), reps)
-        per_dec = 1 if m <= (512 << 10) else 2  # one-launch decode up to 512 KiB
+        per_dec = 1 if m <= (512 << 10) else 3  # one launch up to 512 KiB, else init, body, tail
         g_reps = max(2, reps // 100)
         launches += per_dec * (reps + 100 * g_reps) + (reps + 100 * g_reps)  # timed calls
         rows.append({"file": name, "bytes": n, "base64_bytes": m,

@@ -396,8 +396,8 @@ const char* b64_last_error(void) { return t_last_error.c_str(); }
 int b64_device_fault_flag(int clear) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return set_error(B64_ERR_CUDA, "b64_device_fault_flag: %s", cudaGetErrorString(e));
-    uint32_t f = encode_fault_flag(clear != 0) | mime_fault_flag(clear != 0) |
-                 batch_fault_flag(clear != 0);
+    uint32_t f = encode_fault_flag(clear != 0) | decode_fault_flag(clear != 0) |
+                 mime_fault_flag(clear != 0) | batch_fault_flag(clear != 0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(B64_ERR_CUDA, "b64_device_fault_flag: %s", cudaGetErrorString(e));
     return int(f);

@@ -13,15 +13,17 @@
 // a bad byte looks for its exact offset (cold path) and folds it into the
 // call's result with an atomic minimum.
 //
-// Fast path (src and dst 16-byte aligned): a persistent grid in which every
-// warp works alone on "warp chunks" of 32 x kUnits x 16 characters. Each lane
-// loads its kUnits 16-byte units of the next chunk straight into registers
-// (coalesced: 512 contiguous bytes per warp instruction, streamed past L1)
-// while it decodes the current one, writes its 12-byte results into a ring
-// of kOutStages shared-memory buffers, and lane 0 stores each buffer with a
-// bulk (TMA) store. The error vote and the cold-path search are warp-wide, so
-// no block-wide barrier is taken inside the loop. The body (all but the last
-// 2 to 5 characters) is done by this kernel; a one-thread kernel then checks
+// Body path (src and dst 16-byte aligned): a persistent grid in which every
+// warp works alone on "warp chunks" of 32 x kUnits x 16 characters (1 KiB).
+// Lane 0 of each warp keeps kStagesIn bulk (TMA) copies of its next chunks in
+// flight into a per-warp ring of shared-memory buffers; the warp decodes a
+// landed chunk from shared memory (16 characters a lane), writes the 12-byte
+// results into one of kStagesOut output buffers, and lane 0 stores that
+// buffer with a bulk store and refills the input buffer. At 16 warps a block
+// and one block an SM, 128 KiB of input is in flight per SM at 32 registers a
+// thread. The error vote and the cold-path search are warp-wide, so no
+// block-wide barrier is taken inside the loop. The body (all but the last 2
+// to 5 characters) is done by this kernel; a one-thread kernel then checks
 // the padding and length rules on the tail, decodes it and writes the call's
 // result.
 #include <mutex>
@@ -31,10 +33,13 @@
 #include "b64_internal.h"
 
 #ifndef B64_DEC_WARPS
-#define B64_DEC_WARPS 4
+#define B64_DEC_WARPS 16
 #endif
 #ifndef B64_DEC_UNITS
-#define B64_DEC_UNITS 8
+#define B64_DEC_UNITS 2
+#endif
+#ifndef B64_DEC_IN_STAGES
+#define B64_DEC_IN_STAGES 8
 #endif
 #ifndef B64_DEC_OUT_STAGES
 #define B64_DEC_OUT_STAGES 2
@@ -46,11 +51,22 @@ namespace {
 constexpr int kWarps = B64_DEC_WARPS;
 constexpr int kThreads = 32 * kWarps;
 constexpr int kUnits = B64_DEC_UNITS;                // 16-character units per lane per chunk
+constexpr int kStagesIn = B64_DEC_IN_STAGES;
 constexpr int kStagesOut = B64_DEC_OUT_STAGES;
 constexpr uint32_t kChunkIn = 32 * kUnits * 16;      // characters per warp chunk
 constexpr uint32_t kChunkOut = kChunkIn / 4 * 3;     // bytes per warp chunk
-constexpr size_t kSmem = size_t(kWarps) * kStagesOut * kChunkOut;
+// per warp: kStagesIn input and kStagesOut output buffers; then one barrier
+// per input buffer
+constexpr size_t kSmemRings =
+    size_t(kWarps) * (size_t(kStagesIn) * kChunkIn + size_t(kStagesOut) * kChunkOut);
+constexpr size_t kSmem = kSmemRings + size_t(kWarps) * kStagesIn * sizeof(uint64_t);
 static_assert(kChunkOut % 16 == 0, "bulk copies need 16-byte multiples");
+static_assert(kSmem <= 227 * 1024, "shared memory per block");
+// A body kernel whose bulk copy did not arrive folds this into the result
+// word instead of an offset (offsets are below 2^62); the tail kernel turns
+// it into B64_E_TIMEOUT.
+constexpr uint64_t kTimedOut = uint64_t(1) << 62;
+__device__ uint32_t g_fault;
 
 // Characters [0, body) are whole groups of four that cannot contain valid
 // padding; the last 2..5 characters (all of them when m < 6) are the tail.
@@ -100,14 +116,6 @@ __device__ void block_min_to_global(uint64_t first, unsigned long long* d_err) {
     if ((threadIdx.x & 31) == 0 && w != kNoError) atomicMin(d_err, (unsigned long long)w);
 }
 
-__device__ __forceinline__ uint4 load_stream16(const uint8_t* p) {
-    uint4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
-    return v;
-}
-
 // Programmatic dependent launch: the body and tail kernels may start while
 // the kernel before them finishes; this waits until that kernel has
 // completed and its writes are visible (and makes this kernel's own
@@ -126,14 +134,21 @@ __device__ __forceinline__ int first_bad_in(uint32_t w, const uint8_t* lut) {
 }
 
 __global__ void __launch_bounds__(kThreads)
-    decode_fast_kernel(const uint8_t* __restrict__ src, uint64_t body, uint8_t* __restrict__ dst,
+    decode_body_kernel(const uint8_t* __restrict__ src, uint64_t body, uint8_t* __restrict__ dst,
                        const __grid_constant__ DecodeTable tab, unsigned long long* d_err) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(16) uint8_t lut[256];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    uint8_t* sout = smem + size_t(warp) * kStagesOut * kChunkOut;
+    uint8_t* ring = smem + size_t(warp) * kStagesIn * kChunkIn;
+    uint8_t* sout =
+        smem + size_t(kWarps) * kStagesIn * kChunkIn + size_t(warp) * kStagesOut * kChunkOut;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kSmemRings) + warp * kStagesIn;
     if (tid < 64) reinterpret_cast<uint32_t*>(lut)[tid] = tab.w[tid];
+    if (lane == 0) {
+        for (int s = 0; s < kStagesIn; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+    }
     __syncthreads();
     wait_prior_grid();  // *d_err has been initialised
 
@@ -141,20 +156,31 @@ __global__ void __launch_bounds__(kThreads)
     const uint64_t GW = uint64_t(gridDim.x) * kWarps;
     const uint64_t gw = uint64_t(blockIdx.x) * kWarps + warp;
     const uint64_t K = gw < n_chunks ? (n_chunks - 1 - gw) / GW + 1 : 0;
+    auto chunk_at = [&](uint64_t k) { return gw + k * GW; };
 
-    uint4 cur[kUnits], nxt[kUnits];
-    if (K > 0) {
-#pragma unroll
-        for (int u = 0; u < kUnits; ++u)
-            cur[u] = load_stream16(src + gw * kChunkIn + 16 * (lane + 32 * u));
+    if (lane == 0) {
+        for (uint64_t k = 0; k < K && k < uint64_t(kStagesIn); ++k) {
+            mbar_arrive_expect_tx(&full[k], kChunkIn);
+            bulk_load(ring + k * kChunkIn, src + chunk_at(k) * kChunkIn, kChunkIn, &full[k]);
+        }
     }
     for (uint64_t k = 0; k < K; ++k) {
-        const uint64_t chunk = gw + k * GW;
-        if (k + 1 < K) {
-#pragma unroll
-            for (int u = 0; u < kUnits; ++u)
-                nxt[u] = load_stream16(src + (chunk + GW) * kChunkIn + 16 * (lane + 32 * u));
+        const uint64_t chunk = chunk_at(k);
+        const int s = int(k % kStagesIn);
+        const bool ok = mbar_wait(&full[s], uint32_t(k / kStagesIn) & 1u);
+        if (!__all_sync(0xffffffffu, ok)) {
+            // A bulk copy did not arrive in time: flag it, let the copies in
+            // flight land (bounded), and stop this warp.
+            if (lane == 0) {
+                atomicOr(&g_fault, 1u);
+                atomicMin(d_err, (unsigned long long)kTimedOut);
+                for (uint64_t k2 = k; k2 < K && k2 < k + kStagesIn; ++k2)
+                    mbar_wait(&full[k2 % kStagesIn], uint32_t(k2 / kStagesIn) & 1u);
+                bulk_wait_read<0>();
+            }
+            return;
         }
+        const uint8_t* in = ring + size_t(s) * kChunkIn;
         // The bulk store that last read this output buffer (kStagesOut chunks
         // ago) must be done reading it before it is overwritten.
         const int so = int(k % kStagesOut);
@@ -165,7 +191,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int u = 0; u < kUnits; ++u) {
             const int j = lane + 32 * u;
-            const uint4 c = cur[u];
+            const uint4 c = *reinterpret_cast<const uint4*>(in + 16 * j);
             const uint32_t q0 = decode4(c.x, lut, err);
             const uint32_t q1 = decode4(c.y, lut, err);
             const uint32_t q2 = decode4(c.z, lut, err);
@@ -179,28 +205,29 @@ __global__ void __launch_bounds__(kThreads)
         fence_proxy_async_smem();
         if (__any_sync(0xffffffffu, err & kBad)) {
             // Cold path: the exact first bad offset of this warp chunk, from
-            // the characters still held in registers.
+            // the characters still in the input buffer.
             uint64_t first = kNoError;
-#pragma unroll
-            for (int u = 0; u < kUnits; ++u) {
-                const uint32_t w4[4] = {cur[u].x, cur[u].y, cur[u].z, cur[u].w};
+            for (int u = 0; u < kUnits && first == kNoError; ++u) {
+                const uint32_t* w4 = reinterpret_cast<const uint32_t*>(in + 16 * (lane + 32 * u));
                 for (int q = 0; q < 4 && first == kNoError; ++q) {
                     const int i = first_bad_in(w4[q], lut);
                     if (i >= 0)
                         first = chunk * kChunkIn + uint64_t(16 * (lane + 32 * u) + 4 * q + i);
                 }
-                if (first != kNoError) break;
             }
             const uint64_t w = warp_min_u64(first);
             if (lane == 0 && w != kNoError) atomicMin(d_err, (unsigned long long)w);
         }
-        __syncwarp();
+        __syncwarp();  // every lane is done with `in` and has written `out`
         if (lane == 0) {
             bulk_store(dst + chunk * kChunkOut, out, kChunkOut);
             bulk_commit();
+            if (k + kStagesIn < K) {
+                mbar_arrive_expect_tx(&full[s], kChunkIn);
+                bulk_load(ring + size_t(s) * kChunkIn, src + chunk_at(k + kStagesIn) * kChunkIn,
+                          kChunkIn, &full[s]);
+            }
         }
-#pragma unroll
-        for (int u = 0; u < kUnits; ++u) cur[u] = nxt[u];
     }
     if (lane == 0) bulk_wait_read<0>();
 
@@ -289,7 +316,7 @@ __global__ void decode_finalize_kernel(const uint8_t* __restrict__ src, uint64_t
     wait_prior_grid();  // the body kernel has folded in its offsets
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const uint64_t err = *reinterpret_cast<unsigned long long*>(d_result);
-    *d_result = tail_result(src, m, dst, tab, flags, err);
+    *d_result = err == kTimedOut ? B64_E_TIMEOUT : tail_result(src, m, dst, tab, flags, err);
 }
 
 // Inputs of at most kSmallMax characters: the whole strict decode in one
@@ -393,6 +420,28 @@ struct KernelSetup {
 };
 KernelSetup g_setup[64];
 
+// Launches a persistent body kernel (warps x chunk characters per warp
+// chunk) as a programmatic dependent: one grid of resident CTAs, fewer when
+// the body has fewer chunks than warps.
+template <class Kernel>
+cudaError_t launch_body(Kernel kernel, KernelSetup& ks, int threads, size_t smem, uint32_t chunk,
+                        const uint8_t* src, uint64_t body, uint8_t* dst, const DecodeTable& tab,
+                        unsigned long long* d_err, cudaStream_t stream) {
+    const DeviceInfo& di = device_info();
+    std::call_once(ks.once, [&] {
+        ks.err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (ks.err == cudaSuccess)
+            ks.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ks.ctas_per_sm, kernel, threads, smem);
+        if (ks.ctas_per_sm < 1) ks.ctas_per_sm = 1;
+    });
+    if (ks.err != cudaSuccess) return ks.err;
+    const uint64_t warps = uint64_t(threads / 32);
+    const uint64_t want = (body / chunk + warps - 1) / warps;
+    uint64_t grid = uint64_t(di.sm_count) * ks.ctas_per_sm;
+    if (want < grid) grid = want > 0 ? want : 1;
+    return launch_dependent(kernel, unsigned(grid), threads, smem, stream, src, body, dst, tab, d_err);
+}
+
 }  // namespace
 
 cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const DecodeTable& tab,
@@ -431,23 +480,8 @@ cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const De
         const bool aligned =
             ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0;
         if (aligned) {
-            KernelSetup& ks = g_setup[di.device & 63];
-            std::call_once(ks.once, [&] {
-                ks.err = cudaFuncSetAttribute(decode_fast_kernel,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              int(kSmem));
-                if (ks.err == cudaSuccess)
-                    ks.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        &ks.ctas_per_sm, decode_fast_kernel, kThreads, kSmem);
-                if (ks.ctas_per_sm < 1) ks.ctas_per_sm = 1;
-            });
-            if (ks.err != cudaSuccess) return ks.err;
-            const uint64_t n_chunks = body / kChunkIn;
-            const uint64_t want = (n_chunks + kWarps - 1) / kWarps;
-            uint64_t grid = uint64_t(di.sm_count) * ks.ctas_per_sm;
-            if (want < grid) grid = want > 0 ? want : 1;
-            const cudaError_t e1 = launch_dependent(decode_fast_kernel, unsigned(grid), kThreads,
-                                                    kSmem, stream, src, body, dst, tab, d_err);
+            const cudaError_t e1 = launch_body(decode_body_kernel, g_setup[di.device & 63], kThreads,
+                                               kSmem, kChunkIn, src, body, dst, tab, d_err, stream);
             if (e1 != cudaSuccess) return e1;
         } else {
             const uint64_t quads = body / 4;
@@ -466,5 +500,15 @@ cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const De
                             d_result);
 }
 
+
+uint32_t decode_fault_flag(bool clear) {
+    uint32_t v = 0;
+    cudaMemcpyFromSymbol(&v, g_fault, sizeof(v));
+    if (clear && v) {
+        const uint32_t z = 0;
+        cudaMemcpyToSymbol(g_fault, &z, sizeof(z));
+    }
+    return v;
+}
 
 }  // namespace b64

@@ -49,6 +49,7 @@ uint32_t encode_fault_flag(bool clear);
 // start with a memset of *d_result, then the body kernel and the tail kernel.
 cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const DecodeTable& tab,
                           int flags, int64_t* d_result, cudaStream_t stream);
+uint32_t decode_fault_flag(bool clear);
 
 // ---- batches (b64_batch.cu)
 constexpr int kMaxAlphabets = 4;

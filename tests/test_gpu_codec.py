@@ -16,7 +16,8 @@ from paper_1910_05109_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 ENC_CHUNK = 12288   # bytes per encode chunk of the fast path
-DEC_CHUNK = 16384   # characters per decode chunk of the fast path
+DEC_CHUNK = 1024    # characters per warp chunk of the decode body kernel
+DEC_WARPS = 16      # warps per block of the decode body kernel (one block per SM)
 
 
 @pytest.fixture(scope="module")
@@ -152,7 +153,7 @@ def test_injected_invalid_byte_offsets(b64, orc, alphabets):
             assert want == -(off + 1)
 
 
-@pytest.mark.parametrize("chunks", [4, 200])  # one-launch decode / body kernel + tail kernel
+@pytest.mark.parametrize("chunks", [64, 4000])  # one-launch decode / body kernel + tail kernel
 def test_invalid_bytes_at_chunk_edges(b64, orc, alphabets, chunks):
     alph, chars, padded = alphabets["std"]
     text = orc.encode(wl.random_bytes(chunks // 4 * 3 * DEC_CHUNK, seed=12), chars, padded)
@@ -174,19 +175,26 @@ def test_invalid_bytes_at_chunk_edges(b64, orc, alphabets, chunks):
 
 
 def test_errors_in_refilled_stages(b64, orc, alphabets):
-    """Enough chunks that every CTA refills its shared-memory stages several
-    times; bad bytes anywhere in a chunk (not only in thread 0's unit) must be
-    found while the refill of the same stage is pending."""
+    """Enough chunks that every warp refills each of its eight input buffers
+    several times; bad bytes anywhere in a chunk (not only in lane 0's unit)
+    must be found while the refill of the same buffer is pending, in the
+    first and last chunk of a warp's first pass and in later passes."""
     alph, chars, padded = alphabets["std"]
-    text = orc.encode(wl.random_bytes(3 * DEC_CHUNK // 4 * 2400, seed=15), chars, padded)
+    gw = torch.cuda.get_device_properties(0).multi_processor_count * DEC_WARPS
+    n_chunks = 8 * gw * 3 + 5
+    text = orc.encode(wl.random_bytes(3 * DEC_CHUNK // 4 * n_chunks, seed=15), chars, padded)
     dev = to_dev(text)
-    for chunk in (0, 1, 2, 151, 304, 730, 1500, 2398):
-        for inner in (0, 17, 4095, 8190, 12012, 16383):
+    for chunk in (0, 1, 2, gw - 1, gw, gw + 1, 8 * gw - 1, 8 * gw, 8 * gw + 1, 13 * gw + 77,
+                  n_chunks - 2):
+        for inner in (0, 17, 511, 512, 1000, 1023):
             pos = chunk * DEC_CHUNK + inner
             t = dev.clone()
             t[pos] = 0x18
             r, _ = b64.decode(t, alph)
             assert r == -(pos + 1), (chunk, inner, r)
+    r, out = b64.decode(dev, alph)
+    assert r == 3 * DEC_CHUNK // 4 * n_chunks
+    assert np.array_equal(out.cpu().numpy(), orc.decode(text, chars, padded)[1])
 
 
 def test_every_byte_value_rejected(b64, orc, alphabets):

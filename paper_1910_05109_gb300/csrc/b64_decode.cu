@@ -13,55 +13,58 @@
 // a bad byte looks for its exact offset (cold path) and folds it into the
 // call's result with an atomic minimum.
 //
-// Body path (src and dst 16-byte aligned): a persistent grid in which every
-// warp works alone on "warp chunks" of 32 x kUnits x 16 characters (1 KiB).
-// Lane 0 of each warp keeps kStagesIn bulk (TMA) copies of its next chunks in
-// flight into a per-warp ring of shared-memory buffers; the warp decodes a
-// landed chunk from shared memory (16 characters a lane), writes the 12-byte
-// results into one of kStagesOut output buffers, and lane 0 stores that
-// buffer with a bulk store and refills the input buffer. At 16 warps a block
-// and one block an SM, 128 KiB of input is in flight per SM at 32 registers a
-// thread. The error vote and the cold-path search are warp-wide, so no
-// block-wide barrier is taken inside the loop. The body (all but the last 2
-// to 5 characters) is done by this kernel; a one-thread kernel then checks
-// the padding and length rules on the tail, decodes it and writes the call's
-// result.
+// Body path (src and dst 16-byte aligned): a persistent grid of one 16-warp
+// block an SM in which every warp works alone on "warp chunks" of
+// 32 x kUnits x 16 characters. Lane 0 of each warp keeps kStagesIn bulk (TMA)
+// copies of its next chunks in flight into a per-warp ring of shared-memory
+// buffers; the warp decodes a landed chunk from shared memory (16 characters
+// a lane), writes the 12-byte results into one of kStagesOut output buffers,
+// and lane 0 stores that buffer with a bulk store and refills the input
+// buffer. Inputs of 64 MiB and more use 1 KiB chunks eight deep (128 KiB of
+// input in flight per SM, at 32 registers a thread); smaller ones use 2 KiB
+// chunks four deep. The error vote and the cold-path search are warp-wide,
+// so no block-wide barrier is taken inside the loop. The body (all but the
+// last 2 to 5 characters) is done by this kernel; a one-thread kernel then
+// checks the padding and length rules on the tail, decodes it and writes the
+// call's result.
 #include <mutex>
 
 #include <cooperative_groups.h>
 
 #include "b64_internal.h"
 
-#ifndef B64_DEC_WARPS
-#define B64_DEC_WARPS 16
-#endif
-#ifndef B64_DEC_UNITS
-#define B64_DEC_UNITS 2
-#endif
-#ifndef B64_DEC_IN_STAGES
-#define B64_DEC_IN_STAGES 8
-#endif
-#ifndef B64_DEC_OUT_STAGES
-#define B64_DEC_OUT_STAGES 2
+#ifndef B64_DEC_LARGE_MIN
+#define B64_DEC_LARGE_MIN (64ull << 20)
 #endif
 
 namespace b64 {
 namespace {
 
-constexpr int kWarps = B64_DEC_WARPS;
-constexpr int kThreads = 32 * kWarps;
-constexpr int kUnits = B64_DEC_UNITS;                // 16-character units per lane per chunk
-constexpr int kStagesIn = B64_DEC_IN_STAGES;
-constexpr int kStagesOut = B64_DEC_OUT_STAGES;
-constexpr uint32_t kChunkIn = 32 * kUnits * 16;      // characters per warp chunk
-constexpr uint32_t kChunkOut = kChunkIn / 4 * 3;     // bytes per warp chunk
-// per warp: kStagesIn input and kStagesOut output buffers; then one barrier
-// per input buffer
-constexpr size_t kSmemRings =
-    size_t(kWarps) * (size_t(kStagesIn) * kChunkIn + size_t(kStagesOut) * kChunkOut);
-constexpr size_t kSmem = kSmemRings + size_t(kWarps) * kStagesIn * sizeof(uint64_t);
-static_assert(kChunkOut % 16 == 0, "bulk copies need 16-byte multiples");
-static_assert(kSmem <= 227 * 1024, "shared memory per block");
+// The shape of a body launch: W warps a block, each with SI input buffers of
+// 32 x U x 16 characters filled by bulk copies and SO output buffers.
+template <int W, int U, int SI, int SO>
+struct DecodeShape {
+    static constexpr int kWarps = W;
+    static constexpr int kThreads = 32 * W;
+    static constexpr int kUnits = U;                     // 16-character units per lane per chunk
+    static constexpr int kStagesIn = SI;
+    static constexpr int kStagesOut = SO;
+    static constexpr uint32_t kChunkIn = 32 * U * 16;    // characters per warp chunk
+    static constexpr uint32_t kChunkOut = kChunkIn / 4 * 3;
+    // per warp: SI input and SO output buffers; then one barrier per input buffer
+    static constexpr size_t kSmemRings = size_t(W) * (size_t(SI) * kChunkIn + size_t(SO) * kChunkOut);
+    static constexpr size_t kSmem = kSmemRings + size_t(W) * SI * sizeof(uint64_t);
+    static_assert(kChunkOut % 16 == 0, "bulk copies need 16-byte multiples");
+    static_assert(kSmem <= 227 * 1024, "shared memory per block");
+};
+// One 16-warp block an SM. Below kLargeMin characters: 2 KiB chunks, four
+// deep (fewer bulk copies per byte, which pays when the input is in L2).
+// From kLargeMin up: 1 KiB chunks, eight deep, 128 KiB in flight per SM (the
+// faster shape for inputs streamed from DRAM).
+using SmallShape = DecodeShape<16, 4, 4, 2>;
+using LargeShape = DecodeShape<16, 2, 8, 2>;
+constexpr uint64_t kLargeMin = B64_DEC_LARGE_MIN;
+constexpr int kThreads = 512;                            // generic kernel
 // A body kernel whose bulk copy did not arrive folds this into the result
 // word instead of an offset (offsets are below 2^62); the tail kernel turns
 // it into B64_E_TIMEOUT.
@@ -133,9 +136,13 @@ __device__ __forceinline__ int first_bad_in(uint32_t w, const uint8_t* lut) {
     return -1;
 }
 
-__global__ void __launch_bounds__(kThreads)
+template <class Sh>
+__global__ void __launch_bounds__(Sh::kThreads)
     decode_body_kernel(const uint8_t* __restrict__ src, uint64_t body, uint8_t* __restrict__ dst,
                        const __grid_constant__ DecodeTable tab, unsigned long long* d_err) {
+    constexpr int kWarps = Sh::kWarps, kUnits = Sh::kUnits;
+    constexpr int kStagesIn = Sh::kStagesIn, kStagesOut = Sh::kStagesOut;
+    constexpr uint32_t kChunkIn = Sh::kChunkIn, kChunkOut = Sh::kChunkOut;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(16) uint8_t lut[256];
 
@@ -143,7 +150,7 @@ __global__ void __launch_bounds__(kThreads)
     uint8_t* ring = smem + size_t(warp) * kStagesIn * kChunkIn;
     uint8_t* sout =
         smem + size_t(kWarps) * kStagesIn * kChunkIn + size_t(warp) * kStagesOut * kChunkOut;
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kSmemRings) + warp * kStagesIn;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + Sh::kSmemRings) + warp * kStagesIn;
     if (tid < 64) reinterpret_cast<uint32_t*>(lut)[tid] = tab.w[tid];
     if (lane == 0) {
         for (int s = 0; s < kStagesIn; ++s) mbar_init(&full[s], 1);
@@ -418,7 +425,7 @@ struct KernelSetup {
     cudaError_t err = cudaSuccess;
     int ctas_per_sm = 1;
 };
-KernelSetup g_setup[64];
+KernelSetup g_small[64], g_large[64];
 
 // Launches a persistent body kernel (warps x chunk characters per warp
 // chunk) as a programmatic dependent: one grid of resident CTAs, fewer when
@@ -480,8 +487,15 @@ cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const De
         const bool aligned =
             ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0;
         if (aligned) {
-            const cudaError_t e1 = launch_body(decode_body_kernel, g_setup[di.device & 63], kThreads,
-                                               kSmem, kChunkIn, src, body, dst, tab, d_err, stream);
+            const int dv = di.device & 63;
+            const cudaError_t e1 =
+                body >= kLargeMin
+                    ? launch_body(decode_body_kernel<LargeShape>, g_large[dv], LargeShape::kThreads,
+                                  LargeShape::kSmem, LargeShape::kChunkIn, src, body, dst, tab, d_err,
+                                  stream)
+                    : launch_body(decode_body_kernel<SmallShape>, g_small[dv], SmallShape::kThreads,
+                                  SmallShape::kSmem, SmallShape::kChunkIn, src, body, dst, tab, d_err,
+                                  stream);
             if (e1 != cudaSuccess) return e1;
         } else {
             const uint64_t quads = body / 4;

@@ -12,39 +12,55 @@
 // warp is its own pipeline. A warp streams "warp chunks" of 32 x kUnits x 12
 // input bytes through a ring of kStages shared-memory buffers that its lane 0
 // fills with bulk (TMA) copies, each completing on the warp's own mbarrier;
-// the lanes turn each chunk into characters and write them with coalesced
-// 16-byte stores (512 contiguous bytes per warp instruction). No block-wide
-// barrier is taken inside the loop, so warps never wait for one another.
-// The bytes after the last whole warp chunk and the final 1-2 bytes with
-// their padding are done by one warp with plain loads.
+// the lanes turn each chunk into characters. Inputs below 32 MiB use small
+// chunks (384 bytes) and many blocks, with coalesced 16-byte stores straight
+// to global memory; larger ones use 1152-byte chunks, seven deep, one block
+// an SM, and stage the characters in shared memory for bulk stores. No
+// block-wide barrier is taken inside the loop, so warps never wait for one
+// another. The bytes after the last whole warp chunk and the final 1-2 bytes
+// with their padding are done by one warp with plain loads.
 #include <mutex>
 
 #include "b64_internal.h"
 
-#ifndef B64_ENC_WARPS
-#define B64_ENC_WARPS 16
-#endif
-#ifndef B64_ENC_UNITS
-#define B64_ENC_UNITS 1
-#endif
-#ifndef B64_ENC_STAGES
-#define B64_ENC_STAGES 4
-#endif
 #ifndef B64_ENC_PAIRS
 #define B64_ENC_PAIRS 1
+#endif
+#ifndef B64_ENC_LARGE_MIN
+#define B64_ENC_LARGE_MIN (32ull << 20)
 #endif
 
 namespace b64 {
 namespace {
 
-constexpr int kWarps = B64_ENC_WARPS;
-constexpr int kThreads = 32 * kWarps;
-constexpr int kUnits = B64_ENC_UNITS;                // 12-byte units per lane per chunk
-constexpr int kStages = B64_ENC_STAGES;
-constexpr uint32_t kChunkIn = 32 * kUnits * 12;      // input bytes per warp chunk
-constexpr uint32_t kChunkOut = kChunkIn / 3 * 4;     // characters per warp chunk
-constexpr size_t kSmem = size_t(kWarps) * kStages * (kChunkIn + sizeof(uint64_t));
-static_assert(kChunkIn % 16 == 0 && kChunkIn % 3 == 0, "bulk copies need 16-byte multiples");
+// The shape of a streaming encode launch: W warps a block, each with S input
+// buffers of 32 x U x 12 bytes filled by bulk copies; with BulkOut the
+// characters go through two output buffers a warp and bulk stores, else
+// straight to global memory with 16-byte stores.
+template <int W, int U, int S, bool BulkOut>
+struct EncodeShape {
+    static constexpr int kWarps = W;
+    static constexpr int kThreads = 32 * W;
+    static constexpr int kUnits = U;                      // 12-byte units per lane per chunk
+    static constexpr int kStages = S;
+    static constexpr int kOutStages = 2;
+    static constexpr bool kBulkOut = BulkOut;
+    static constexpr uint32_t kChunkIn = 32 * U * 12;     // input bytes per warp chunk
+    static constexpr uint32_t kChunkOut = kChunkIn / 3 * 4;
+    static constexpr size_t kSmemIn = size_t(W) * S * (kChunkIn + sizeof(uint64_t));
+    static constexpr size_t kSmem = kSmemIn + (BulkOut ? size_t(W) * kOutStages * kChunkOut : 0);
+    static_assert(kChunkIn % 16 == 0, "bulk copies need 16-byte multiples");
+    static_assert(kSmemIn % 16 == 0, "output buffers start on 16-byte boundaries");
+    static_assert(kSmem <= 200 * 1024, "shared memory per block, with the pair table");
+};
+// Below kLargeMin input bytes: 4 blocks an SM of 16 warps with 4 buffers of
+// 384 bytes (fine grain for small inputs). From kLargeMin up: one block an SM
+// of 16 warps with 7 buffers of 1152 bytes each, 126 KiB of input in flight
+// per SM, and bulk stores.
+using SmallShape = EncodeShape<16, 1, 4, false>;
+using LargeShape = EncodeShape<16, 3, 7, true>;
+constexpr uint64_t kLargeMin = B64_ENC_LARGE_MIN;
+constexpr int kThreads = 512;                            // generic kernel
 
 __device__ uint32_t g_fault;
 
@@ -118,9 +134,13 @@ __device__ __forceinline__ uint4 encode12_pairs(uint32_t x, uint32_t y, uint32_t
 }
 #endif
 
-__global__ void __launch_bounds__(kThreads)
+template <class Sh>
+__global__ void __launch_bounds__(Sh::kThreads)
     encode_tma_kernel(const uint8_t* __restrict__ src, uint64_t n, uint8_t* __restrict__ dst,
                       const __grid_constant__ EncodeTable tab, int padded) {
+    constexpr int kWarps = Sh::kWarps, kThreads = Sh::kThreads, kUnits = Sh::kUnits;
+    constexpr int kStages = Sh::kStages, kOutStages = Sh::kOutStages;
+    constexpr uint32_t kChunkIn = Sh::kChunkIn, kChunkOut = Sh::kChunkOut;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(16) uint8_t lut[64];
 
@@ -163,11 +183,21 @@ __global__ void __launch_bounds__(kThreads)
                 atomicOr(&g_fault, 1u);
                 for (uint64_t k2 = k; k2 < K && k2 < k + kStages; ++k2)
                     mbar_wait(&full[k2 % kStages], uint32_t(k2 / kStages) & 1u);
+                if constexpr (Sh::kBulkOut) bulk_wait_read<0>();
             }
             return;
         }
         const uint8_t* in = ring + size_t(s) * kChunkIn;
+        uint8_t* const sbuf =
+            Sh::kBulkOut ? smem + Sh::kSmemIn + (size_t(warp) * kOutStages + k % kOutStages) * kChunkOut
+                         : nullptr;
         uint4* out = reinterpret_cast<uint4*>(dst + (gw + k * GW) * kChunkOut);
+        if constexpr (Sh::kBulkOut) {
+            // the bulk store that last read this buffer is done reading it
+            if (lane == 0) bulk_wait_read<kOutStages - 1>();
+            __syncwarp();
+            out = reinterpret_cast<uint4*>(sbuf);
+        }
 #pragma unroll
         for (int u = 0; u < kUnits; ++u) {
             const int j = lane + 32 * u;
@@ -178,6 +208,14 @@ __global__ void __launch_bounds__(kThreads)
             out[j] = encode12(w[0], w[1], w[2], lut);
 #endif
         }
+        if constexpr (Sh::kBulkOut) {
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                bulk_store(dst + (gw + k * GW) * kChunkOut, sbuf, kChunkOut);
+                bulk_commit();
+            }
+        }
         __syncwarp();
         if (lane == 0 && k + kStages < K) {
             mbar_arrive_expect_tx(&full[s], kChunkIn);
@@ -186,6 +224,9 @@ __global__ void __launch_bounds__(kThreads)
         }
     }
 
+    if constexpr (Sh::kBulkOut) {
+        if (lane == 0) bulk_wait_read<0>();
+    }
     if (gw == n_chunks % GW) {
         encode_triples_plain(src, n_chunks * (kChunkIn / 3), n / 3, dst, lut, lane, 32, true);
         if (lane == 0) encode_tail(src, n, dst, lut, padded);
@@ -209,7 +250,31 @@ struct KernelSetup {
     cudaError_t err = cudaSuccess;
     int ctas_per_sm = 1;
 };
-KernelSetup g_setup[64];
+KernelSetup g_small[64], g_large[64];
+
+// One resident grid of encode_tma_kernel<Sh> (fewer blocks when the input
+// has fewer chunks than the grid has warps).
+template <class Sh>
+cudaError_t launch_tma(KernelSetup& ks, const uint8_t* src, uint64_t n, uint8_t* dst,
+                       const EncodeTable& tab, int padded, cudaStream_t stream) {
+    const DeviceInfo& di = device_info();
+    std::call_once(ks.once, [&] {
+        ks.err = cudaFuncSetAttribute(encode_tma_kernel<Sh>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::kSmem));
+        if (ks.err == cudaSuccess)
+            ks.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &ks.ctas_per_sm, encode_tma_kernel<Sh>, Sh::kThreads, Sh::kSmem);
+        if (ks.ctas_per_sm < 1) ks.ctas_per_sm = 1;
+    });
+    if (ks.err != cudaSuccess) return ks.err;
+    const uint64_t n_chunks = n / Sh::kChunkIn;
+    const uint64_t want = (n_chunks + Sh::kWarps - 1) / Sh::kWarps;
+    uint64_t grid = uint64_t(di.sm_count) * ks.ctas_per_sm;
+    if (want < grid) grid = want > 0 ? want : 1;
+    encode_tma_kernel<Sh><<<unsigned(grid), Sh::kThreads, Sh::kSmem, stream>>>(src, n, dst, tab,
+                                                                              padded);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -219,29 +284,16 @@ cudaError_t launch_encode(const uint8_t* src, uint64_t n, uint8_t* dst, const En
     const bool aligned = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) &
                           15u) == 0;
     if (aligned) {
-        KernelSetup& ks = g_setup[di.device & 63];
-        std::call_once(ks.once, [&] {
-            ks.err = cudaFuncSetAttribute(encode_tma_kernel,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmem));
-            if (ks.err == cudaSuccess)
-                ks.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &ks.ctas_per_sm, encode_tma_kernel, kThreads, kSmem);
-            if (ks.ctas_per_sm < 1) ks.ctas_per_sm = 1;
-        });
-        if (ks.err != cudaSuccess) return ks.err;
-        const uint64_t n_chunks = n / kChunkIn;
-        const uint64_t want = (n_chunks + kWarps - 1) / kWarps;
-        uint64_t grid = uint64_t(di.sm_count) * ks.ctas_per_sm;
-        if (want < grid) grid = want > 0 ? want : 1;
-        encode_tma_kernel<<<unsigned(grid), kThreads, kSmem, stream>>>(src, n, dst, tab, padded);
-    } else {
-        const uint64_t triples = n / 3;
-        uint64_t grid = (triples + kThreads - 1) / kThreads;
-        const uint64_t cap = uint64_t(di.sm_count) * 8;
-        if (grid > cap) grid = cap;
-        if (grid == 0) grid = 1;
-        encode_generic_kernel<<<unsigned(grid), kThreads, 0, stream>>>(src, n, dst, tab, padded);
+        return n >= kLargeMin
+                   ? launch_tma<LargeShape>(g_large[di.device & 63], src, n, dst, tab, padded, stream)
+                   : launch_tma<SmallShape>(g_small[di.device & 63], src, n, dst, tab, padded, stream);
     }
+    const uint64_t triples = n / 3;
+    uint64_t grid = (triples + kThreads - 1) / kThreads;
+    const uint64_t cap = uint64_t(di.sm_count) * 8;
+    if (grid > cap) grid = cap;
+    if (grid == 0) grid = 1;
+    encode_generic_kernel<<<unsigned(grid), kThreads, 0, stream>>>(src, n, dst, tab, padded);
     return cudaGetLastError();
 }
 

@@ -15,9 +15,14 @@ from paper_1910_05109_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-ENC_CHUNK = 12288   # bytes per encode chunk of the fast path
-DEC_CHUNK = 1024    # characters per warp chunk of the decode body kernel
+ENC_CHUNK = 384     # input bytes per warp chunk of the encode kernel below 32 MiB
+ENC_LARGE_MIN = 32 << 20   # from here on: 1152-byte warp chunks, bulk stores
+ENC_LARGE_CHUNK = 1152
+DEC_CHUNK = 2048    # characters per warp chunk of the decode body kernel below 64 MiB
 DEC_WARPS = 16      # warps per block of the decode body kernel (one block per SM)
+# (characters per warp chunk, input buffers per warp) below and from 64 MiB
+DEC_SHAPES = {"small": (2048, 4), "large": (1024, 8)}
+DEC_LARGE_MIN = 64 << 20
 
 
 @pytest.fixture(scope="module")
@@ -111,6 +116,23 @@ def test_encode_decode_parity_sizes(b64, orc, alphabets, name):
         assert np.array_equal(d, d_want), (name, n)
 
 
+@pytest.mark.parametrize("name", ["std", "url"])
+def test_encode_large_shape(b64, orc, alphabets, name):
+    """Sizes around the switch to the large encode shape, and one where every
+    warp refills its seven input buffers twice with a ragged remainder;
+    bit-exact against the oracle, then decoded back."""
+    alph, chars, padded = alphabets[name]
+    gw = torch.cuda.get_device_properties(0).multi_processor_count * 16
+    for i, n in enumerate((ENC_LARGE_MIN - 1, ENC_LARGE_MIN, ENC_LARGE_MIN + 2,
+                           ENC_LARGE_CHUNK * gw * 14 + ENC_LARGE_CHUNK - 1)):
+        data = wl.random_bytes(n, seed=5000 + i)
+        want = orc.encode(data, chars, padded)
+        got = gpu_encode(b64, data, alph)
+        assert np.array_equal(got, want), (name, n)
+        r, d = gpu_decode(b64, want, alph)
+        assert r == n and np.array_equal(d, data), (name, n)
+
+
 def test_config1_single_buffer(b64, orc, alphabets):
     # 2^20 - 1 bytes of seed 0 (and the two sizes that give '=' and '==').
     alph, chars, padded = alphabets["std"]
@@ -174,26 +196,32 @@ def test_invalid_bytes_at_chunk_edges(b64, orc, alphabets, chunks):
     assert gpu_decode(b64, bad, alph)[0] == -(DEC_CHUNK + 10)
 
 
-def test_errors_in_refilled_stages(b64, orc, alphabets):
-    """Enough chunks that every warp refills each of its eight input buffers
-    several times; bad bytes anywhere in a chunk (not only in lane 0's unit)
-    must be found while the refill of the same buffer is pending, in the
-    first and last chunk of a warp's first pass and in later passes."""
+@pytest.mark.parametrize("shape", ["small", "large"])
+def test_errors_in_refilled_stages(b64, orc, alphabets, shape):
+    """Enough chunks that every warp refills each of its input buffers several
+    times; bad bytes anywhere in a chunk (not only in lane 0's unit) must be
+    found while the refill of the same buffer is pending, in the first and
+    last chunk of a warp's first pass and in later passes. Both body shapes."""
     alph, chars, padded = alphabets["std"]
+    chunk, stages = DEC_SHAPES[shape]
     gw = torch.cuda.get_device_properties(0).multi_processor_count * DEC_WARPS
-    n_chunks = 8 * gw * 3 + 5
-    text = orc.encode(wl.random_bytes(3 * DEC_CHUNK // 4 * n_chunks, seed=15), chars, padded)
+    n_chunks = stages * gw * 3 + 5
+    if shape == "large":
+        n_chunks = max(n_chunks, DEC_LARGE_MIN // chunk + 5)
+    else:
+        assert n_chunks * chunk < DEC_LARGE_MIN
+    text = orc.encode(wl.random_bytes(3 * chunk // 4 * n_chunks, seed=15), chars, padded)
     dev = to_dev(text)
-    for chunk in (0, 1, 2, gw - 1, gw, gw + 1, 8 * gw - 1, 8 * gw, 8 * gw + 1, 13 * gw + 77,
-                  n_chunks - 2):
-        for inner in (0, 17, 511, 512, 1000, 1023):
-            pos = chunk * DEC_CHUNK + inner
+    for c in (0, 1, 2, gw - 1, gw, gw + 1, stages * gw - 1, stages * gw, stages * gw + 1,
+              2 * stages * gw + 77, n_chunks - 2):
+        for inner in (0, 17, 511, 512, chunk - 24, chunk - 1):
+            pos = c * chunk + inner
             t = dev.clone()
             t[pos] = 0x18
             r, _ = b64.decode(t, alph)
-            assert r == -(pos + 1), (chunk, inner, r)
+            assert r == -(pos + 1), (c, inner, r)
     r, out = b64.decode(dev, alph)
-    assert r == 3 * DEC_CHUNK // 4 * n_chunks
+    assert r == 3 * chunk // 4 * n_chunks
     assert np.array_equal(out.cpu().numpy(), orc.decode(text, chars, padded)[1])
 
 

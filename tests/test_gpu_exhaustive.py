@@ -8,11 +8,17 @@ applied to each one separately:
   this holds every "XY==" and every final group with one pad;
 - all 16,777,216 three-character strings, base64url, unpadded (decodes to 2
   bytes, or the first bad offset);
-- all 65,536 two-character strings in both modes.
+- all 65,536 two-character strings in both modes;
+- all 4,294,967,296 four-byte strings, standard padded and base64url
+  unpadded: every result against the oracle's result for the string's class
+  pattern (quad_classes.py; pinned in test_oracle_quads.py), and the bytes of
+  every accepted string against the oracle's decode of it.
 """
 import numpy as np
 import pytest
 import torch
+
+import quad_classes as qc
 
 pytestmark = pytest.mark.gpu
 
@@ -86,3 +92,50 @@ def test_every_two_characters(b64, orc, padded):
         assert (res == -3).sum() == 64 * 64 + 64 + 1
     else:
         assert (res == 1).sum() == 64 * 64
+
+
+@pytest.mark.parametrize("padded", [True, False])
+def test_every_four_byte_string(b64, orc, padded):
+    alph = b64.Alphabet.standard() if padded else b64.Alphabet.url()
+    chars = orc.standard_alphabet() if padded else orc.url_alphabet()
+    table = torch.from_numpy(qc.pattern_table(orc, chars, padded)).cuda()
+    cls = torch.from_numpy(qc.byte_classes(chars)).cuda()
+    N = 1 << 26                                     # strings per batch; 64 batches
+    dev = "cuda"
+    off = torch.arange(0, 4 * (N + 1), 4, dtype=torch.int64, device=dev)
+    doff = torch.arange(0, 3 * (N + 1), 3, dtype=torch.int64, device=dev)
+    dst = torch.empty(3 * N + 16, dtype=torch.uint8, device=dev)
+    res = torch.empty(N, dtype=torch.int64, device=dev)
+    ws = torch.empty(max(1, b64.lib().b64_batch_workspace_size(N)), dtype=torch.uint8, device=dev)
+    s = torch.empty((N, 4), dtype=torch.uint8, device=dev)
+    base = torch.arange(N, dtype=torch.int64, device=dev)
+    acc_in, acc_out, acc_len = [], [], []
+    for c in range(64):
+        x = base + (c << 26)                        # string x: bytes x & 255, (x >> 8) & 255, ...
+        for i in range(4):
+            s[:, i] = ((x >> (8 * i)) & 255).to(torch.uint8)
+        b64.decode_batch(s.view(-1), off, dst, doff, [alph], results=res, workspace=ws)
+        pat = cls[s[:, 0].long()] + 3 * cls[s[:, 1].long()] + 9 * cls[s[:, 2].long()] + \
+            27 * cls[s[:, 3].long()]
+        want = table[pat]
+        if not torch.equal(res, want):
+            i = int(torch.nonzero(res != want)[0])
+            raise AssertionError((c, bytes(s[i].cpu().numpy()), int(res[i]), int(want[i])))
+        ok = res >= 0
+        acc_in.append(s[ok].cpu())
+        acc_out.append(dst[:3 * N].view(N, 3)[ok].cpu())
+        acc_len.append(res[ok].cpu())
+    vin = torch.cat(acc_in).numpy()
+    vout = torch.cat(acc_out).numpy()
+    vlen = torch.cat(acc_len).numpy()
+    n = vin.shape[0]
+    assert n == (64 ** 4 + 64 ** 3 + 64 ** 2 if padded else 64 ** 4)
+    want_dec, want_res = orc.decode_batch(vin.ravel(), np.arange(n + 1, dtype=np.int64) * 4,
+                                          np.arange(n + 1, dtype=np.int64) * 3, chars,
+                                          np.zeros(n, np.int32), np.full(n, int(padded), np.int32),
+                                          3 * n)
+    assert np.array_equal(want_res, vlen)
+    want_dec = want_dec.reshape(n, 3)
+    for k in np.unique(vlen):
+        rows = vlen == k
+        assert np.array_equal(vout[rows, :k], want_dec[rows, :k])

@@ -200,10 +200,28 @@ constexpr int kScanItems = 8;
 
 __global__ void __launch_bounds__(kScanThreads)
     mime_scan_kernel(unsigned long long* __restrict__ totals, uint64_t nblk,
-                     unsigned long long* __restrict__ status) {
+                     unsigned long long* __restrict__ status, const uint8_t* __restrict__ src,
+                     uint64_t m) {
     __shared__ uint64_t warp_sum[kScanThreads / 32];
     __shared__ uint64_t warp_key[kScanThreads / 32];
+    __shared__ uint32_t first_space;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // status[6] = L if the input starts with a line of L data characters and
+    // CR LF, L a multiple of 4 below kScanThreads (the decode kernel's
+    // line-layout fast path, checked there segment by segment), else 0
+    if (tid == 0) first_space = kScanThreads;
+    __syncthreads();
+    if (uint64_t(tid) < m) {
+        const uint32_t c = src[tid];
+        if (c == '\r' || c == '\n' || c == ' ') atomicMin(&first_space, uint32_t(tid));
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const uint32_t f = first_space;
+        const bool lines = f < kScanThreads && f >= 4 && f % 4 == 0 && uint64_t(f) + 1 < m &&
+                           src[f] == '\r' && src[f + 1] == '\n';
+        status[6] = lines ? f : 0;
+    }
     uint64_t carry = 0, carry_key = 0;  // key: (block + 1) << 8 | last byte, 0 = none
     for (uint64_t base = 0; base < nblk; base += uint64_t(kScanThreads) * kScanItems) {
         const uint64_t i0 = base + uint64_t(tid) * kScanItems;
@@ -285,6 +303,9 @@ __device__ __forceinline__ bool wait_copy(uint64_t* bar, uint32_t parity, uint64
 // relative to raw_base / the document), the whole groups and the output bytes
 // whose second character the segment holds. P: data characters before the
 // segment in its document; prev_last: the last data byte before it.
+__device__ __forceinline__ void copy_out(const uint8_t* buf, uint32_t skip, uint32_t nout,
+                                         uint8_t* __restrict__ q, int lane);
+
 __device__ __forceinline__ void decode_segment(uint8_t* buf, const uint8_t* lut, int flags,
                                                int lane, uint64_t P, uint32_t prev_last,
                                                uint64_t raw_base, uint8_t* __restrict__ out_doc,
@@ -414,9 +435,14 @@ __device__ __forceinline__ void decode_segment(uint8_t* buf, const uint8_t* lut,
         }
     }
     __syncwarp();
-    // copy out buf[skip .. skip + nout): 16-byte stores at aligned addresses,
-    // each built from two aligned 16-byte shared loads; bytes at the edges
-    uint8_t* q = out_doc + ob;
+    copy_out(buf, skip, nout, out_doc + ob, lane);
+}
+
+// Copies buf[skip .. skip + nout) to global q: 16-byte stores at aligned
+// addresses, each built from two aligned 16-byte shared loads; bytes at the
+// edges. Reads up to 32 bytes past skip + nout. Warp-collective.
+__device__ __forceinline__ void copy_out(const uint8_t* buf, uint32_t skip, uint32_t nout,
+                                         uint8_t* __restrict__ q, int lane) {
     const uint32_t head = uint32_t((16 - (reinterpret_cast<uintptr_t>(q) & 15)) & 15);
     const uint32_t h = head < nout ? head : nout;
     if (lane < int(h)) q[lane] = buf[skip + lane];
@@ -436,6 +462,139 @@ __device__ __forceinline__ void decode_segment(uint8_t* buf, const uint8_t* lut,
                        __funnelshift_r(v[2], v[3], sb), __funnelshift_r(v[3], v[4], sb));
     }
     for (uint32_t i = h + body + lane; i < nout; i += 32) q[i] = buf[skip + i];
+}
+
+// Fast path for a whole segment of a document laid out as lines of exactly
+// L data characters, each followed by CR LF, with L a multiple of 4 (76 for
+// MIME, 64 for PEM): no group of four then straddles a line break, and data
+// character j sits at raw position (L + 2) floor(j / L) + j mod L. The warp
+// decodes the groups straight from the raw bytes (four translations, one
+// 24-bit value and three output bytes a group), writing the output in place
+// below the bytes still to be read, and checks on the way that the segment
+// really has that layout: every byte it takes as data is in the alphabet
+// (not '=', not whitespace) and every byte it skips is whitespace. Only then
+// does it copy the output out (kLinesDone). If the count of data characters
+// before the segment does not fit the layout it returns kLinesNo at once,
+// the staged bytes untouched; if a check fails it returns kLinesSpoilt:
+// nothing has been written to global memory, but the staged bytes are
+// spoilt and the caller stages the segment again for the general path
+// (which also finds the segment's errors). S: the segment's raw start in the
+// document; P: the data characters before it; prev_last: the last data byte
+// before it.
+enum LinesResult { kLinesNo, kLinesDone, kLinesSpoilt };
+
+// The line layout's constants (L = 0: the input does not start with it).
+struct LineLayout {
+    uint32_t L = 0, Q = 0;        // data characters a line; raw bytes a line (L + 2)
+    uint32_t inv = 0;             // 2^32 / L rounded up: t / L = umulhi(t, inv) for t < 2^13
+    uint32_t seg_q = 0, seg_r = 0;  // kSeg = seg_q Q + seg_r
+    __device__ explicit LineLayout(uint32_t line_len) {
+        if (line_len) {
+            L = line_len;
+            Q = L + 2;
+            inv = 0xFFFFFFFFu / L + 1u;
+            seg_q = kSeg / Q;
+            seg_r = kSeg - seg_q * Q;
+        }
+    }
+};
+
+// S = k Q + r is the segment's raw start in the document.
+__device__ LinesResult decode_segment_lines(uint8_t* buf, const uint8_t* lut, int lane,
+                                            const LineLayout& ly, uint64_t k, uint32_t r,
+                                            uint64_t P, uint32_t prev_last,
+                                            uint8_t* __restrict__ out_doc) {
+    const uint32_t L = ly.L, Q = ly.Q;
+    // data characters before S, and before the segment's end, in the layout
+    if (k * L + (r < L ? r : L) != P) return kLinesNo;  // it does not hold up to here
+    uint64_t k1 = k + ly.seg_q;
+    uint32_t r1 = r + ly.seg_r;
+    if (r1 >= Q) {
+        r1 -= Q;
+        ++k1;
+    }
+    const uint64_t P1 = k1 * L + (r1 < L ? r1 : L);
+    const uint8_t* raw = buf + kLead;
+    // raw offset in the segment of data character P + d (d < 4096 + L): the
+    // column of P in its line, and the raw offset of that line's start
+    const uint32_t rP = r < L ? r : 0;
+    const int32_t off0 = r < L ? -int32_t(r) : int32_t(Q - r);
+    auto raw_of = [&](uint32_t d) -> uint32_t {
+        const uint32_t t = rP + d, line = __umulhi(t, ly.inv);
+        return uint32_t(off0) + line * 2u + t;  // line Q + (t - line L)
+    };
+    uint32_t bad = 0;
+    // the skipped bytes: break j at raw offsets L - r + j Q and one more
+    for (int32_t rel = int32_t(L) - int32_t(r) + lane * int32_t(Q); rel < int32_t(kSeg);
+         rel += 32 * int32_t(Q)) {
+        if (rel >= 0 && lut[raw[rel]] != kSpace) bad = 0x80u;
+        if (rel + 1 >= 0 && rel + 1 < int32_t(kSeg) && lut[raw[rel + 1]] != kSpace) bad = 0x80u;
+    }
+    // groups: the one holding P (edge A: it started before the segment), the
+    // whole ones, the one holding P1 - 1 (edge B: it ends after the segment)
+    const uint32_t rA = uint32_t(P & 3), rB = uint32_t(P1 & 3);
+    const uint32_t cA = rA ? 4 - rA : 0;              // edge A's output bytes; first whole d
+    const uint32_t nfull = uint32_t((P1 - P - cA) / 4);
+    const uint32_t base = kLead;                      // whole group i at buf[base + 3 i]
+    // edge values, one a lane: lanes 0..3 value t of group A (t = rA - 1 is
+    // the data byte before the segment), lanes 4..7 value t - 4 of group B
+    uint32_t ea = 0, eb = 0;
+    if (lane < 4 && rA && uint32_t(lane) + 1 >= rA) {
+        const uint32_t t = uint32_t(lane);
+        const uint32_t v = t + 1 == rA ? lut[prev_last] : lut[raw[raw_of(t - rA)]];
+        if (t + 1 != rA) bad |= v & 0x80u;
+        ea = (v & 63u) << (6 * (3 - t));
+    } else if (lane >= 4 && lane < 8 && rB >= 2 && uint32_t(lane) - 4 < rB) {
+        const uint32_t t = uint32_t(lane) - 4;
+        const uint32_t v = lut[raw[raw_of(cA + 4 * nfull + t)]];
+        bad |= v & 0x80u;
+        eb = (v & 63u) << (6 * (3 - t));
+    }
+    const uint32_t wA = __reduce_or_sync(0xffffffffu, ea);
+    const uint32_t wB = __reduce_or_sync(0xffffffffu, eb);
+    // whole groups, 128 a round: every read of a round comes before its
+    // writes, and a round's writes (below 384 (r + 1)) stay below the next
+    // round's reads (a group's raw offset is at least 4 times its index)
+    constexpr int kPer = 4;  // groups a lane per round, 32 apart
+    for (uint32_t i0 = 0; i0 < nfull; i0 += 32 * kPer) {
+        uint32_t q[kPer];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const uint32_t i = i0 + 32 * u + lane;
+            q[u] = 0;
+            if (i < nfull) {
+                const uint32_t ro = raw_of(cA + 4 * i);  // even
+                const uint32_t x = __byte_perm(*reinterpret_cast<const uint16_t*>(raw + ro),
+                                               *reinterpret_cast<const uint16_t*>(raw + ro + 2),
+                                               0x5410u);
+                const uint32_t a = lut[x & 0xFFu], b = lut[(x >> 8) & 0xFFu];
+                const uint32_t c = lut[(x >> 16) & 0xFFu], d = lut[x >> 24];
+                bad |= a | b | c | d;
+                q[u] = ((a * 64u + b) * 64u + c) * 64u + d;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const uint32_t i = i0 + 32 * u + lane;
+            if (i < nfull) {
+                uint8_t* o = buf + base + 3 * i;
+                o[0] = uint8_t(q[u] >> 16);
+                o[1] = uint8_t(q[u] >> 8);
+                o[2] = uint8_t(q[u]);
+            }
+        }
+        __syncwarp();
+    }
+    if (__any_sync(0xffffffffu, bad & 0x80u)) return kLinesSpoilt;
+    if (uint32_t(lane) < cA)  // bytes rA - 1 .. 2 of edge A
+        buf[base - cA + lane] = uint8_t(wA >> (16 - 8 * (rA - 1 + lane)));
+    if (rB >= 2 && uint32_t(lane) + 1 < rB)  // bytes 0 .. rB - 2 of edge B
+        buf[base + 3 * nfull + lane] = uint8_t(wB >> (16 - 8 * lane));
+    __syncwarp();
+    const uint64_t ob = bytes_for(P);
+    copy_out(buf, base - cA, uint32_t(bytes_for(P1) - ob), out_doc + ob, lane);
+    return kLinesDone;
 }
 
 __global__ void __launch_bounds__(kThreads, 6)
@@ -460,6 +619,7 @@ __global__ void __launch_bounds__(kThreads, 6)
     __syncthreads();  // the only block-wide barrier: tables and barriers ready
     const bool aligned = (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
     unsigned long long* timeout = status + 4;
+    const LineLayout ly{uint32_t(status[6])};
     const uint64_t GW = uint64_t(gridDim.x) * kWarps;
 
     // Starts the bulk copy of a whole, aligned segment into buffer k; false if
@@ -478,6 +638,15 @@ __global__ void __launch_bounds__(kThreads, 6)
     uint64_t seg = uint64_t(blockIdx.x) * kWarps + warp;
     int k = 0;
     bool by_copy = seg < nseg ? issue(seg, 0) : false;
+    // the segment's raw start as lk ly.Q + lr, stepped by dk ly.Q + dr
+    uint64_t lk = 0, dk = 0;
+    uint32_t lr = 0, dr = 0;
+    if (ly.L) {
+        lk = seg * kSeg / ly.Q;
+        lr = uint32_t(seg * kSeg - lk * ly.Q);
+        dk = GW * kSeg / ly.Q;
+        dr = uint32_t(GW * kSeg - dk * ly.Q);
+    }
     for (; seg < nseg; seg += GW, k ^= 1) {
         const uint64_t next = seg + GW;
         fence_proxy_async_smem();  // this lane's accesses to buffer k^1 before the copy below
@@ -511,7 +680,27 @@ __global__ void __launch_bounds__(kThreads, 6)
         const uint64_t P = st_count(blk) + st_count(pre);
         const uint32_t prev_last = st_flag(pre) ? st_last(pre) : st_flag(blk) ? st_last(blk) : 0u;
 
-        decode_segment(buf, lut, flags, lane, P, prev_last, base, dst, status);
+        const LinesResult fast =
+            ly.L && len == kSeg
+                ? decode_segment_lines(buf, lut, lane, ly, lk, lr, P, prev_last, dst)
+                : kLinesNo;
+        lk += dk;
+        lr += dr;
+        if (lr >= ly.Q) {
+            lr -= ly.Q;
+            ++lk;
+        }
+        if (fast != kLinesDone) {
+            if (fast == kLinesSpoilt) {  // stage the segment again
+                uint4 v[kRows];
+                load_rows(src + base, len, aligned, lane, v);
+#pragma unroll
+                for (int r = 0; r < kRows; ++r)
+                    *reinterpret_cast<uint4*>(buf + kLead + kRow * r + 16 * lane) = v[r];
+                __syncwarp();
+            }
+            decode_segment(buf, lut, flags, lane, P, prev_last, base, dst, status);
+        }
         by_copy = next_by_copy;
     }
 }
@@ -846,7 +1035,7 @@ cudaError_t launch_mime_decode(const uint8_t* src, uint64_t m, uint8_t* dst,
         mime_count_kernel<<<unsigned(nblk), kCountThreads, 0, st>>>(src, m, states, totals, nseg);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        mime_scan_kernel<<<1, kScanThreads, 0, st>>>(totals, nblk, status);
+        mime_scan_kernel<<<1, kScanThreads, 0, st>>>(totals, nblk, status, src, m);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         uint64_t grid = uint64_t(di.sm_count) *

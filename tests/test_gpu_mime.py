@@ -175,3 +175,67 @@ def test_stale_tile_memory_does_not_leak_into_seams(b64, orc):
         r, out = b64.mime_decode(torch.from_numpy(text).cuda(), std)
         assert r == data.size
         assert torch.equal(out, torch.from_numpy(data).cuda())
+
+
+# ---- documents laid out as lines of L data characters + CR LF (L a multiple
+#      of 4): the decode kernel's line fast path, and every way out of it
+
+
+@pytest.mark.parametrize("L", [4, 64, 76, 1020])
+@pytest.mark.parametrize("src_off", [0, 3])
+def test_line_layout_sizes(b64, orc, L, src_off):
+    std = b64.Alphabet.standard()
+    for i, n in enumerate([3 * TILE, 3 * TILE + 1, 3 * TILE + 2, 200_000, 1_000_003]):
+        text = wl.mime_wrap(orc.encode(wl.random_bytes(n, 700 + i)), line=L)
+        if i % 2:
+            text = np.concatenate([text, np.frombuffer(b"\r\n", np.uint8)])
+        assert check(b64, orc, text, std, orc.standard_alphabet(), True, src_off=src_off) == n
+
+
+def test_line_layout_broken(b64, orc):
+    """Errors and layout breaks in every position class of a 76-column
+    document: a data byte, a CR or LF replaced (by data, by a bad byte, by
+    a space), a line one group longer or shorter, '=' inside, a bad byte at
+    a segment's first or last byte."""
+    std, chars = b64.Alphabet.standard(), orc.standard_alphabet()
+    data = wl.random_bytes(300_000, 710)
+    good = wl.mime_wrap(orc.encode(data))
+    m = good.size
+    g = wl.rng(711)
+    edits = []
+    for seg in (0, 1, 7, 20, m // TILE - 1):
+        base = seg * TILE
+        for off in (0, 1, 2, 3, 75, 76, 77, 1000, TILE - 2, TILE - 1):
+            p = base + off
+            if p < m:
+                edits += [(p, 0x21), (p, ord("A")), (p, ord(" ")), (p, ord("="))]
+    crs = np.nonzero(good == 13)[0]
+    for p in crs[g.integers(0, crs.size, 20)]:
+        edits += [(int(p), ord("Q")), (int(p) + 1, ord("Q")), (int(p), 0xC3), (int(p), ord("\n"))]
+    for p, v in edits:
+        t = good.copy()
+        t[p] = v
+        check(b64, orc, t, std, chars, True)
+    # one line a group longer, one a group shorter (every later segment shifts)
+    lines = [good[k:k + 78] for k in range(0, m, 78)]
+    for j, delta in ((3, 4), (100, -4), (600, 4)):
+        t = [x.copy() for x in lines]
+        if delta > 0:
+            t[j] = np.concatenate([t[j][:76], np.frombuffer(b"ABCD", np.uint8), t[j][76:]])
+        else:
+            t[j] = np.concatenate([t[j][:72], t[j][76:]])
+        check(b64, orc, np.concatenate(t), std, chars, True)
+
+
+def test_line_layout_first_line_only(b64, orc):
+    """The first line looks like the layout, the rest does not: spaces,
+    LF-only breaks, random whitespace after the first line."""
+    std, chars = b64.Alphabet.standard(), orc.standard_alphabet()
+    text = orc.encode(wl.random_bytes(150_000, 720))
+    head = wl.mime_wrap(text[:152])          # two 76-character lines
+    rest = text[152:]
+    for k, tail in enumerate([wl.insert_spaces(rest, seed=721, count=3000),
+                              wl.mime_wrap(rest, line=76, eol=b"\n"),
+                              wl.mime_wrap(rest, line=72)]):
+        t = np.concatenate([head, np.frombuffer(b"\r\n", np.uint8), tail])
+        assert check(b64, orc, t, std, chars, True) == 150_000, k

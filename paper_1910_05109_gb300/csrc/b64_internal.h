@@ -99,7 +99,7 @@ cudaError_t launch_mime_decode(const uint8_t* src, uint64_t m, uint8_t* dst,
 // Self-test of the bounded wait: a barrier armed for a copy that never comes.
 cudaError_t launch_selftest_wait(int64_t* d_result, uint64_t wait_limit_ns, cudaStream_t stream);
 // Many MIME documents (BatchArgs: document i is src[src_off[i] .. src_off[i+1])
-// -> dst + dst_off[i], results[i]); the workspace holds 8 * (4 n + slots)
+// -> dst + dst_off[i], results[i]); the workspace holds 8 * (5 n + slots)
 // bytes, slots = total_bytes / 4096 + n + 1 (a smaller one makes every result
 // B64_E_INVAL on the device).
 size_t mime_batch_workspace_bytes(int64_t n, uint64_t total_bytes);

@@ -876,14 +876,30 @@ __global__ void __launch_bounds__(kCountThreads, 4)
 // characters and last data byte before the segment, within the document);
 // doc_state[d] = the whole document's.
 __global__ void __launch_bounds__(256)
-    mime_scan_docs_kernel(const int64_t* __restrict__ src_off, int64_t n,
-                          unsigned long long* __restrict__ states,
-                          unsigned long long* __restrict__ doc_state, uint64_t slot_cap) {
+    mime_scan_docs_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
+                          int64_t n, unsigned long long* __restrict__ states,
+                          unsigned long long* __restrict__ doc_state,
+                          unsigned long long* __restrict__ line_docs, uint64_t slot_cap) {
     const int lane = threadIdx.x & 31;
     if (doc_slots(src_off, n) > slot_cap) return;
     const int64_t gw = (int64_t(blockIdx.x) * 256 + threadIdx.x) >> 5;
     const int64_t GW = (int64_t(gridDim.x) * 256) >> 5;
     for (int64_t d = gw; d < n; d += GW) {
+        {  // line_docs[d]: the line layout's L, as status[6] of the single-document call
+            const uint8_t* p = src + src_off[d];
+            const uint64_t len = uint64_t(src_off[d + 1] - src_off[d]);
+            uint32_t f = kScanThreads;
+            for (uint32_t i = uint32_t(lane); i < kScanThreads && i < len; i += 32) {
+                const uint32_t c = p[i];
+                if ((c == '\r' || c == '\n' || c == ' ') && i < f) f = i;
+            }
+            f = __reduce_min_sync(0xffffffffu, f);
+            if (lane == 0) {
+                const bool lines = f < kScanThreads && f >= 4 && f % 4 == 0 &&
+                                   uint64_t(f) + 1 < len && p[f] == '\r' && p[f + 1] == '\n';
+                line_docs[d] = lines ? f : 0;
+            }
+        }
         const uint64_t first = doc_slot(src_off, d);
         const uint64_t segs = (uint64_t(src_off[d + 1] - src_off[d]) + kSeg - 1) / kSeg;
         uint64_t carry = 0, carry_key = 0;  // key: (segment + 1) << 8 | last byte
@@ -923,6 +939,7 @@ __global__ void __launch_bounds__(32 * kDocWarps, 6)
                             const __grid_constant__ BatchTables tabs,
                             const uint8_t* __restrict__ alph_id,
                             unsigned long long* __restrict__ status_docs,
+                            const unsigned long long* __restrict__ line_docs,
                             const unsigned long long* __restrict__ states, uint64_t slot_cap) {
     __shared__ uint8_t luts[kMaxAlphabets][256];  // 0..63, 0x80, kSpace
     __shared__ __align__(16) uint8_t bufs[kDocWarps][kBuf];
@@ -941,17 +958,32 @@ __global__ void __launch_bounds__(32 * kDocWarps, 6)
     for (uint64_t g = uint64_t(blockIdx.x) * kDocWarps + warp; g < nslots; g += GW) {
         DocSeg ds;
         if (!doc_segment(src, src_off, n, g, lane, &ds)) continue;
+        auto stage = [&] {
 #pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-            const uint32_t off = kRow * r + 16 * lane;
-            *reinterpret_cast<uint4*>(buf + kLead + off) = load_chunk_any(ds.p, off, ds.len, lo, hi);
-        }
-        __syncwarp();
+            for (int r = 0; r < kRows; ++r) {
+                const uint32_t off = kRow * r + 16 * lane;
+                *reinterpret_cast<uint4*>(buf + kLead + off) =
+                    load_chunk_any(ds.p, off, ds.len, lo, hi);
+            }
+            __syncwarp();
+        };
+        stage();
         const uint64_t pre = states[g];
         const int a = alph_id ? (alph_id[ds.d] & (kMaxAlphabets - 1)) : 0;
         const int flags = (tabs.padded[a] ? 1 : 0) | (tabs.canonical[a] ? 2 : 0);
-        decode_segment(buf, luts[a], flags, lane, st_count(pre), st_flag(pre) ? st_last(pre) : 0u,
-                       ds.k * kSeg, dst + dst_off[ds.d], status_docs + 3 * ds.d);
+        const uint64_t P = st_count(pre);
+        const uint32_t prev_last = st_flag(pre) ? st_last(pre) : 0u;
+        const LineLayout ly{uint32_t(line_docs[ds.d])};
+        LinesResult fast = kLinesNo;
+        if (ly.L && ds.len == kSeg) {
+            const uint64_t S = ds.k * kSeg, k = S / ly.Q;
+            fast = decode_segment_lines(buf, luts[a], lane, ly, k, uint32_t(S - k * ly.Q), P,
+                                        prev_last, dst + dst_off[ds.d]);
+        }
+        if (fast == kLinesSpoilt) stage();
+        if (fast != kLinesDone)
+            decode_segment(buf, luts[a], flags, lane, P, prev_last, ds.k * kSeg,
+                           dst + dst_off[ds.d], status_docs + 3 * ds.d);
         __syncwarp();  // the buffer is restaged for the next segment
     }
 }
@@ -1058,18 +1090,19 @@ cudaError_t launch_selftest_wait(int64_t* d_result, uint64_t wait_limit_ns, cuda
 
 size_t mime_batch_workspace_bytes(int64_t n, uint64_t total_bytes) {
     const uint64_t slots = total_bytes / kSeg + uint64_t(n) + 1;
-    return 8 * (4 * size_t(n) + size_t(slots));
+    return 8 * (5 * size_t(n) + size_t(slots));
 }
 
 cudaError_t launch_mime_decode_batch(const BatchArgs& a, const BatchTables& tabs, void* workspace,
                                      size_t workspace_bytes, cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
-    // [status: 3 words per document][document states: n][segment slots]
+    // [status: 3 words per document][document states: n][line layouts: n][segment slots]
     unsigned long long* status_docs = static_cast<unsigned long long*>(workspace);
     unsigned long long* doc_state = status_docs + 3 * a.n;
-    unsigned long long* states = doc_state + a.n;
+    unsigned long long* line_docs = doc_state + a.n;
+    unsigned long long* states = line_docs + a.n;
     const uint64_t words = workspace_bytes / 8;
-    const uint64_t slot_cap = words > 4 * uint64_t(a.n) ? words - 4 * uint64_t(a.n) : 0;
+    const uint64_t slot_cap = words > 5 * uint64_t(a.n) ? words - 5 * uint64_t(a.n) : 0;
     cudaError_t e = cudaMemsetAsync(status_docs, 0xFF, 3 * size_t(a.n) * sizeof(uint64_t), st);
     if (e != cudaSuccess) return e;
     const DeviceInfo& di = device_info();
@@ -1080,12 +1113,14 @@ cudaError_t launch_mime_decode_batch(const BatchArgs& a, const BatchTables& tabs
     if (e != cudaSuccess) return e;
     const uint64_t scan_blocks = (uint64_t(a.n) + 7) / 8;
     const unsigned sb = unsigned(scan_blocks < uint64_t(di.sm_count) * 8 ? scan_blocks : di.sm_count * 8);
-    mime_scan_docs_kernel<<<sb, 256, 0, st>>>(a.src_off, a.n, states, doc_state, slot_cap);
+    mime_scan_docs_kernel<<<sb, 256, 0, st>>>(a.src, a.src_off, a.n, states, doc_state, line_docs,
+                                              slot_cap);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int dd = occupancy(mime_decode_docs_kernel, 32 * kDocWarps, g_dd_occ[di.device & 63]);
     mime_decode_docs_kernel<<<unsigned(di.sm_count * dd), 32 * kDocWarps, 0, st>>>(
-        a.src, a.src_off, a.n, a.dst, a.dst_off, tabs, a.alph_id, status_docs, states, slot_cap);
+        a.src, a.src_off, a.n, a.dst, a.dst_off, tabs, a.alph_id, status_docs, line_docs, states,
+        slot_cap);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     mime_finalize_docs_kernel<<<unsigned((a.n + 255) / 256), 256, 0, st>>>(

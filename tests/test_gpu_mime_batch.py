@@ -18,6 +18,7 @@ pytestmark = pytest.mark.gpu
 
 STD = b"ABCDEFGHIJKLMNOPQRSTUVWXYZabcdefghijklmnopqrstuvwxyz0123456789+/"
 URL = STD[:62] + b"-_"
+TILE = 4096  # raw bytes per segment of the decode kernels
 
 
 @pytest.fixture(scope="module")
@@ -149,3 +150,37 @@ def test_small_workspace_and_empty_batch(b64, orc):
     # n == 0 enqueues nothing
     z = torch.zeros(1, dtype=torch.int64, device="cuda")
     b64.mime_decode_batch(torch.zeros(1, dtype=torch.uint8, device="cuda"), z, dst, z, alph)
+
+
+def test_line_layout_documents(b64, orc):
+    """Documents in the line layout (L = 64 or 76, CR LF) over several
+    segments, next to broken ones (a CR turned into data, a bad byte, a line
+    one group longer, LF-only breaks), at odd offsets in the batch."""
+    std, chars = b64.Alphabet.standard(), orc.standard_alphabet()
+    g = wl.rng(31)
+    docs = []
+    for i in range(60):
+        L = 64 if i % 2 else 76
+        n = int(g.integers(3 * TILE, 40_000))
+        t = wl.mime_wrap(orc.encode(wl.random_bytes(n, 9000 + i)), line=L)
+        kind = i % 6
+        if kind == 1:
+            crs = np.nonzero(t == 13)[0]
+            t = t.copy()
+            t[int(crs[g.integers(0, crs.size)])] = ord("A")
+        elif kind == 2:
+            t = t.copy()
+            t[int(g.integers(0, t.size))] = 0x21
+        elif kind == 3:
+            p = (L + 2) * int(g.integers(1, t.size // (L + 2) - 1))
+            t = np.concatenate([t[:p + L], np.frombuffer(b"QUJD", np.uint8), t[p + L:]])
+        elif kind == 4:
+            t = wl.mime_wrap(orc.encode(wl.random_bytes(n, 9000 + i)), line=L, eol=b"\n")
+        docs.append(np.ascontiguousarray(t, np.uint8))
+    for origin in (0, 5):
+        res, outs = run_batch(b64, docs, [std], None, origin)
+        for i, text in enumerate(docs):
+            want_r, want = orc.decode(text, chars, True, mime=True)
+            assert res[i] == want_r, (origin, i, res[i], want_r)
+            if want_r >= 0:
+                assert np.array_equal(outs[i][:want_r], want), i

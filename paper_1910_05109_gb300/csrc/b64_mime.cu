@@ -888,11 +888,16 @@ __global__ void __launch_bounds__(256)
         {  // line_docs[d]: the line layout's L, as status[6] of the single-document call
             const uint8_t* p = src + src_off[d];
             const uint64_t len = uint64_t(src_off[d + 1] - src_off[d]);
-            uint32_t f = kScanThreads;
-            for (uint32_t i = uint32_t(lane); i < kScanThreads && i < len; i += 32) {
-                const uint32_t c = p[i];
-                if ((c == '\r' || c == '\n' || c == ' ') && i < f) f = i;
+            uint32_t c[kScanThreads / 32];  // all loads issued before any is used
+#pragma unroll
+            for (int j = 0; j < kScanThreads / 32; ++j) {
+                const uint32_t i = uint32_t(lane) + 32 * j;
+                c[j] = i < len ? p[i] : 0u;
             }
+            uint32_t f = kScanThreads;
+#pragma unroll
+            for (int j = kScanThreads / 32 - 1; j >= 0; --j)
+                if (c[j] == '\r' || c[j] == '\n' || c[j] == ' ') f = uint32_t(lane) + 32 * j;
             f = __reduce_min_sync(0xffffffffu, f);
             if (lane == 0) {
                 const bool lines = f < kScanThreads && f >= 4 && f % 4 == 0 &&

@@ -35,12 +35,26 @@ namespace b64 {
 namespace {
 
 
-// Warps per block of the tile kernels: the per-warp staging buffers are
-// static shared memory, which must stay under 48 KiB per block.
-template <int U>
+#ifndef B64_BATCH_STAGES
+#define B64_BATCH_STAGES 2
+#endif
+
+// The tile kernels' shape for U units a lane: 8 warps a block, each with a
+// ring of kStages input staging buffers (kStages - 1 tiles in flight while
+// one is coded) and one output buffer, in dynamic shared memory. Two stages:
+// three and four measured no faster (the kernels are bound by instruction
+// issue, not by the latency of the copies) and cost resident blocks.
+template <int U, bool kDecode>
 struct TileShape {
-    static constexpr int kWarps = U >= 8 ? 4 : 8;
+    static constexpr int kWarps = 8;
     static constexpr int kThreads = 32 * kWarps;
+    static constexpr int kStages = B64_BATCH_STAGES;
+    static constexpr uint32_t T = kDecode ? 32 * U * 16 : 32 * U * 12;  // input per tile
+    static constexpr uint32_t TO = kDecode ? T / 4 * 3 : T / 3 * 4 + 4;  // output (+ padding)
+    static constexpr uint32_t SIN = T + 32;                    // room for a ragged start
+    static constexpr uint32_t SOUT = (TO + 16 + 15) & ~15u;     // rows stay 16-byte aligned
+    static constexpr size_t kSmem = size_t(kWarps) * (size_t(kStages) * SIN + SOUT);
+    static_assert(SIN % 16 == 0 && kStages >= 2 && kStages <= 32, "staging ring");
 };
 
 __host__ __device__ __forceinline__ uint64_t dec_body_length(uint64_t m) {
@@ -232,6 +246,65 @@ struct Cursor {
     }
 };
 
+// The warp's walk over its tiles with a ring of S staging buffers: the next
+// S - 1 tiles are described (by the warp-uniform cursor) and their bulk
+// copies started before the current one is coded; lane 0 keeps each tile's
+// description in the warp's ring in shared memory. process(t, sin) codes
+// one staged tile. Returns false if a bulk copy did not arrive in time.
+template <bool kDecode, int S, class Process>
+__device__ __forceinline__ bool walk_tiles(Cursor<kDecode>& cur, const uint8_t* __restrict__ src,
+                                           const int64_t* __restrict__ src_off,
+                                           const int64_t* __restrict__ dst_off,
+                                           const uint8_t* __restrict__ alph_id, int64_t n,
+                                           int64_t T, uint64_t src_end, uint8_t* sin_base,
+                                           uint32_t sin_stride, uint64_t* bars, Tile* ring,
+                                           uint32_t* ring_copy, int lane, Process process) {
+    bool more = true;
+    int64_t issued = 0;
+    auto issue = [&](int slot) {
+        Tile nt;
+        if (!cur.next(src_off, dst_off, alph_id, n, T, lane, &nt)) return false;
+        if (lane == 0) {
+            ring_copy[slot] = issue_tile_load(sin_base + size_t(slot) * sin_stride, src,
+                                              uint64_t(nt.a), uint64_t(nt.b), src_end, &bars[slot]);
+            ring[slot] = nt;
+        }
+        return true;
+    };
+    for (int k = 0; k < S - 1 && more; ++k) {
+        more = issue(k);
+        issued += more;
+    }
+    uint32_t phases = 0;
+    for (int64_t it = 0; it < issued; ++it) {
+        const int k = int(it % S);
+        fence_proxy_async_smem();  // this lane's reads of tile it - 1 before the copy below
+        __syncwarp();              // every lane is done with tile it - 1's buffer and ring slot
+        if (more) {
+            more = issue(int((it + S - 1) % S));
+            issued += more;
+        }
+        __syncwarp();              // ring writes of lane 0 are visible
+        const Tile t = ring[k];
+        const bool by_copy = ring_copy[k] != 0;
+        uint8_t* sin = sin_base + size_t(k) * sin_stride;
+        if (!tile_ready(by_copy, sin, &bars[k], phases, k, src, uint64_t(t.a), uint64_t(t.b),
+                        src_end, lane)) {
+            // let this copy and the later ones in flight land (bounded) before
+            // the block can exit; this tile's wait already flipped its parity
+            if (lane == 0)
+                for (int64_t i = it; i < issued; ++i) {
+                    const int kk = int(i % S);
+                    if (ring_copy[kk])
+                        mbar_wait(&bars[kk], ((phases >> kk) & 1u) ^ (i == it ? 1u : 0u));
+                }
+            return false;
+        }
+        process(t, sin);
+    }
+    return true;
+}
+
 // Each string's encoded length (encode results), one thread per string.
 __global__ void encode_results_kernel(const int64_t* __restrict__ src_off, int64_t n,
                                       const __grid_constant__ BatchTables tabs,
@@ -245,31 +318,30 @@ __global__ void encode_results_kernel(const int64_t* __restrict__ src_off, int64
 
 // ------------------------------------------------------------------ encode tiles
 template <int U>
-__global__ void __launch_bounds__(TileShape<U>::kThreads)
+__global__ void __launch_bounds__(TileShape<U, false>::kThreads)
     encode_batch_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
                         int64_t n, uint8_t* __restrict__ dst, const int64_t* __restrict__ dst_off,
                         const __grid_constant__ BatchTables tabs,
                         const uint8_t* __restrict__ alph_id) {
-    constexpr int kWarps = TileShape<U>::kWarps, kThreads = TileShape<U>::kThreads;
-    constexpr uint32_t T = 32 * U * 12;        // input bytes per tile
-    constexpr uint32_t TO = T / 3 * 4 + 4;     // output characters per tile (+ padding group)
-    constexpr uint32_t SIN = T + 32;           // staging room for a ragged start
-    constexpr uint32_t SOUT = (TO + 16 + 15) & ~15u;  // rows stay 16-byte aligned
+    using Sh = TileShape<U, false>;
+    constexpr int kWarps = Sh::kWarps, kThreads = Sh::kThreads, S = Sh::kStages;
+    constexpr uint32_t T = Sh::T, SIN = Sh::SIN, SOUT = Sh::SOUT;
+    extern __shared__ __align__(16) uint8_t smem[];  // [warp][stage] inputs, then [warp] outputs
     __shared__ __align__(16) uint8_t luts[kMaxAlphabets][64];
-    __shared__ __align__(16) uint8_t sin_all[kWarps][2][SIN];
-    __shared__ __align__(16) uint8_t sout_all[kWarps][SOUT];
-    __shared__ uint64_t bars[kWarps][2];
+    __shared__ uint64_t bars[kWarps][S];
+    __shared__ Tile ring[kWarps][S];
+    __shared__ uint32_t ring_copy[kWarps][S];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < kMaxAlphabets * 16; i += kThreads)
         reinterpret_cast<uint32_t*>(luts)[i] = tabs.enc[i / 16].w[i % 16];
     if (lane == 0) {
-        mbar_init(&bars[warp][0], 1);
-        mbar_init(&bars[warp][1], 1);
+        for (int k = 0; k < S; ++k) mbar_init(&bars[warp][k], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    uint8_t* sout = sout_all[warp];
+    uint8_t* sin_base = smem + size_t(warp) * S * SIN;
+    uint8_t* sout = smem + size_t(kWarps) * S * SIN + size_t(warp) * SOUT;
 
     const int64_t origin = src_off[0], bytes = src_off[n] - origin;
     const int64_t GW = int64_t(gridDim.x) * kWarps;
@@ -282,34 +354,8 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
     cur.s = cur.pos < src_off[n] ? warp_find_string(src_off, n, cur.pos, lane) : n;
     const uint64_t src_end = uint64_t(src_off[n]);
 
-    // The tile after the current one is described and its bulk copy started
-    // before the current one is coded (two staging buffers per warp).
-    Tile t, nt;
-    if (!cur.next(src_off, dst_off, alph_id, n, T, lane, &t)) return;
-    bool by_copy = false, n_by_copy = false;
-    if (lane == 0)
-        by_copy = issue_tile_load(sin_all[warp][0], src, uint64_t(t.a), uint64_t(t.b), src_end,
-                                  &bars[warp][0]);
-    by_copy = __shfl_sync(0xffffffffu, by_copy, 0);
-    uint32_t phases = 0;
-
-    for (int64_t it = 0;; ++it) {
-        const int k = int(it & 1);
-        fence_proxy_async_smem();  // this lane's reads of tile t - 1 before the copy below
-        __syncwarp();              // every lane is done with the other buffer
-        const bool more = cur.next(src_off, dst_off, alph_id, n, T, lane, &nt);
-        if (more) {
-            if (lane == 0)
-                n_by_copy = issue_tile_load(sin_all[warp][k ^ 1], src, uint64_t(nt.a),
-                                            uint64_t(nt.b), src_end, &bars[warp][k ^ 1]);
-            n_by_copy = __shfl_sync(0xffffffffu, n_by_copy, 0);
-        }
-        uint8_t* sin = sin_all[warp][k];
+    auto process = [&](const Tile& t, const uint8_t* sin) {
         const uint64_t a = uint64_t(t.a), b = uint64_t(t.b);
-        if (!tile_ready(by_copy, sin, &bars[warp][k], phases, k, src, a, b, src_end, lane)) {
-            if (lane == 0) atomicOr(&g_fault, 1u);
-            return;
-        }
         const bool last = t.b == t.s1;
         const int ai = int(t.id);
         const uint8_t* lut = luts[ai];
@@ -353,40 +399,40 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
         const uint64_t rel = a - uint64_t(t.s0);  // a multiple of 3
         warp_stage_out(dst + t.d0 + rel / 3 * 4, sout, nout, lane);
         __syncwarp();  // sout is rewritten by the next tile
-        if (!more) break;
-        t = nt;
-        by_copy = n_by_copy;
+    };
+    if (!walk_tiles<false, S>(cur, src, src_off, dst_off, alph_id, n, T, src_end, sin_base, SIN,
+                              bars[warp], ring[warp], ring_copy[warp], lane, process)) {
+        if (lane == 0) atomicOr(&g_fault, 1u);
     }
 }
 
 // ------------------------------------------------------------------ decode tiles
 template <int U>
-__global__ void __launch_bounds__(TileShape<U>::kThreads)
+__global__ void __launch_bounds__(TileShape<U, true>::kThreads)
     decode_batch_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
                         int64_t n, uint8_t* __restrict__ dst, const int64_t* __restrict__ dst_off,
                         const __grid_constant__ BatchTables tabs,
                         const uint8_t* __restrict__ alph_id,
                         unsigned long long* __restrict__ err) {
-    constexpr int kWarps = TileShape<U>::kWarps, kThreads = TileShape<U>::kThreads;
-    constexpr uint32_t T = 32 * U * 16;  // characters per tile
-    constexpr uint32_t TO = T / 4 * 3;   // output bytes per tile
-    constexpr uint32_t SIN = T + 32;
-    constexpr uint32_t SOUT = (TO + 16 + 15) & ~15u;
+    using Sh = TileShape<U, true>;
+    constexpr int kWarps = Sh::kWarps, kThreads = Sh::kThreads, S = Sh::kStages;
+    constexpr uint32_t T = Sh::T, SIN = Sh::SIN, SOUT = Sh::SOUT;
+    extern __shared__ __align__(16) uint8_t smem[];  // [warp][stage] inputs, then [warp] outputs
     __shared__ __align__(16) uint8_t luts[kMaxAlphabets][256];
-    __shared__ __align__(16) uint8_t sin_all[kWarps][2][SIN];
-    __shared__ __align__(16) uint8_t sout_all[kWarps][SOUT];
-    __shared__ uint64_t bars[kWarps][2];
+    __shared__ uint64_t bars[kWarps][S];
+    __shared__ Tile ring[kWarps][S];
+    __shared__ uint32_t ring_copy[kWarps][S];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < kMaxAlphabets * 64; i += kThreads)
         reinterpret_cast<uint32_t*>(luts)[i] = tabs.dec[i / 64].w[i % 64];
     if (lane == 0) {
-        mbar_init(&bars[warp][0], 1);
-        mbar_init(&bars[warp][1], 1);
+        for (int k = 0; k < S; ++k) mbar_init(&bars[warp][k], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    uint8_t* sout = sout_all[warp];
+    uint8_t* sin_base = smem + size_t(warp) * S * SIN;
+    uint8_t* sout = smem + size_t(kWarps) * S * SIN + size_t(warp) * SOUT;
 
     const int64_t origin = src_off[0], bytes = src_off[n] - origin;
     const int64_t GW = int64_t(gridDim.x) * kWarps;
@@ -399,34 +445,8 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
     cur.s = cur.pos < src_off[n] ? warp_find_string(src_off, n, cur.pos, lane) : n;
     const uint64_t src_end = uint64_t(src_off[n]);
 
-    // The tile after the current one is described and its bulk copy started
-    // before the current one is coded (two staging buffers per warp).
-    Tile t, nt;
-    if (!cur.next(src_off, dst_off, alph_id, n, T, lane, &t)) return;
-    bool by_copy = false, n_by_copy = false;
-    if (lane == 0)
-        by_copy = issue_tile_load(sin_all[warp][0], src, uint64_t(t.a), uint64_t(t.b), src_end,
-                                  &bars[warp][0]);
-    by_copy = __shfl_sync(0xffffffffu, by_copy, 0);
-    uint32_t phases = 0;
-
-    for (int64_t it = 0;; ++it) {
-        const int k = int(it & 1);
-        fence_proxy_async_smem();  // this lane's reads of tile t - 1 before the copy below
-        __syncwarp();              // every lane is done with the other buffer
-        const bool more = cur.next(src_off, dst_off, alph_id, n, T, lane, &nt);
-        if (more) {
-            if (lane == 0)
-                n_by_copy = issue_tile_load(sin_all[warp][k ^ 1], src, uint64_t(nt.a),
-                                            uint64_t(nt.b), src_end, &bars[warp][k ^ 1]);
-            n_by_copy = __shfl_sync(0xffffffffu, n_by_copy, 0);
-        }
-        uint8_t* sin = sin_all[warp][k];
+    auto process = [&](const Tile& t, const uint8_t* sin) {
         const uint64_t a = uint64_t(t.a), b = uint64_t(t.b);
-        if (!tile_ready(by_copy, sin, &bars[warp][k], phases, k, src, a, b, src_end, lane)) {
-            if (lane == 0) atomicOr(&g_fault, 1u);
-            return;
-        }
         const uint8_t* lut = luts[t.id];
         const uint32_t nchars = uint32_t(b - a);  // a multiple of 4
         const uint32_t delta = uint32_t((reinterpret_cast<uintptr_t>(src + a)) & 15);
@@ -475,15 +495,18 @@ __global__ void __launch_bounds__(TileShape<U>::kThreads)
                 }
             }
         }
-        const uint64_t wmin = warp_min_u64(first);
-        if (lane == 0 && wmin != kNoError) atomicMin(&err[t.s], (unsigned long long)wmin);
+        if (__any_sync(0xffffffffu, first != kNoError)) {  // rare: a bad byte in the tile
+            const uint64_t wmin = warp_min_u64(first);
+            if (lane == 0) atomicMin(&err[t.s], (unsigned long long)wmin);
+        }
         __syncwarp();
         const uint64_t rel = a - uint64_t(t.s0);  // a multiple of 4
         warp_stage_out(dst + t.d0 + rel / 4 * 3, sout, nchars / 4 * 3, lane);
         __syncwarp();  // sout is rewritten by the next tile
-        if (!more) break;
-        t = nt;
-        by_copy = n_by_copy;
+    };
+    if (!walk_tiles<true, S>(cur, src, src_off, dst_off, alph_id, n, T, src_end, sin_base, SIN,
+                             bars[warp], ring[warp], ring_copy[warp], lane, process)) {
+        if (lane == 0) atomicOr(&g_fault, 1u);
     }
 }
 
@@ -551,17 +574,25 @@ __global__ void decode_batch_finalize_kernel(const uint8_t* __restrict__ src,
 
 struct Occ {
     std::once_flag once;
+    cudaError_t err = cudaSuccess;
     int ctas = 1;
 };
 
+// Allows the kernel its dynamic shared memory and returns its resident
+// blocks per SM (once per kernel and device).
 template <class K>
-int occupancy(K kernel, int threads, Occ& occ) {
+int occupancy(K kernel, int threads, size_t smem, Occ& occ, cudaError_t* err) {
     std::call_once(occ.once, [&] {
+        if (smem > 48 * 1024)
+            occ.err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           int(smem));
         int c = 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, kernel, threads, 0) != cudaSuccess)
+        if (occ.err == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, kernel, threads, smem) != cudaSuccess)
             c = 1;
         occ.ctas = c > 0 ? c : 1;
     });
+    *err = occ.err;
     return occ.ctas;
 }
 
@@ -571,11 +602,13 @@ int unit_slot(int units) { return units == 1 ? 0 : units == 2 ? 1 : units == 4 ?
 
 template <int U>
 cudaError_t launch_encode_tiles(const BatchArgs& a, const BatchTables& t, cudaStream_t st) {
+    using Sh = TileShape<U, false>;
     const DeviceInfo& di = device_info();
-    constexpr int threads = TileShape<U>::kThreads;
-    const int occ =
-        occupancy(encode_batch_kernel<U>, threads, g_enc_occ[unit_slot(U)][di.device & 63]);
-    encode_batch_kernel<U><<<unsigned(di.sm_count * occ), threads, 0, st>>>(
+    cudaError_t e = cudaSuccess;
+    const int occ = occupancy(encode_batch_kernel<U>, Sh::kThreads, Sh::kSmem,
+                              g_enc_occ[unit_slot(U)][di.device & 63], &e);
+    if (e != cudaSuccess) return e;
+    encode_batch_kernel<U><<<unsigned(di.sm_count * occ), Sh::kThreads, Sh::kSmem, st>>>(
         a.src, a.src_off, a.n, a.dst, a.dst_off, t, a.alph_id);
     return cudaGetLastError();
 }
@@ -583,11 +616,13 @@ cudaError_t launch_encode_tiles(const BatchArgs& a, const BatchTables& t, cudaSt
 template <int U>
 cudaError_t launch_decode_tiles(const BatchArgs& a, const BatchTables& t,
                                 unsigned long long* err, cudaStream_t st) {
+    using Sh = TileShape<U, true>;
     const DeviceInfo& di = device_info();
-    constexpr int threads = TileShape<U>::kThreads;
-    const int occ =
-        occupancy(decode_batch_kernel<U>, threads, g_dec_occ[unit_slot(U)][di.device & 63]);
-    decode_batch_kernel<U><<<unsigned(di.sm_count * occ), threads, 0, st>>>(
+    cudaError_t e = cudaSuccess;
+    const int occ = occupancy(decode_batch_kernel<U>, Sh::kThreads, Sh::kSmem,
+                              g_dec_occ[unit_slot(U)][di.device & 63], &e);
+    if (e != cudaSuccess) return e;
+    decode_batch_kernel<U><<<unsigned(di.sm_count * occ), Sh::kThreads, Sh::kSmem, st>>>(
         a.src, a.src_off, a.n, a.dst, a.dst_off, t, a.alph_id, err);
     return cudaGetLastError();
 }

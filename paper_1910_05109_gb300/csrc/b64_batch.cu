@@ -39,14 +39,17 @@ namespace {
 #define B64_BATCH_STAGES 2
 #endif
 
-// The tile kernels' shape for U units a lane: 8 warps a block, each with a
-// ring of kStages input staging buffers (kStages - 1 tiles in flight while
-// one is coded) and one output buffer, in dynamic shared memory. Two stages:
-// three and four measured no faster (the kernels are bound by instruction
-// issue, not by the latency of the copies) and cost resident blocks.
+// The tile kernels' shape for U units a lane: 8 warps a block (4 for U = 8,
+// measured faster there), each with a ring of kStages input staging buffers
+// (kStages - 1 tiles in flight while one is coded) and one output buffer, in
+// dynamic shared memory. Two stages: three and four measured no faster (the
+// kernels are bound by instruction issue, not by the latency of the copies)
+// and cost resident blocks. The encoder keeps the 64-entry table: the
+// character-pair table of the single-buffer encoder measured slower here
+// (its 8 KiB a block cost resident blocks).
 template <int U, bool kDecode>
 struct TileShape {
-    static constexpr int kWarps = 8;
+    static constexpr int kWarps = U >= 8 ? 4 : 8;
     static constexpr int kThreads = 32 * kWarps;
     static constexpr int kStages = B64_BATCH_STAGES;
     static constexpr uint32_t T = kDecode ? 32 * U * 16 : 32 * U * 12;  // input per tile
@@ -578,14 +581,15 @@ struct Occ {
     int ctas = 1;
 };
 
-// Allows the kernel its dynamic shared memory and returns its resident
-// blocks per SM (once per kernel and device).
+// Allows the kernel up to max_smem bytes of dynamic shared memory and
+// returns its resident blocks per SM with smem bytes (once per kernel,
+// device and smem).
 template <class K>
-int occupancy(K kernel, int threads, size_t smem, Occ& occ, cudaError_t* err) {
+int occupancy(K kernel, int threads, size_t smem, size_t max_smem, Occ& occ, cudaError_t* err) {
     std::call_once(occ.once, [&] {
-        if (smem > 48 * 1024)
+        if (max_smem > 48 * 1024)
             occ.err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           int(smem));
+                                           int(max_smem));
         int c = 1;
         if (occ.err == cudaSuccess &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, kernel, threads, smem) != cudaSuccess)
@@ -605,7 +609,7 @@ cudaError_t launch_encode_tiles(const BatchArgs& a, const BatchTables& t, cudaSt
     using Sh = TileShape<U, false>;
     const DeviceInfo& di = device_info();
     cudaError_t e = cudaSuccess;
-    const int occ = occupancy(encode_batch_kernel<U>, Sh::kThreads, Sh::kSmem,
+    const int occ = occupancy(encode_batch_kernel<U>, Sh::kThreads, Sh::kSmem, Sh::kSmem,
                               g_enc_occ[unit_slot(U)][di.device & 63], &e);
     if (e != cudaSuccess) return e;
     encode_batch_kernel<U><<<unsigned(di.sm_count * occ), Sh::kThreads, Sh::kSmem, st>>>(
@@ -619,7 +623,7 @@ cudaError_t launch_decode_tiles(const BatchArgs& a, const BatchTables& t,
     using Sh = TileShape<U, true>;
     const DeviceInfo& di = device_info();
     cudaError_t e = cudaSuccess;
-    const int occ = occupancy(decode_batch_kernel<U>, Sh::kThreads, Sh::kSmem,
+    const int occ = occupancy(decode_batch_kernel<U>, Sh::kThreads, Sh::kSmem, Sh::kSmem,
                               g_dec_occ[unit_slot(U)][di.device & 63], &e);
     if (e != cudaSuccess) return e;
     decode_batch_kernel<U><<<unsigned(di.sm_count * occ), Sh::kThreads, Sh::kSmem, st>>>(

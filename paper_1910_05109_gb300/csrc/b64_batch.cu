@@ -129,6 +129,27 @@ __device__ __forceinline__ bool tile_ready(bool by_copy, uint8_t* sbuf, uint64_t
     return true;
 }
 
+// load16_shifted for off mod 16 the same in every lane (lanes 16 bytes
+// apart): two aligned 128-bit loads, which keep the shared-memory
+// accesses free of bank conflicts (five 32-bit loads 16 bytes apart would
+// meet four lanes in a bank), then funnel shifts. Reads up to 32 bytes
+// from off & ~15.
+__device__ __forceinline__ uint4 load16_shifted_u(const uint8_t* sbuf, uint32_t off) {
+    const uint32_t A = off & ~15u, r = off & 15u, sb = 8 * (r & 3u);
+    const uint4 a = *reinterpret_cast<const uint4*>(sbuf + A);
+    if (r == 0) return a;
+    const uint4 b = *reinterpret_cast<const uint4*>(sbuf + A + 16);
+    uint32_t v0, v1, v2, v3, v4;
+    switch (r >> 2) {  // the same in every lane
+        case 0: v0 = a.x; v1 = a.y; v2 = a.z; v3 = a.w; v4 = b.x; break;
+        case 1: v0 = a.y; v1 = a.z; v2 = a.w; v3 = b.x; v4 = b.y; break;
+        case 2: v0 = a.z; v1 = a.w; v2 = b.x; v3 = b.y; v4 = b.z; break;
+        default: v0 = a.w; v1 = b.x; v2 = b.y; v3 = b.z; v4 = b.w; break;
+    }
+    return make_uint4(__funnelshift_r(v0, v1, sb), __funnelshift_r(v1, v2, sb),
+                      __funnelshift_r(v2, v3, sb), __funnelshift_r(v3, v4, sb));
+}
+
 // Writes sbuf[0 .. len) to global q (any alignment): aligned 16-byte stores
 // for the middle, byte stores for the ragged head and tail. Warp-collective.
 __device__ __forceinline__ void warp_stage_out(uint8_t* q, const uint8_t* sbuf, uint32_t len,
@@ -137,10 +158,9 @@ __device__ __forceinline__ void warp_stage_out(uint8_t* q, const uint8_t* sbuf, 
     const uint32_t h = head < len ? head : len;
     if (lane < int(h)) q[lane] = sbuf[lane];
     const uint32_t body = (len - h) & ~15u;
-    const uint32_t sh = h & 3;
     for (uint32_t k = lane; k < body / 16; k += 32) {
         const uint32_t off = h + 16 * k;
-        *reinterpret_cast<uint4*>(q + off) = load16_shifted(sbuf, off, sh);
+        *reinterpret_cast<uint4*>(q + off) = load16_shifted_u(sbuf, off);
     }
     for (uint32_t i = h + body + lane; i < len; i += 32) q[i] = sbuf[i];
 }
@@ -453,13 +473,12 @@ __global__ void __launch_bounds__(TileShape<U, true>::kThreads)
         const uint8_t* lut = luts[t.id];
         const uint32_t nchars = uint32_t(b - a);  // a multiple of 4
         const uint32_t delta = uint32_t((reinterpret_cast<uintptr_t>(src + a)) & 15);
-        const uint32_t sh = delta & 3;
         uint64_t first = kNoError;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint32_t j = lane + 32 * u;
             if (16 * j + 16 <= nchars) {
-                const uint4 c = load16_shifted(sin, delta + 16 * j, sh);
+                const uint4 c = load16_shifted_u(sin, delta + 16 * j);
                 uint32_t e = 0;
                 const uint3 o = pack4x24(decode4(c.x, lut, e), decode4(c.y, lut, e),
                                          decode4(c.z, lut, e), decode4(c.w, lut, e));

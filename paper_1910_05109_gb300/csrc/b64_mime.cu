@@ -33,6 +33,7 @@
 #include <mutex>
 
 #include "b64_internal.h"
+#include "b64_smem.cuh"
 
 namespace b64 {
 namespace {
@@ -936,6 +937,25 @@ __global__ void __launch_bounds__(256)
 }
 
 constexpr int kDocWarps = 4;
+constexpr uint32_t kStage = kSeg + 32;  // a segment's 16-byte aligned span
+// status word 0 of a document whose bulk copy did not arrive (offsets are
+// below 2^62): its result becomes B64_E_TIMEOUT
+constexpr uint64_t kDocTimedOut = uint64_t(1) << 62;
+
+// Starts the bulk copy of the 16-byte aligned span around a document
+// segment's bytes into stage (byte 0 of the segment lands at
+// stage[p & 15]); false (nothing started) when the span would leave the
+// batch's input [lo, hi). Lane 0 only.
+__device__ __forceinline__ bool issue_doc_segment(uint8_t* stage, const DocSeg& ds,
+                                                  const uint8_t* lo, const uint8_t* hi,
+                                                  uint64_t* bar) {
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(ds.p) & ~uintptr_t(15);
+    const uintptr_t a1 = (reinterpret_cast<uintptr_t>(ds.p) + ds.len + 15) & ~uintptr_t(15);
+    if (a0 < reinterpret_cast<uintptr_t>(lo) || a1 > reinterpret_cast<uintptr_t>(hi)) return false;
+    mbar_arrive_expect_tx(bar, uint32_t(a1 - a0));
+    bulk_load(stage, reinterpret_cast<const void*>(a0), uint32_t(a1 - a0), bar);
+    return true;
+}
 
 __global__ void __launch_bounds__(32 * kDocWarps, 6)
     mime_decode_docs_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
@@ -948,11 +968,17 @@ __global__ void __launch_bounds__(32 * kDocWarps, 6)
                             const unsigned long long* __restrict__ states, uint64_t slot_cap) {
     __shared__ uint8_t luts[kMaxAlphabets][256];  // 0..63, 0x80, kSpace
     __shared__ __align__(16) uint8_t bufs[kDocWarps][kBuf];
+    __shared__ __align__(16) uint8_t stages[kDocWarps][kStage];
+    __shared__ uint64_t bars[kDocWarps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < kMaxAlphabets * 64; i += 32 * kDocWarps)
         reinterpret_cast<uint32_t*>(luts)[i] = tabs.dec[i / 64].w[i % 64];
     __syncthreads();
     if (tid < kMaxAlphabets) luts[tid]['\r'] = luts[tid]['\n'] = luts[tid][' '] = uint8_t(kSpace);
+    if (lane == 0) {
+        mbar_init(&bars[warp], 1);
+        fence_mbar_init();
+    }
     __syncthreads();
     const uint64_t nslots = doc_slots(src_off, n);
     if (nslots > slot_cap) return;
@@ -960,10 +986,26 @@ __global__ void __launch_bounds__(32 * kDocWarps, 6)
     const uint8_t* hi = src + src_off[n];
     uint8_t* buf = bufs[warp];
     const uint64_t GW = uint64_t(gridDim.x) * kDocWarps;
-    for (uint64_t g = uint64_t(blockIdx.x) * kDocWarps + warp; g < nslots; g += GW) {
-        DocSeg ds;
-        if (!doc_segment(src, src_off, n, g, lane, &ds)) continue;
-        auto stage = [&] {
+
+    // The next used slot at or after g (false: none left), its segment in *ds.
+    auto next_slot = [&](uint64_t& g, DocSeg* ds) {
+        for (; g < nslots; g += GW)
+            if (doc_segment(src, src_off, n, g, lane, ds)) return true;
+        return false;
+    };
+    // Slot g's segment arrives in the warp's stage buffer by a bulk copy
+    // started while the slot before it is decoded, and is re-aligned into
+    // buf; then the next slot's copy is started.
+    uint64_t g = uint64_t(blockIdx.x) * kDocWarps + warp;
+    DocSeg ds;
+    bool have = next_slot(g, &ds), by_copy = false;
+    uint8_t* stg = stages[warp];
+    if (have && lane == 0) by_copy = issue_doc_segment(stg, ds, lo, hi, &bars[warp]);
+    by_copy = __shfl_sync(0xffffffffu, by_copy, 0);
+    uint32_t phase = 0;
+    while (have) {
+        unsigned long long* st3 = status_docs + 3 * ds.d;
+        auto stage_plain = [&] {
 #pragma unroll
             for (int r = 0; r < kRows; ++r) {
                 const uint32_t off = kRow * r + 16 * lane;
@@ -972,7 +1014,44 @@ __global__ void __launch_bounds__(32 * kDocWarps, 6)
             }
             __syncwarp();
         };
-        stage();
+        if (by_copy) {
+            const bool ok = __all_sync(0xffffffffu, wait_copy(&bars[warp], phase, kWaitLimitNs));
+            phase ^= 1u;
+            if (!ok) {
+                if (lane == 0) {
+                    atomicMin(st3, (unsigned long long)kDocTimedOut);
+                    atomicOr(&g_fault, 1u);
+                }
+                return;
+            }
+            // re-align: segment byte i is at stg[(p & 15) + i]; bytes at or
+            // past len read as spaces
+            const uint32_t delta = uint32_t(reinterpret_cast<uintptr_t>(ds.p) & 15);
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                const uint32_t off = kRow * r + 16 * lane;
+                uint4 v;
+                if (off + 16 <= ds.len) {
+                    v = load16_shifted_u(stg, delta + off);
+                } else {
+                    uint8_t* bv = reinterpret_cast<uint8_t*>(&v);
+                    for (int j = 0; j < 16; ++j)
+                        bv[j] = off + j < ds.len ? stg[delta + off + j] : uint8_t(' ');
+                }
+                *reinterpret_cast<uint4*>(buf + kLead + off) = v;
+            }
+        } else {
+            stage_plain();
+        }
+        // the stage buffer is read; the next slot's copy may overwrite it
+        fence_proxy_async_smem();
+        __syncwarp();
+        uint64_t g2 = g + GW;
+        DocSeg ds2;
+        const bool have2 = next_slot(g2, &ds2);
+        bool by_copy2 = false;
+        if (have2 && lane == 0) by_copy2 = issue_doc_segment(stg, ds2, lo, hi, &bars[warp]);
+        by_copy2 = __shfl_sync(0xffffffffu, by_copy2, 0);
         const uint64_t pre = states[g];
         const int a = alph_id ? (alph_id[ds.d] & (kMaxAlphabets - 1)) : 0;
         const int flags = (tabs.padded[a] ? 1 : 0) | (tabs.canonical[a] ? 2 : 0);
@@ -981,15 +1060,19 @@ __global__ void __launch_bounds__(32 * kDocWarps, 6)
         const LineLayout ly{uint32_t(line_docs[ds.d])};
         LinesResult fast = kLinesNo;
         if (ly.L && ds.len == kSeg) {
-            const uint64_t S = ds.k * kSeg, k = S / ly.Q;
-            fast = decode_segment_lines(buf, luts[a], lane, ly, k, uint32_t(S - k * ly.Q), P,
+            const uint64_t S = ds.k * kSeg, lk = S / ly.Q;
+            fast = decode_segment_lines(buf, luts[a], lane, ly, lk, uint32_t(S - lk * ly.Q), P,
                                         prev_last, dst + dst_off[ds.d]);
         }
-        if (fast == kLinesSpoilt) stage();
+        if (fast == kLinesSpoilt) stage_plain();
         if (fast != kLinesDone)
             decode_segment(buf, luts[a], flags, lane, P, prev_last, ds.k * kSeg,
-                           dst + dst_off[ds.d], status_docs + 3 * ds.d);
+                           dst + dst_off[ds.d], st3);
         __syncwarp();  // the buffer is restaged for the next segment
+        g = g2;
+        ds = ds2;
+        have = have2;
+        by_copy = by_copy2;
     }
 }
 
@@ -1004,6 +1087,10 @@ __global__ void mime_finalize_docs_kernel(const uint8_t* __restrict__ src,
     if (d >= n) return;
     if (doc_slots(src_off, n) > slot_cap) {
         results[d] = B64_E_INVAL;
+        return;
+    }
+    if (status_docs[3 * d] == kDocTimedOut) {
+        results[d] = B64_E_TIMEOUT;
         return;
     }
     const int a = alph_id ? (alph_id[d] & (kMaxAlphabets - 1)) : 0;

@@ -31,6 +31,7 @@
 // time; one that runs out sets the timeout word, and the result becomes
 // B64_E_TIMEOUT.
 #include <mutex>
+#include <type_traits>
 
 #include "b64_internal.h"
 #include "b64_smem.cuh"
@@ -557,13 +558,13 @@ __device__ LinesResult decode_segment_lines(uint8_t* buf, const uint8_t* lut, in
     // writes, and a round's writes (below 384 (r + 1)) stay below the next
     // round's reads (a group's raw offset is at least 4 times its index)
     constexpr int kPer = 4;  // groups a lane per round, 32 apart
-    for (uint32_t i0 = 0; i0 < nfull; i0 += 32 * kPer) {
+    auto round = [&](uint32_t i0, auto checked) {
         uint32_t q[kPer];
 #pragma unroll
         for (int u = 0; u < kPer; ++u) {
             const uint32_t i = i0 + 32 * u + lane;
             q[u] = 0;
-            if (i < nfull) {
+            if (!decltype(checked)::value || i < nfull) {
                 const uint32_t ro = raw_of(cA + 4 * i);  // even
                 const uint32_t x = __byte_perm(*reinterpret_cast<const uint16_t*>(raw + ro),
                                                *reinterpret_cast<const uint16_t*>(raw + ro + 2),
@@ -578,7 +579,7 @@ __device__ LinesResult decode_segment_lines(uint8_t* buf, const uint8_t* lut, in
 #pragma unroll
         for (int u = 0; u < kPer; ++u) {
             const uint32_t i = i0 + 32 * u + lane;
-            if (i < nfull) {
+            if (!decltype(checked)::value || i < nfull) {
                 uint8_t* o = buf + base + 3 * i;
                 o[0] = uint8_t(q[u] >> 16);
                 o[1] = uint8_t(q[u] >> 8);
@@ -586,7 +587,10 @@ __device__ LinesResult decode_segment_lines(uint8_t* buf, const uint8_t* lut, in
             }
         }
         __syncwarp();
-    }
+    };
+    const uint32_t nwhole = nfull / (32 * kPer) * (32 * kPer);
+    for (uint32_t i0 = 0; i0 < nwhole; i0 += 32 * kPer) round(i0, std::false_type{});
+    if (nwhole < nfull) round(nwhole, std::true_type{});
     if (__any_sync(0xffffffffu, bad & 0x80u)) return kLinesSpoilt;
     if (uint32_t(lane) < cA)  // bytes rA - 1 .. 2 of edge A
         buf[base - cA + lane] = uint8_t(wA >> (16 - 8 * (rA - 1 + lane)));

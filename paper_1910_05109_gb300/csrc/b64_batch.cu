@@ -366,18 +366,27 @@ __global__ void __launch_bounds__(TileShape<U, false>::kThreads)
         const uint32_t triples = nbytes / 3;
         const uint32_t delta = uint32_t((reinterpret_cast<uintptr_t>(src + a)) & 15);
         const uint32_t sh = delta & 3;
+        if (nbytes == T) {  // a whole tile: every unit is whole, no tests
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint32_t j = lane + 32 * u;
-            if (4 * j + 4 <= triples) {
+            for (int u = 0; u < U; ++u) {
+                const uint32_t j = lane + 32 * u;
                 const uint4 x = load16_shifted(sin, delta + 12 * j, sh);
                 reinterpret_cast<uint4*>(sout)[j] = encode12(x.x, x.y, x.z, lut);
-            } else if (4 * j < triples) {
-                for (uint32_t q = 4 * j; q < triples; ++q) {
-                    const uint32_t p = delta + 3 * q;
-                    const uint32_t s1b = sin[p], s2b = sin[p + 1], s3b = sin[p + 2];
-                    reinterpret_cast<uint32_t*>(sout)[q] =
-                        encode_gathered(s2b | (s1b << 8) | (s3b << 16) | (s2b << 24), lut);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t j = lane + 32 * u;
+                if (4 * j + 4 <= triples) {
+                    const uint4 x = load16_shifted(sin, delta + 12 * j, sh);
+                    reinterpret_cast<uint4*>(sout)[j] = encode12(x.x, x.y, x.z, lut);
+                } else if (4 * j < triples) {
+                    for (uint32_t q = 4 * j; q < triples; ++q) {
+                        const uint32_t p = delta + 3 * q;
+                        const uint32_t s1b = sin[p], s2b = sin[p + 1], s3b = sin[p + 2];
+                        reinterpret_cast<uint32_t*>(sout)[q] =
+                            encode_gathered(s2b | (s1b << 8) | (s3b << 16) | (s2b << 24), lut);
+                    }
                 }
             }
         }

@@ -332,11 +332,18 @@ __global__ void decode_finalize_kernel(const uint8_t* __restrict__ src, uint64_t
 // groups before decoding any of them; each block folds its first bad offset
 // into its shared memory, and after a cluster barrier block 0 reads the
 // others' through distributed shared memory and applies the tail rules.
+// One block up to kSmallSingle characters; above, a cluster of one block per
+// kSmallCtaBytes, at most kSmallCtas blocks (16, a non-portable cluster size,
+// where the device can co-schedule it; else 8). Measured in CUDA graphs: a
+// 188 KB input in 5.2 us with 16 blocks against 7.1 us with three 64 KiB
+// blocks.
 constexpr int kSmallThreads = 1024;
-constexpr int kSmallPer = 16;                                   // groups per thread
-constexpr int kSmallCtas = 8;                                   // portable cluster size
+constexpr int kSmallPer = 16;                                   // groups per thread, at most
+constexpr int kSmallCtas = 16;
 constexpr uint64_t kSmallPerCta = uint64_t(kSmallThreads) * kSmallPer * 4;  // 64 KiB
-constexpr uint64_t kSmallMax = kSmallPerCta * kSmallCtas;                   // 512 KiB
+constexpr uint64_t kSmallMax = kSmallPerCta * 8;                            // 512 KiB
+constexpr uint64_t kSmallSingle = 32u << 10;
+constexpr uint64_t kSmallCtaBytes = 8u << 10;
 
 template <bool kCluster>
 __global__ void __launch_bounds__(kSmallThreads)
@@ -449,12 +456,48 @@ cudaError_t launch_body(Kernel kernel, KernelSetup& ks, int threads, size_t smem
     return launch_dependent(kernel, unsigned(grid), threads, smem, stream, src, body, dst, tab, d_err);
 }
 
+struct ClusterLimit {
+    std::once_flag once;
+    int ctas = 8;
+};
+ClusterLimit g_small_limit[64];
+
+// The largest cluster of the small-input kernel this device co-schedules:
+// kSmallCtas if it allows that non-portable size, else the portable 8.
+int small_cluster_limit() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    ClusterLimit& cl = g_small_limit[dev & 63];
+    std::call_once(cl.once, [&] {
+        if (cudaFuncSetAttribute(decode_small_kernel<true>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        cudaLaunchConfig_t c = {};
+        c.gridDim = dim3(kSmallCtas);
+        c.blockDim = dim3(kSmallThreads);
+        int size = 0;
+        if (cudaOccupancyMaxPotentialClusterSize(&size, decode_small_kernel<true>, &c) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        if (size > 8) cl.ctas = size < kSmallCtas ? size : kSmallCtas;
+    });
+    return cl.ctas;
+}
+
 }  // namespace
 
 cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const DecodeTable& tab,
                           int flags, int64_t* d_result, cudaStream_t stream) {
     if (m <= kSmallMax) {
-        const unsigned ctas = unsigned(m <= kSmallPerCta ? 1 : (m + kSmallPerCta - 1) / kSmallPerCta);
+        const int max_ctas = small_cluster_limit();
+        uint64_t want = (m + kSmallCtaBytes - 1) / kSmallCtaBytes;
+        if (want > uint64_t(max_ctas)) want = uint64_t(max_ctas);
+        // m <= 8 blocks x kSmallPerCta, so 8 blocks always hold every group
+        const unsigned ctas = unsigned(m <= kSmallSingle ? 1 : (want < 2 ? 2 : want));
         if (ctas == 1) {
             decode_small_kernel<false><<<1, kSmallThreads, 0, stream>>>(src, m, dst, tab, flags,
                                                                         d_result);

@@ -96,9 +96,11 @@ SIZES = sorted(set(
     [k * ENC_CHUNK + d for k in (1, 2, 3, 7) for d in (-3, -2, -1, 0, 1, 2, 3)] +
     [k * DEC_CHUNK // 4 * 3 + d for k in (1, 2, 5) for d in (-4, -1, 0, 1, 4)] +
     list(wl.TABLE2_SIZES[:3]) + [1_048_575, 1_048_576, 1_048_577, 3_000_001] +
-    # encoded length around 64 KiB (one block / a cluster of blocks) and around
-    # 512 KiB (one cluster / the three-launch decode)
-    [49_149, 49_150, 49_151, 49_152, 49_153, 49_155, 98_304, 98_305,
+    # encoded length around 32 KiB (one block / a cluster of blocks), 64 KiB
+    # and 128 KiB (8 and 16 blocks of 8 KiB) and 512 KiB (one cluster / the
+    # three-launch decode)
+    [24_573, 24_574, 24_575, 24_576, 24_577, 24_579,
+     49_149, 49_150, 49_151, 49_152, 49_153, 49_155, 98_304, 98_305, 98_307,
      393_213, 393_215, 393_216, 393_217, 393_219]))
 
 

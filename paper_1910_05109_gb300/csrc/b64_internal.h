@@ -44,9 +44,9 @@ uint32_t encode_fault_flag(bool clear);
 
 // ---- decode (b64_decode.cu)
 // Enqueues the strict decode of m characters; *d_result receives the length
-// or -(offset+1). Up to 512 KiB of input takes one launch (one cluster of
-// up to 8 blocks); larger inputs
-// start with a memset of *d_result, then the body kernel and the tail kernel.
+// or -(offset+1). Up to 512 KiB of input takes one launch (one block, or one
+// cluster of up to 16 blocks); larger inputs take a kernel that initialises
+// *d_result, then the body kernel and the tail kernel.
 cudaError_t launch_decode(const uint8_t* src, uint64_t m, uint8_t* dst, const DecodeTable& tab,
                           int flags, int64_t* d_result, cudaStream_t stream);
 uint32_t decode_fault_flag(bool clear);

@@ -195,6 +195,16 @@ __global__ void __launch_bounds__(kCountThreads, 4)
     }
 }
 
+// The layout word of an input whose first whitespace byte is at f (f = the
+// input's first 1024 bytes if none): L = f if f is a multiple of 4
+// (at least 4) and the bytes at f are CR LF or a lone LF.
+__device__ __forceinline__ uint32_t line_layout_word(const uint8_t* p, uint64_t len, uint32_t f) {
+    if (f >= 1024 || f < 4 || f % 4 != 0 || uint64_t(f) >= len) return 0;
+    if (p[f] == '\n') return f | (1u << 16);
+    if (p[f] == '\r' && uint64_t(f) + 1 < len && p[f + 1] == '\n') return f | (2u << 16);
+    return 0;
+}
+
 // ---------------------------------------------------------------- 2. scan
 // One block: totals[b] = (data characters before block b, last data byte
 // before it); status[5] = the whole input's (count, last data byte).
@@ -208,9 +218,9 @@ __global__ void __launch_bounds__(kScanThreads)
     __shared__ uint64_t warp_key[kScanThreads / 32];
     __shared__ uint32_t first_space;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // status[6] = L if the input starts with a line of L data characters and
-    // CR LF, L a multiple of 4 below kScanThreads (the decode kernel's
-    // line-layout fast path, checked there segment by segment), else 0
+    // status[6] = the line layout word if the input starts with a line of L
+    // data characters and CR LF or LF, L a multiple of 4 below 1024 (the
+    // decode kernel's fast path, checked there segment by segment), else 0
     if (tid == 0) first_space = kScanThreads;
     __syncthreads();
     if (uint64_t(tid) < m) {
@@ -218,12 +228,7 @@ __global__ void __launch_bounds__(kScanThreads)
         if (c == '\r' || c == '\n' || c == ' ') atomicMin(&first_space, uint32_t(tid));
     }
     __syncthreads();
-    if (tid == 0) {
-        const uint32_t f = first_space;
-        const bool lines = f < kScanThreads && f >= 4 && f % 4 == 0 && uint64_t(f) + 1 < m &&
-                           src[f] == '\r' && src[f + 1] == '\n';
-        status[6] = lines ? f : 0;
-    }
+    if (tid == 0) status[6] = line_layout_word(src, m, first_space);
     uint64_t carry = 0, carry_key = 0;  // key: (block + 1) << 8 | last byte, 0 = none
     for (uint64_t base = 0; base < nblk; base += uint64_t(kScanThreads) * kScanItems) {
         const uint64_t i0 = base + uint64_t(tid) * kScanItems;
@@ -486,14 +491,16 @@ __device__ __forceinline__ void copy_out(const uint8_t* buf, uint32_t skip, uint
 enum LinesResult { kLinesNo, kLinesDone, kLinesSpoilt };
 
 // The line layout's constants (L = 0: the input does not start with it).
+// word: L | eol << 16 (eol = 2 for CR LF, 1 for LF), 0 for none.
 struct LineLayout {
-    uint32_t L = 0, Q = 0;        // data characters a line; raw bytes a line (L + 2)
-    uint32_t inv = 0;             // 2^32 / L rounded up: t / L = umulhi(t, inv) for t < 2^13
-    uint32_t seg_q = 0, seg_r = 0;  // kSeg = seg_q Q + seg_r
-    __device__ explicit LineLayout(uint32_t line_len) {
-        if (line_len) {
-            L = line_len;
-            Q = L + 2;
+    uint32_t L = 0, eol = 0, Q = 0;  // data characters a line; break bytes; raw bytes a line
+    uint32_t inv = 0;                // 2^32 / L rounded up: t / L = umulhi(t, inv) for t < 2^13
+    uint32_t seg_q = 0, seg_r = 0;   // kSeg = seg_q Q + seg_r
+    __device__ explicit LineLayout(uint32_t word) {
+        if (word) {
+            L = word & 0xFFFFu;
+            eol = word >> 16;
+            Q = L + eol;
             inv = 0xFFFFFFFFu / L + 1u;
             seg_q = kSeg / Q;
             seg_r = kSeg - seg_q * Q;
@@ -501,12 +508,14 @@ struct LineLayout {
     }
 };
 
-// S = k Q + r is the segment's raw start in the document.
-__device__ LinesResult decode_segment_lines(uint8_t* buf, const uint8_t* lut, int lane,
-                                            const LineLayout& ly, uint64_t k, uint32_t r,
-                                            uint64_t P, uint32_t prev_last,
-                                            uint8_t* __restrict__ out_doc) {
-    const uint32_t L = ly.L, Q = ly.Q;
+
+// S = k Q + r is the segment's raw start in the document; kCrLf: breaks
+// are CR LF (ly.eol == 2), so every group starts at an even raw offset.
+template <bool kCrLf>
+__device__ LinesResult decode_lines(uint8_t* buf, const uint8_t* lut, int lane,
+                                    const LineLayout& ly, uint64_t k, uint32_t r, uint64_t P,
+                                    uint32_t prev_last, uint8_t* __restrict__ out_doc) {
+    const uint32_t L = ly.L, Q = ly.Q, eol = kCrLf ? 2u : 1u;
     // data characters before S, and before the segment's end, in the layout
     if (k * L + (r < L ? r : L) != P) return kLinesNo;  // it does not hold up to here
     uint64_t k1 = k + ly.seg_q;
@@ -523,14 +532,16 @@ __device__ LinesResult decode_segment_lines(uint8_t* buf, const uint8_t* lut, in
     const int32_t off0 = r < L ? -int32_t(r) : int32_t(Q - r);
     auto raw_of = [&](uint32_t d) -> uint32_t {
         const uint32_t t = rP + d, line = __umulhi(t, ly.inv);
-        return uint32_t(off0) + line * 2u + t;  // line Q + (t - line L)
+        return uint32_t(off0) + line * eol + t;  // line Q + (t - line L)
     };
     uint32_t bad = 0;
-    // the skipped bytes: break j at raw offsets L - r + j Q and one more
+    // the skipped bytes: break j at raw offsets L - r + j Q (and one more
+    // for CR LF)
     for (int32_t rel = int32_t(L) - int32_t(r) + lane * int32_t(Q); rel < int32_t(kSeg);
          rel += 32 * int32_t(Q)) {
         if (rel >= 0 && lut[raw[rel]] != kSpace) bad = 0x80u;
-        if (rel + 1 >= 0 && rel + 1 < int32_t(kSeg) && lut[raw[rel + 1]] != kSpace) bad = 0x80u;
+        if (kCrLf && rel + 1 >= 0 && rel + 1 < int32_t(kSeg) && lut[raw[rel + 1]] != kSpace)
+            bad = 0x80u;
     }
     // groups: the one holding P (edge A: it started before the segment), the
     // whole ones, the one holding P1 - 1 (edge B: it ends after the segment)
@@ -565,10 +576,15 @@ __device__ LinesResult decode_segment_lines(uint8_t* buf, const uint8_t* lut, in
             const uint32_t i = i0 + 32 * u + lane;
             q[u] = 0;
             if (!decltype(checked)::value || i < nfull) {
-                const uint32_t ro = raw_of(cA + 4 * i);  // even
-                const uint32_t x = __byte_perm(*reinterpret_cast<const uint16_t*>(raw + ro),
-                                               *reinterpret_cast<const uint16_t*>(raw + ro + 2),
-                                               0x5410u);
+                const uint32_t ro = raw_of(cA + 4 * i);
+                uint32_t x;
+                if constexpr (kCrLf) {  // even offsets: two 16-bit loads
+                    x = __byte_perm(*reinterpret_cast<const uint16_t*>(raw + ro),
+                                    *reinterpret_cast<const uint16_t*>(raw + ro + 2), 0x5410u);
+                } else {  // any offset: two aligned words, one shift
+                    const uint32_t* w = reinterpret_cast<const uint32_t*>(raw + (ro & ~3u));
+                    x = __funnelshift_r(w[0], w[1], 8 * (ro & 3u));
+                }
                 const uint32_t a = lut[x & 0xFFu], b = lut[(x >> 8) & 0xFFu];
                 const uint32_t c = lut[(x >> 16) & 0xFFu], d = lut[x >> 24];
                 bad |= a | b | c | d;
@@ -600,6 +616,15 @@ __device__ LinesResult decode_segment_lines(uint8_t* buf, const uint8_t* lut, in
     const uint64_t ob = bytes_for(P);
     copy_out(buf, base - cA, uint32_t(bytes_for(P1) - ob), out_doc + ob, lane);
     return kLinesDone;
+}
+
+__device__ __forceinline__ LinesResult decode_segment_lines(uint8_t* buf, const uint8_t* lut,
+                                                            int lane, const LineLayout& ly,
+                                                            uint64_t k, uint32_t r, uint64_t P,
+                                                            uint32_t prev_last,
+                                                            uint8_t* __restrict__ out_doc) {
+    return ly.eol == 2 ? decode_lines<true>(buf, lut, lane, ly, k, r, P, prev_last, out_doc)
+                       : decode_lines<false>(buf, lut, lane, ly, k, r, P, prev_last, out_doc);
 }
 
 __global__ void __launch_bounds__(kThreads, 6)
@@ -904,11 +929,7 @@ __global__ void __launch_bounds__(256)
             for (int j = kScanThreads / 32 - 1; j >= 0; --j)
                 if (c[j] == '\r' || c[j] == '\n' || c[j] == ' ') f = uint32_t(lane) + 32 * j;
             f = __reduce_min_sync(0xffffffffu, f);
-            if (lane == 0) {
-                const bool lines = f < kScanThreads && f >= 4 && f % 4 == 0 &&
-                                   uint64_t(f) + 1 < len && p[f] == '\r' && p[f + 1] == '\n';
-                line_docs[d] = lines ? f : 0;
-            }
+            if (lane == 0) line_docs[d] = line_layout_word(p, len, f);
         }
         const uint64_t first = doc_slot(src_off, d);
         const uint64_t segs = (uint64_t(src_off[d + 1] - src_off[d]) + kSeg - 1) / kSeg;

@@ -182,14 +182,33 @@ def test_stale_tile_memory_does_not_leak_into_seams(b64, orc):
 
 
 @pytest.mark.parametrize("L", [4, 64, 76, 1020])
+@pytest.mark.parametrize("eol", [b"\r\n", b"\n"])
 @pytest.mark.parametrize("src_off", [0, 3])
-def test_line_layout_sizes(b64, orc, L, src_off):
+def test_line_layout_sizes(b64, orc, L, eol, src_off):
     std = b64.Alphabet.standard()
     for i, n in enumerate([3 * TILE, 3 * TILE + 1, 3 * TILE + 2, 200_000, 1_000_003]):
-        text = wl.mime_wrap(orc.encode(wl.random_bytes(n, 700 + i)), line=L)
+        text = wl.mime_wrap(orc.encode(wl.random_bytes(n, 700 + i)), line=L, eol=eol)
         if i % 2:
-            text = np.concatenate([text, np.frombuffer(b"\r\n", np.uint8)])
+            text = np.concatenate([text, np.frombuffer(eol, np.uint8)])
         assert check(b64, orc, text, std, orc.standard_alphabet(), True, src_off=src_off) == n
+
+
+def test_line_layout_lf_broken(b64, orc):
+    """LF-only lines: a data byte where an LF belongs, an LF replaced by a
+    bad byte or by CR, an extra LF, a line one group short."""
+    std, chars = b64.Alphabet.standard(), orc.standard_alphabet()
+    good = wl.mime_wrap(orc.encode(wl.random_bytes(250_000, 730)), line=76, eol=b"\n")
+    lfs = np.nonzero(good == 10)[0]
+    g = wl.rng(731)
+    for p in lfs[g.integers(0, lfs.size, 12)]:
+        for v in (ord("Q"), 0x21, 13, 32):
+            t = good.copy()
+            t[int(p)] = v
+            check(b64, orc, t, std, chars, True)
+    p = int(lfs[40])
+    check(b64, orc, np.concatenate([good[:p], np.frombuffer(b"\n", np.uint8), good[p:]]), std,
+          chars, True)
+    check(b64, orc, np.concatenate([good[:p - 4], good[p:]]), std, chars, True)
 
 
 def test_line_layout_broken(b64, orc):

@@ -174,8 +174,12 @@ def test_line_layout_documents(b64, orc):
         elif kind == 3:
             p = (L + 2) * int(g.integers(1, t.size // (L + 2) - 1))
             t = np.concatenate([t[:p + L], np.frombuffer(b"QUJD", np.uint8), t[p + L:]])
-        elif kind == 4:
+        elif kind in (4, 5):  # LF-only lines (kind 5 with a CR in one break)
             t = wl.mime_wrap(orc.encode(wl.random_bytes(n, 9000 + i)), line=L, eol=b"\n")
+            if kind == 5:
+                lfs = np.nonzero(t == 10)[0]
+                t = t.copy()
+                t[int(lfs[g.integers(0, lfs.size)])] = 13
         docs.append(np.ascontiguousarray(t, np.uint8))
     for origin in (0, 5):
         res, outs = run_batch(b64, docs, [std], None, origin)

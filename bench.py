@@ -167,6 +167,19 @@ def oracle_pass(data: np.ndarray, threads: int) -> tuple[int, float]:
     return consumed, time.perf_counter() - t0
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu's, else the platform's)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(data: np.ndarray) -> dict:
     cores = len(os.sched_getaffinity(0))
     consumed, sec = 0, 0.0
@@ -179,7 +192,8 @@ def cpu_baseline(data: np.ndarray) -> dict:
             "sample": (f"three full steps (1 GiB each; encode+decode, standard and url tables) "
                        f"split over {cores} threads at 3-byte boundaries; {sec:.2f} s wall"),
             "value_1core": c1 / s1 / 1e9,
-            "sample_1core": "first 64 MiB of the same buffer, one thread, both tables"}
+            "sample_1core": "first 64 MiB of the same buffer, one thread, both tables",
+            "cpu": cpu_model()}
 
 
 # ---------------------------------------------------------------- helpers
@@ -236,6 +250,7 @@ def run_reference(args):
           "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
           "config": {"workload": WORKLOAD, "bytes": N_BYTES, "sample_bytes": sample.size},
           "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                           "cpu": cpu_model(),
                            "sample": "first 128 MiB of the 1 GiB buffer per step, both tables, "
                                      f"split over {cores} threads"},
           "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,

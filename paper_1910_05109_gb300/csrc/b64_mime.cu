@@ -100,20 +100,48 @@ __device__ __forceinline__ uint32_t byte_of(uint4 w, int k) {
     return __byte_perm(x, 0, 0x4440u + (k & 3));
 }
 
-// Data characters of a 16-byte chunk (exact: every byte but CR, LF, space)
-// and, if any, the position + 1 (within the segment; off = the chunk's
-// position) and value of the last one, as (pos + 1) << 8 | byte in *key.
-__device__ __forceinline__ uint32_t chunk_count(uint4 w, uint32_t off, uint32_t* key) {
+// Data characters of a 16-byte chunk (exact: every byte but CR, LF, space).
+__device__ __forceinline__ uint32_t chunk_data(uint4 w) {
+    return __popc(~space_bytes(w.x) & 0x80808080u) + __popc(~space_bytes(w.y) & 0x80808080u) +
+           __popc(~space_bytes(w.z) & 0x80808080u) + __popc(~space_bytes(w.w) & 0x80808080u);
+}
+
+// The position + 1 (within the segment; off = the chunk's position) and value
+// of a chunk's last data character, as (pos + 1) << 8 | byte; 0 if none.
+__device__ __forceinline__ uint32_t chunk_last(uint4 w, uint32_t off) {
     const uint32_t d0 = ~space_bytes(w.x) & 0x80808080u, d1 = ~space_bytes(w.y) & 0x80808080u;
     const uint32_t d2 = ~space_bytes(w.z) & 0x80808080u, d3 = ~space_bytes(w.w) & 0x80808080u;
-    const uint32_t c = __popc(d0) + __popc(d1) + __popc(d2) + __popc(d3);
     // highest data byte: the top set bit of the four masks laid end to end
     const uint32_t hi = d3 ? 12 + (31 - __clz(d3)) / 8
                       : d2 ? 8 + (31 - __clz(d2)) / 8
                       : d1 ? 4 + (31 - __clz(d1)) / 8
                       : d0 ? (31 - __clz(d0)) / 8 : 0xFFu;
-    if (hi != 0xFFu) *key = ((off + hi + 1) << 8) | byte_of(w, int(hi));
-    return c;
+    return hi != 0xFFu ? ((off + hi + 1) << 8) | byte_of(w, int(hi)) : 0u;
+}
+
+// Data characters of a lane's kRows chunks (row r at kRow r + 16 lane), and
+// the key of its last data character (chunk_last of the last chunk holding
+// one). When every lane has data in its last row (the usual case), the key
+// comes from that row alone; otherwise from each row that holds data, in
+// order. Each row is used once, in order, so the rows need no longer life.
+__device__ __forceinline__ uint32_t rows_count(const uint4 (&v)[kRows], int lane, uint32_t* key) {
+    const uint32_t last = chunk_data(v[kRows - 1]);
+    uint32_t count = last, k = 0;
+    if (__all_sync(0xffffffffu, last != 0)) {
+        k = chunk_last(v[kRows - 1], kRow * (kRows - 1) + 16 * lane);
+#pragma unroll
+        for (int r = 0; r < kRows - 1; ++r) count += chunk_data(v[r]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < kRows - 1; ++r) {
+            const uint32_t c = chunk_data(v[r]);
+            count += c;
+            if (c) k = chunk_last(v[r], kRow * r + 16 * lane);
+        }
+        if (last) k = chunk_last(v[kRows - 1], kRow * (kRows - 1) + 16 * lane);
+    }
+    *key = k;
+    return count;
 }
 
 // Segment bytes [0, len) in registers, row r of this lane in v[r]; bytes past
@@ -168,9 +196,7 @@ __global__ void __launch_bounds__(kCountThreads, 4)
             const uint32_t len = uint32_t(m - base < kSeg ? m - base : kSeg);
             uint4 v[kRows];
             load_rows(src + base, len, aligned, lane, v);
-#pragma unroll
-            for (int r = 0; r < kRows; ++r) count += chunk_count(v[r], kRow * r + 16 * lane, &key);
-            count = __reduce_add_sync(0xffffffffu, count);
+            count = __reduce_add_sync(0xffffffffu, rows_count(v, lane, &key));
             key = __reduce_max_sync(0xffffffffu, key);
         }
         if (lane == 0) {
@@ -890,13 +916,11 @@ __global__ void __launch_bounds__(kCountThreads, 4)
     for (uint64_t g = gw; g < nslots; g += GW) {
         DocSeg ds;
         if (!doc_segment(src, src_off, n, g, lane, &ds)) continue;
-        uint32_t count = 0, key = 0;
+        uint32_t key = 0;
+        uint4 v[kRows];
 #pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-            const uint32_t off = kRow * r + 16 * lane;
-            count += chunk_count(load_chunk_any(ds.p, off, ds.len, lo, hi), off, &key);
-        }
-        count = __reduce_add_sync(0xffffffffu, count);
+        for (int r = 0; r < kRows; ++r) v[r] = load_chunk_any(ds.p, kRow * r + 16 * lane, ds.len, lo, hi);
+        const uint32_t count = __reduce_add_sync(0xffffffffu, rows_count(v, lane, &key));
         key = __reduce_max_sync(0xffffffffu, key);
         if (lane == 0) states[g] = make_state(key != 0, key & 0xFFu, count);
     }

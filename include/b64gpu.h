@@ -169,7 +169,8 @@ int b64_mime_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b6
  * (room for b64_decoded_max_length of its length, e.g. from
  * b64_batch_offsets with decode != 0), with alphabets[alph_id[i]] (alph_id
  * NULL: alphabet 0); results[i] receives its length or -(offset+1), offset
- * within the document. workspace: device memory of
+ * within the document, or B64_E_TIMEOUT (a bounded wait on one of its
+ * segments' bulk copies ran out). workspace: device memory of
  * b64_mime_batch_workspace_size(n, src_off[n] - src_off[0]) bytes, 8-byte
  * aligned; if the documents' total turns out larger than the size was
  * computed for, every results[i] becomes B64_E_INVAL and nothing else is

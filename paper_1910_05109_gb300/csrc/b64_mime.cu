@@ -885,23 +885,47 @@ struct DocSeg {
     const uint8_t* p;  // its first byte
 };
 
-// Slot g's document segment; false for a slot no segment uses.
-__device__ __forceinline__ bool doc_segment(const uint8_t* src, const int64_t* __restrict__ src_off,
-                                            int64_t n, uint64_t g, int lane, DocSeg* ds) {
-    const int64_t d = warp_find_doc(src_off, n, g, lane);
-    const uint64_t k = g - doc_slot(src_off, d);
-    const uint64_t len = uint64_t(src_off[d + 1] - src_off[d]);
-    if (k * kSeg >= len) return false;
-    ds->d = d;
-    ds->k = k;
-    ds->len = uint32_t(len - k * kSeg < kSeg ? len - k * kSeg : kSeg);
-    ds->p = src + src_off[d] + k * kSeg;
-    return true;
-}
-
 __device__ __forceinline__ uint64_t doc_slots(const int64_t* __restrict__ src_off, int64_t n) {
     return uint64_t(src_off[n] - src_off[0]) / kSeg + uint64_t(n) + 1;
 }
+
+// A warp's walk over its own contiguous range of slots [g0, g1): the
+// document of the last slot found is remembered, so the 32-way document
+// search runs once per document the range touches instead of once per slot.
+struct SlotWalk {
+    uint64_t g, g1;
+    int64_t d = -1;                  // the remembered document
+    uint64_t first = 0, nseg = 0;    // its first slot and its segments
+    __device__ SlotWalk(uint64_t nslots, uint64_t warp, uint64_t warps) {
+        const uint64_t per = (nslots + warps - 1) / warps;
+        g = warp * per < nslots ? warp * per : nslots;
+        g1 = g + per < nslots ? g + per : nslots;
+    }
+    // The next used slot of the range (its segment in *ds, its slot in *slot);
+    // false when the range is done. Warp-collective.
+    __device__ bool next(const uint8_t* src, const int64_t* __restrict__ src_off, int64_t n,
+                         int lane, DocSeg* ds, uint64_t* slot) {
+        for (; g < g1; ++g) {
+            if (d < 0 || g < first || g >= first + nseg) {
+                if (d >= 0 && g >= first + nseg && d + 1 < n && g < doc_slot(src_off, d + 1))
+                    continue;  // a slot between the remembered document and the next
+                d = warp_find_doc(src_off, n, g, lane);
+                first = doc_slot(src_off, d);
+                nseg = (uint64_t(src_off[d + 1] - src_off[d]) + kSeg - 1) / kSeg;
+                if (g >= first + nseg) continue;  // an unused slot
+            }
+            const uint64_t k = g - first;
+            const uint64_t len = uint64_t(src_off[d + 1] - src_off[d]);
+            ds->d = d;
+            ds->k = k;
+            ds->len = uint32_t(len - k * kSeg < kSeg ? len - k * kSeg : kSeg);
+            ds->p = src + src_off[d] + k * kSeg;
+            *slot = g++;
+            return true;
+        }
+        return false;
+    }
+};
 
 __global__ void __launch_bounds__(kCountThreads, 4)
     mime_count_docs_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
@@ -913,9 +937,10 @@ __global__ void __launch_bounds__(kCountThreads, 4)
     const uint64_t GW = (uint64_t(gridDim.x) * kCountThreads) >> 5;
     const uint8_t* lo = src + src_off[0];
     const uint8_t* hi = src + src_off[n];
-    for (uint64_t g = gw; g < nslots; g += GW) {
-        DocSeg ds;
-        if (!doc_segment(src, src_off, n, g, lane, &ds)) continue;
+    SlotWalk walk(nslots, gw, GW);
+    DocSeg ds;
+    uint64_t g;
+    while (walk.next(src, src_off, n, lane, &ds, &g)) {
         uint32_t key = 0;
         uint4 v[kRows];
 #pragma unroll
@@ -1036,18 +1061,13 @@ __global__ void __launch_bounds__(32 * kDocWarps, 6)
     uint8_t* buf = bufs[warp];
     const uint64_t GW = uint64_t(gridDim.x) * kDocWarps;
 
-    // The next used slot at or after g (false: none left), its segment in *ds.
-    auto next_slot = [&](uint64_t& g, DocSeg* ds) {
-        for (; g < nslots; g += GW)
-            if (doc_segment(src, src_off, n, g, lane, ds)) return true;
-        return false;
-    };
+    SlotWalk walk(nslots, uint64_t(blockIdx.x) * kDocWarps + warp, GW);
     // Slot g's segment arrives in the warp's stage buffer by a bulk copy
     // started while the slot before it is decoded, and is re-aligned into
     // buf; then the next slot's copy is started.
-    uint64_t g = uint64_t(blockIdx.x) * kDocWarps + warp;
+    uint64_t g = 0;
     DocSeg ds;
-    bool have = next_slot(g, &ds), by_copy = false;
+    bool have = walk.next(src, src_off, n, lane, &ds, &g), by_copy = false;
     uint8_t* stg = stages[warp];
     if (have && lane == 0) by_copy = issue_doc_segment(stg, ds, lo, hi, &bars[warp]);
     by_copy = __shfl_sync(0xffffffffu, by_copy, 0);
@@ -1095,9 +1115,9 @@ __global__ void __launch_bounds__(32 * kDocWarps, 6)
         // the stage buffer is read; the next slot's copy may overwrite it
         fence_proxy_async_smem();
         __syncwarp();
-        uint64_t g2 = g + GW;
+        uint64_t g2 = 0;
         DocSeg ds2;
-        const bool have2 = next_slot(g2, &ds2);
+        const bool have2 = walk.next(src, src_off, n, lane, &ds2, &g2);
         bool by_copy2 = false;
         if (have2 && lane == 0) by_copy2 = issue_doc_segment(stg, ds2, lo, hi, &bars[warp]);
         by_copy2 = __shfl_sync(0xffffffffu, by_copy2, 0);

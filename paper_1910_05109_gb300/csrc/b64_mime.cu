@@ -1090,6 +1090,9 @@ __global__ void __launch_bounds__(32 * kDocWarps, 6)
                 if (lane == 0) {
                     atomicMin(st3, (unsigned long long)kDocTimedOut);
                     atomicOr(&g_fault, 1u);
+                    // give the copy one more bounded wait to land before the
+                    // block can exit (its stage buffer belongs to the block)
+                    wait_copy(&bars[warp], phase ^ 1u, kWaitLimitNs);
                 }
                 return;
             }

@@ -131,13 +131,15 @@ int64_t b64_encode(const uint8_t* src, size_t len, uint8_t* dst, const b64_alpha
  * int64 *d_result (8-byte aligned, caller-owned) and returns B64_SUCCESS
  * without waiting. *d_result becomes the decoded length (>= 0) or
  * -(offset+1), offset in [0, len] being the first error (offset == len: bad
- * length). Returns B64_ERR_INVALID_ARGUMENT / B64_ERR_CUDA on failure to
+ * length), or B64_E_TIMEOUT if a bounded wait on one of the kernel's bulk
+ * copies ran out (the output is then incomplete; b64_device_fault_flag
+ * reports it). Returns B64_ERR_INVALID_ARGUMENT / B64_ERR_CUDA on failure to
  * enqueue. */
 int b64_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b64_alphabet* a,
                      int64_t* d_result, void* stream);
 
 /* As b64_decode_async, then waits for the stream and returns *d_result's
- * value (or B64_E_INVAL / B64_E_CUDA). Uses one 8-byte device word and one
+ * value (which may be B64_E_TIMEOUT), or B64_E_INVAL / B64_E_CUDA. Uses one 8-byte device word and one
  * pinned host word per calling thread and device, allocated on the thread's
  * first call and kept until the process exits. */
 int64_t b64_decode(const uint8_t* src, size_t len, uint8_t* dst, const b64_alphabet* a,
@@ -205,8 +207,10 @@ int b64_mime_decode_batch(const uint8_t* src, const int64_t* src_off, int64_t n,
  * device memory of at least b64_batch_workspace_size(n) bytes, 256-byte
  * aligned, owned by the caller and busy until the enqueued work completes.
  * Strings may start at any alignment; src and dst may be NULL only if every
- * string is empty. Returns B64_SUCCESS or an error code; nothing is enqueued
- * on error. n == 0 enqueues nothing. */
+ * string is empty. If a bounded wait on a tile's bulk copy runs out, the
+ * kernel stops early and sets the flag b64_device_fault_flag reads; results
+ * and output are then incomplete. Returns B64_SUCCESS or an error code;
+ * nothing is enqueued on error. n == 0 enqueues nothing. */
 #define B64_BATCH_MAX_ALPHABETS 4
 
 size_t b64_batch_workspace_size(int64_t n);

@@ -181,7 +181,7 @@ def encode(src: torch.Tensor, alphabet: Alphabet | None = None, dst: torch.Tenso
 def decode_async(src: torch.Tensor, dst: torch.Tensor, d_result: torch.Tensor,
                  alphabet: Alphabet | None = None, stream=None) -> None:
     """Enqueues a strict decode; d_result (int64, 1 element, on the device)
-    receives the length or -(offset+1)."""
+    receives the length, -(offset+1), or B64_E_TIMEOUT."""
     alphabet = alphabet or Alphabet.standard()
     src, dst = _dev_u8(src, "src"), _dev_u8(dst, "dst")
     if d_result.dtype != torch.int64 or d_result.device.type != "cuda":
@@ -211,6 +211,8 @@ def decode(src: torch.Tensor, alphabet: Alphabet | None = None, dst: torch.Tenso
     r = lib().b64_decode(src.data_ptr(), m, dst.data_ptr(), alphabet.handle, _stream_ptr(stream))
     if r in (B64_E_INVAL, B64_E_CUDA):
         raise B64Error(last_error())
+    if r == B64_E_TIMEOUT:
+        raise B64Error("a device wait ran out of time (see device_fault_flag)")
     return int(r), dst[: max(r, 0)]
 
 
@@ -315,6 +317,8 @@ def mime_decode_async(src: torch.Tensor, dst: torch.Tensor, d_result: torch.Tens
     """Enqueues a whitespace-skipping strict decode; returns the workspace used."""
     alphabet = alphabet or Alphabet.standard()
     src, dst = _dev_u8(src, "src"), _dev_u8(dst, "dst")
+    if d_result.dtype != torch.int64 or d_result.device.type != "cuda":
+        raise B64Error("d_result must be a CUDA int64 tensor")
     m = src.numel()
     if dst.numel() < decoded_max_length(m):
         raise B64Error("dst is smaller than decoded_max_length(len(src))")
@@ -415,6 +419,7 @@ def mime_decode_batch(src: torch.Tensor, src_off: torch.Tensor, dst: torch.Tenso
                       stream=None) -> torch.Tensor:
     """Enqueues the whitespace-skipping strict decode of every document;
     returns the device int64 results."""
+    src, dst = _dev_u8(src, "src"), _dev_u8(dst, "dst")
     src_off = _dev(src_off, torch.int64, "src_off")
     dst_off = _dev(dst_off, torch.int64, "dst_off")
     n = src_off.numel() - 1

@@ -159,3 +159,34 @@ def test_new_entry_points_reject_bad_arguments_without_gpu(L):
     assert L.b64_host_decode(None, 16, 10, 16, std) == b.B64_E_INVAL
     assert L.b64_host_codec_device_bytes(None) == 0
     L.b64_host_codec_destroy(None)
+
+
+def test_binding_rejects_host_and_mistyped_tensors(L):
+    """Every wrapper checks its tensors before calling into the library, so a
+    CPU tensor or a wrong dtype is an error, never a host-side computation."""
+    import torch
+    from paper_1910_05109_gb300 import binding as b
+    host = torch.zeros(16, dtype=torch.uint8)
+    off = torch.zeros(2, dtype=torch.int64)
+    res = torch.zeros(1, dtype=torch.int64)
+    calls = [
+        lambda: b.encode(host),
+        lambda: b.decode(host),
+        lambda: b.encode(torch.zeros(16, dtype=torch.int32)),
+        lambda: b.decode_async(host, host, res),
+        lambda: b.mime_decode_async(host, host, res),
+        lambda: b.mime_decode(host),
+        lambda: b.encode_batch(host, off, host, off, [b.Alphabet.standard()]),
+        lambda: b.decode_batch(host, off, host, off, [b.Alphabet.standard()]),
+        lambda: b.mime_decode_batch(host, off, host, off, [b.Alphabet.standard()]),
+        lambda: b.batch_offsets(off, [b.Alphabet.standard()], None, decode=True),
+    ]
+    for i, call in enumerate(calls):
+        with pytest.raises(b.B64Error):
+            call()
+    with pytest.raises(b.B64Error, match="1..4"):
+        b._alphabet_array([])
+    with pytest.raises(b.B64Error, match="1..4"):
+        b._alphabet_array([b.Alphabet.standard()] * 5)
+    with pytest.raises(ValueError):
+        b._host_u8(torch.zeros(4, dtype=torch.int16), "src")

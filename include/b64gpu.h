@@ -132,9 +132,11 @@ int64_t b64_encode(const uint8_t* src, size_t len, uint8_t* dst, const b64_alpha
  * without waiting. *d_result becomes the decoded length (>= 0) or
  * -(offset+1), offset in [0, len] being the first error (offset == len: bad
  * length), or B64_E_TIMEOUT if a bounded wait on one of the kernel's bulk
- * copies ran out (the output is then incomplete; b64_device_fault_flag
- * reports it). Returns B64_ERR_INVALID_ARGUMENT / B64_ERR_CUDA on failure to
- * enqueue. */
+ * copies ran out (the output is then incomplete). If such a wait ran out
+ * while another part of the input held a bad character, *d_result is that
+ * character's offset, which then need not be the first; b64_device_fault_flag
+ * reports the timeout in both cases. Returns B64_ERR_INVALID_ARGUMENT /
+ * B64_ERR_CUDA on failure to enqueue. */
 int b64_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b64_alphabet* a,
                      int64_t* d_result, void* stream);
 
@@ -172,7 +174,9 @@ int b64_mime_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b6
  * b64_batch_offsets with decode != 0), with alphabets[alph_id[i]] (alph_id
  * NULL: alphabet 0); results[i] receives its length or -(offset+1), offset
  * within the document, or B64_E_TIMEOUT (a bounded wait on one of its
- * segments' bulk copies ran out). workspace: device memory of
+ * segments' bulk copies ran out; if another of its segments held a bad
+ * character, that offset is reported instead and need not be the first;
+ * b64_device_fault_flag reports the timeout in both cases). workspace: device memory of
  * b64_mime_batch_workspace_size(n, src_off[n] - src_off[0]) bytes, 8-byte
  * aligned; if the documents' total turns out larger than the size was
  * computed for, every results[i] becomes B64_E_INVAL and nothing else is

@@ -28,46 +28,15 @@
 #include <vector>
 
 #include "b64_internal.h"
+#include "b64_serve_plan.h"
 
 using Clock = std::chrono::steady_clock;
 
 namespace {
 
-constexpr size_t kAlign = 256;
+using b64serve::align_up;
+using b64serve::Ring;
 constexpr size_t kMaxBatchRequests = 16384;
-size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
-
-// Contiguous blocks of [0, cap), released in the order they were reserved.
-class Ring {
-public:
-    explicit Ring(size_t cap) : cap_(cap) {}
-    bool reserve(size_t size, size_t* off) {
-        size_t at;
-        if (blocks_.empty()) {
-            at = 0;
-            if (size > cap_) return false;
-        } else {
-            const size_t first = blocks_.front().first;
-            const size_t end = blocks_.back().first + blocks_.back().second;
-            if (end >= first) {  // not wrapped: room after the end, or before the first
-                if (end + size <= cap_) at = end;
-                else if (size <= first) at = 0;
-                else return false;
-            } else {  // wrapped: room between the end and the first
-                if (end + size <= first) at = end;
-                else return false;
-            }
-        }
-        blocks_.emplace_back(at, size);
-        *off = at;
-        return true;
-    }
-    void release_front() { blocks_.pop_front(); }
-
-private:
-    size_t cap_;
-    std::deque<std::pair<size_t, size_t>> blocks_;
-};
 
 // Host copies of one poll (packing payloads into staging, unpacking
 // results into the callers' buffers) spread over worker threads: the tasks
@@ -222,20 +191,22 @@ size_t out_capacity(const b64_server* s, int op, int alph, size_t len) {
 // [outputs][results n][workspace], sections 256-byte aligned, so that one
 // host-to-device copy moves the offsets and the payload, and one
 // device-to-host copy the outputs and the results.
+size_t workspace_bytes(size_t n) { return b64::batch_workspace_bytes(int64_t(n)); }
+
+// Section offsets of the block; the total is b64serve::block_bytes.
 size_t batch_layout(b64_server_batch& b, size_t in_bytes, size_t out_bytes) {
     const size_t n = b.reqs.size();
     b.o_meta = 0;
-    b.meta_bytes = align_up(2 * (n + 1) * sizeof(int64_t) + n);
+    b.meta_bytes = b64serve::meta_bytes(n);
     b.o_in = b.meta_bytes;
     b.o_out = b.o_in + align_up(in_bytes);
     b.o_res = b.o_out + align_up(out_bytes);
     b.o_ws = b.o_res + align_up(n * sizeof(int64_t));
-    return b.o_ws + align_up(b64::batch_workspace_bytes(int64_t(n)));
+    return b64serve::block_bytes(n, in_bytes, out_bytes, workspace_bytes(n));
 }
 
 size_t single_request_bytes(size_t len, size_t cap) {
-    return align_up(len) + align_up(cap) + align_up(2 * 2 * sizeof(int64_t) + 1) +
-           align_up(sizeof(int64_t)) + align_up(b64::batch_workspace_bytes(1));
+    return b64serve::block_bytes(1, len, cap, workspace_bytes(1));
 }
 
 int launch(b64_server* s, b64_server_batch& b) {
@@ -272,17 +243,22 @@ int launch(b64_server* s, b64_server_batch& b) {
     s->copies->run(s->tasks);
     cudaStream_t st = s->streams[b.stream];
     cudaError_t e = cudaMemcpyAsync(d, h, b.o_in + in_bytes, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return -1;
     b64::BatchArgs a{d + b.o_in, reinterpret_cast<const int64_t*>(d + b.o_meta), int64_t(n),
                      d + b.o_out, reinterpret_cast<const int64_t*>(d + b.o_meta) + (n + 1),
                      d + b.o_meta + 2 * (n + 1) * sizeof(int64_t),
                      reinterpret_cast<int64_t*>(d + b.o_res)};
-    e = b64::launch_batch(b.op == 1, a, s->tabs, 4, d + b.o_ws, st);
+    if (e == cudaSuccess) e = b64::launch_batch(b.op == 1, a, s->tabs, 4, d + b.o_ws, st);
     if (e == cudaSuccess)  // outputs and results in one copy
         e = cudaMemcpyAsync(h + b.o_out, d + b.o_out, b.o_res - b.o_out + n * sizeof(int64_t),
                             cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaEventRecord(b.done, st);
-    return e == cudaSuccess ? 0 : -1;
+    if (e != cudaSuccess) {
+        // Whatever was enqueued finishes before the block is handed out again.
+        cudaStreamSynchronize(st);
+        s->ring.release_back();
+        return -1;
+    }
+    return 0;
 }
 
 }  // namespace
@@ -303,7 +279,7 @@ b64_server* b64_server_create(size_t budget_bytes, int n_streams, size_t max_bat
         return nullptr;
     }
     for (int k = 0; k < kMaxAlphabets; ++k) s->padded[k] = s->tabs.padded[k];
-    s->budget = budget_bytes & ~(kAlign - 1);
+    s->budget = budget_bytes & ~(b64serve::kAlign - 1);
     s->max_batch_bytes = max_batch_bytes ? max_batch_bytes : (size_t(64) << 20);
     s->ring = Ring(s->budget);
     cudaGetDevice(&s->device);
@@ -341,7 +317,7 @@ int b64_server_submit(b64_server* s, uint64_t tag, int op, int alph_id, const ui
 }
 
 int b64_server_poll(b64_server* s, b64_completion* out, int max_out) {
-    if (!s || (max_out > 0 && !out))
+    if (!s || max_out < 0 || (max_out > 0 && !out))
         return set_error(B64_ERR_INVALID_ARGUMENT, "b64_server_poll: bad argument");
     int nout = 0;
     // 1. reap finished batches (results in staging), release the ring prefix
@@ -386,15 +362,9 @@ int b64_server_poll(b64_server* s, b64_completion* out, int max_out) {
     for (size_t si = 0; si < s->streams.size() && !s->queue.empty(); ++si) {
         if (s->busy[si]) continue;
         b64_server_batch parts[2];
-        size_t taken = 0, bytes = 0;
-        while (taken < s->queue.size() && taken < kMaxBatchRequests) {
-            const auto& r = s->queue[taken];
-            const size_t add = r.len + r.cap;
-            if (taken > 0 && bytes + add > s->max_batch_bytes) break;
-            bytes += add;
-            parts[r.op].reqs.push_back(r);
-            ++taken;
-        }
+        const size_t taken = b64serve::plan_take(s->queue, s->max_batch_bytes, s->budget,
+                                                 kMaxBatchRequests, workspace_bytes);
+        for (size_t k = 0; k < taken; ++k) parts[s->queue[k].op].reqs.push_back(s->queue[k]);
         bool sent[2] = {false, false}, stalled = false;
         for (int op = 0; op < 2; ++op) {
             b64_server_batch& b = parts[op];

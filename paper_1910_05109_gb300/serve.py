@@ -97,7 +97,9 @@ class HostRing:
         else:
             first = self.live[0][0]
             end = self.live[-1][0] + self.live[-1][1]
-            if end >= first:
+            # wrapped when the newest slot starts before the oldest; its end
+            # may then equal the oldest slot's start (no room left)
+            if self.live[-1][0] >= first:
                 at = end if end + size <= self.cap else (0 if size <= first else None)
             else:
                 at = end if end + size <= first else None

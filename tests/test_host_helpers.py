@@ -57,3 +57,40 @@ def test_host_ring_wraps_and_releases_in_order():
     ring.release(3)
     assert not ring.live and ring.take(5, 960) == 0
     assert ring.take(6, 2000) is None                        # larger than the ring
+
+
+def test_host_ring_full_after_wrap_refuses():
+    """After a wrap the newest slot may end exactly where the oldest begins;
+    the ring is then full and must not hand out space after that end."""
+    ring = serve.HostRing(1024)
+    assert ring.take(0, 256) == 0
+    assert ring.take(1, 256) == 256
+    ring.release(0)                                          # oldest now starts at 256
+    assert ring.take(2, 256) == 512
+    assert ring.take(3, 256) == 768
+    assert ring.take(4, 256) == 0                            # wraps; ends at 256 == oldest start
+    assert ring.take(5, 64) is None                          # full: [256, 1024) is live
+
+
+def test_host_ring_slots_never_overlap():
+    g = np.random.default_rng(17)
+    ring = serve.HostRing(4096)
+    live = {}
+    tag = 0
+    for _ in range(20_000):
+        if live and g.random() < 0.45:
+            t = min(live)                                    # release in submission order...
+            if g.random() < 0.3 and len(live) > 1:
+                t = sorted(live)[1]                          # ...or one out of order
+            ring.release(t)
+            del live[t]
+            continue
+        size = int(g.choice([64, 128, 256, 512, 1024, 3000]))
+        at = ring.take(tag, size)
+        if at is not None:
+            span = (size + 63) // 64 * 64
+            assert 0 <= at and at + span <= 4096
+            for a, s in live.values():
+                assert at + span <= a or a + s <= at, (at, span, a, s)
+            live[tag] = (at, span)
+        tag += 1

@@ -94,3 +94,45 @@ def test_small_budget_waits_and_refuses(env):
     with pytest.raises(b64.B64Error, match="budget"):
         srv.submit(1, 0, 0, big.ctypes.data, big.size, out.ctypes.data, out.size)
     srv.close()
+
+
+def test_burst_larger_than_budget_drains(env):
+    """Requests queued all at once whose total is many times the budget (and
+    a batch cap far above it) are split into batches that each fit the arena,
+    and all of them complete."""
+    import base64
+    import time
+    b64, serve, pools = env
+    raw, text = pools[0][0], pools[1][0]
+    srv = serve.Server(2 << 20, [b64.Alphabet.standard()], n_streams=2,
+                       max_batch_bytes=256 << 20)
+    g = wl.rng(21)
+    reqs, outs = [], []
+    for i in range(600):
+        op = int(g.integers(0, 2))
+        size = int(g.integers(1, 40_000))
+        if op == 1:
+            size = size // 4 * 4 + 4
+            off = int(g.integers(0, (text.size - size) // 4)) * 4
+            data = text[off:off + size]
+            cap = size // 4 * 3
+        else:
+            off = int(g.integers(0, raw.size - size))
+            data = raw[off:off + size]
+            cap = (size + 2) // 3 * 4
+        out = np.zeros(cap, np.uint8)
+        srv.submit(i, op, 0, data.ctypes.data, data.size, out.ctypes.data, cap)
+        reqs.append((op, data))
+        outs.append(out)
+    results = {}
+    deadline = time.monotonic() + 60
+    while len(results) < len(reqs):
+        assert time.monotonic() < deadline, f"{len(results)} of {len(reqs)} done"
+        for c in srv.poll():
+            results[int(c["tag"])] = int(c["result"])
+    assert srv.batches() > 1
+    for i, (op, data) in enumerate(reqs):
+        want = base64.b64encode(data.tobytes()) if op == 0 else base64.b64decode(data.tobytes())
+        assert results[i] == len(want), i
+        assert outs[i][:results[i]].tobytes() == want, i
+    srv.close()

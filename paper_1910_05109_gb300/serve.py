@@ -56,7 +56,7 @@ class Server:
         return int(b64.lib().b64_server_batches(self.handle))
 
     def close(self):
-        if self.handle:
+        if getattr(self, "handle", None):
             b64.lib().b64_server_destroy(self.handle)
             self.handle = None
 

@@ -261,8 +261,8 @@ int b64_batch_offsets(const int64_t* src_off, int64_t n, const b64_alphabet* con
  * of piece_bytes to the device, codes them and copies the results back, the
  * three steps of different pieces overlapping on the streams. Host buffers
  * that are page-locked (cudaHostAlloc / cudaHostRegister, torch
- * pin_memory) give full overlap; pageable ones work, with copies the driver
- * stages itself. Results are those of b64_encode / b64_decode on the whole
+ * pin_memory) give full overlap; pageable ones work, with copies the CUDA
+ * driver stages itself. Results are those of b64_encode / b64_decode on the whole
  * buffer: decode pieces after the first are offset-shifted, inner pieces
  * treat every '=' as an error and the last piece always holds the last two
  * characters, so the padding and length rules apply to the whole input

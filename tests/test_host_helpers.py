@@ -94,3 +94,20 @@ def test_host_ring_slots_never_overlap():
                 assert at + span <= a or a + s <= at, (at, span, a, s)
             live[tag] = (at, span)
         tag += 1
+
+
+def test_clock_sampler_summary_parses_nvidia_smi_lines():
+    import bench
+    c = bench.ClockSampler("GPU-0")
+    c.lines = [
+        "2070, 2070, 812.50, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "1965, 2070, 1390.10, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "2040, 2070, 1100.00, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "[N/A], 2070, 0.0, 0x0, Not Active, Not Active, Not Active, Not Active",   # unreadable
+        "garbage",
+    ]
+    s = c.summary()
+    assert s == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                 "samples": 3}
+    c.lines = []
+    assert c.summary()["samples"] == 0 and c.summary()["sm_mhz"] is None

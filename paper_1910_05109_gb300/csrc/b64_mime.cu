@@ -4,7 +4,7 @@
 // original input. The paper cites MIME only as motivation (Sec. 1); the
 // whitespace removal and this single-pass design are this library's.
 //
-// Three kernels, no waits on other blocks:
+// One input: four kernels, no waits on other blocks:
 //   1. count: every block takes 64 consecutive 4 KiB segments (rows of 32
 //      lanes x 16 bytes; exact word-parallel tests for CR, LF and space),
 //      counts each segment's data characters and last data byte, and writes
@@ -27,7 +27,15 @@
 //      by atomic minima.
 //   4. finalize (one thread): the padding and length rules on the compacted
 //      stream, and the result.
-// The only waits are on the decode kernel's own bulk copies, each bounded in
+// Inputs laid out as lines of L data characters (L a multiple of 4) and a
+// fixed line break (CR LF or LF), detected from the first line, take a fast
+// path in step 3: groups are decoded straight from the raw bytes at
+// positions the layout gives, and a segment that does not fit the layout
+// falls back to the general compaction. Many documents in one call (the
+// batched entry point, further down) run the same steps with a memset of
+// their status words, a per-document scan instead of the one-block scan, and
+// a result per document.
+// The only waits are on the decode kernels' own bulk copies, each bounded in
 // time; one that runs out sets the timeout word, and the result becomes
 // B64_E_TIMEOUT.
 #include <mutex>
@@ -498,9 +506,10 @@ __device__ __forceinline__ void copy_out(const uint8_t* buf, uint32_t skip, uint
 }
 
 // Fast path for a whole segment of a document laid out as lines of exactly
-// L data characters, each followed by CR LF, with L a multiple of 4 (76 for
-// MIME, 64 for PEM): no group of four then straddles a line break, and data
-// character j sits at raw position (L + 2) floor(j / L) + j mod L. The warp
+// L data characters, each followed by a line break of e bytes (CR LF, e = 2,
+// or a lone LF, e = 1), with L a multiple of 4 (76 for MIME, 64 for PEM): no
+// group of four then straddles a line break, and data character j sits at
+// raw position (L + e) floor(j / L) + j mod L. The warp
 // decodes the groups straight from the raw bytes (four translations, one
 // 24-bit value and three output bytes a group), writing the output in place
 // below the bytes still to be read, and checks on the way that the segment
@@ -822,8 +831,11 @@ __global__ void mime_finalize_kernel(const uint8_t* __restrict__ src, uint64_t m
 // documents is needed and a slot's document is found by a search. Launch
 // sequence: memset of the documents' status words, count (all segments), one
 // warp per document scanning its segments, decode (all segments), one thread
-// per document for the result. Documents start anywhere, so segments are
-// staged with aligned loads and a funnel shift (no bulk copies, no waits).
+// per document for the result. Documents start anywhere, so a segment is
+// staged by one bulk copy of the 16-byte aligned span around it (plain
+// aligned loads where that span would leave the batch's input) and read
+// through a funnel shift; the wait on each copy is bounded in time, and a
+// document one of whose copies timed out gets B64_E_TIMEOUT.
 __device__ __forceinline__ uint64_t doc_slot(const int64_t* __restrict__ src_off, int64_t d) {
     return uint64_t(src_off[d] - src_off[0]) / kSeg + uint64_t(d);
 }

@@ -54,12 +54,40 @@ KERNEL_SOURCES = {
 }
 
 
+def code_only(text: str) -> str:
+    """C/C++/CUDA source without its comments, trailing blanks and blank lines
+    (string and character literals kept), so that an edit of comments alone
+    leaves a kernel's digest unchanged."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == "/" and text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif c == "/" and text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    lines = (line.rstrip() for line in "".join(out).splitlines())
+    return "\n".join(line for line in lines if line)
+
+
 def source_digest(kernel: str) -> str:
+    """Digest of the code (comments aside) of the files `kernel` is built from."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1910_05109_gb300", "csrc")
     for name in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(d, name), "rb") as f:
-            h.update(name.encode() + f.read())
+        with open(os.path.join(d, name), encoding="utf-8") as f:
+            h.update(name.encode() + code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

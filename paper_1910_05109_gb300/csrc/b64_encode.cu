@@ -3,10 +3,14 @@
 // The paper's AVX-512 loop turns 48 input bytes into 64 characters per
 // iteration with one byte gather (vpermb), one multi-shift (vpmultishiftqb)
 // and one 64-entry table lookup (vpermb). Here the same three steps run per
-// thread on 12-byte units: __byte_perm builds the (s2,s1,s3,s2) word of each
-// triple, shifts by 10, 4, 22 and 16 pick the 6-bit values, and a 64-byte
-// shared-memory table maps them to characters (16 words in 16 distinct banks,
-// so lookups never conflict).
+// thread on 12-byte units. In the streaming kernel, __byte_perm gathers each
+// triple as the 24-bit number s1<<16 | s2<<8 | s3 (Sec. 2), whose two 12-bit
+// halves index a 4096-entry table of character pairs built in shared memory
+// from the run-time alphabet: two 16-bit lookups and one byte permute give
+// the four characters. The plain paths (unaligned buffers, the ragged end)
+// build the paper's (s2,s1,s3,s2) word, pick the 6-bit values at bits 10, 4,
+// 22 and 16, and look each up in the 64-byte table (16 words in 16 distinct
+// banks, so lookups never conflict).
 //
 // Fast path (src and dst 16-byte aligned): a persistent grid in which every
 // warp is its own pipeline. A warp streams "warp chunks" of 32 x kUnits x 12

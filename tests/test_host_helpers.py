@@ -1,6 +1,10 @@
-"""Host-side helpers that need no GPU: the synthetic input recipes and the
-serving driver's host output ring."""
+"""Host-side helpers that need no GPU: the synthetic input recipes, the
+serving driver's host output ring, and the benchmark's clock summary and
+kernel-source digest."""
+import os
+
 import numpy as np
+from conftest import ROOT
 
 from paper_1910_05109_gb300 import serve
 from paper_1910_05109_gb300 import workloads as wl
@@ -111,3 +115,28 @@ def test_clock_sampler_summary_parses_nvidia_smi_lines():
                  "samples": 3}
     c.lines = []
     assert c.summary()["samples"] == 0 and c.summary()["sm_mhz"] is None
+
+
+def test_kernel_digest_ignores_comments_only(tmp_path, monkeypatch):
+    """The digest that ties a committed DRAM-traffic figure to a kernel's
+    sources changes with the code and not with its comments."""
+    import shutil
+    import bench
+    src = os.path.join(ROOT, "paper_1910_05109_gb300", "csrc")
+    dst = tmp_path / "paper_1910_05109_gb300" / "csrc"
+    dst.mkdir(parents=True)
+    for name in ("b64_encode.cu", "b64_decode.cu", "b64_device.cuh"):
+        shutil.copy(os.path.join(src, name), dst / name)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    before = {k: bench.source_digest(k) for k in bench.KERNEL_SOURCES}
+    enc = dst / "b64_encode.cu"
+    text = enc.read_text()
+    enc.write_text("// a new first line of comment\n/* and a block\n   comment */\n" +
+                   text.replace("// ", "//  ") + "\n\n// trailing note\n")
+    assert {k: bench.source_digest(k) for k in bench.KERNEL_SOURCES} == before
+    enc.write_text(text.replace("kStages", "kStagez"))
+    after = {k: bench.source_digest(k) for k in bench.KERNEL_SOURCES}
+    assert after["encode_tma_kernel"] != before["encode_tma_kernel"]
+    assert after["decode_body_kernel"] == before["decode_body_kernel"]
+    assert bench.code_only('a = "/* x */ // y"; /* z */ b = \'/\'; // w') == \
+        'a = "/* x */ // y";   b = \'/\';'

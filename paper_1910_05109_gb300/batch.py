@@ -1,6 +1,6 @@
 """Resident batched codec: buffers kept on the device, the launch sequence
-recorded once as a CUDA graph and replayed, the tile size chosen by the
-autotuner.
+recorded once as a CUDA graph and replayed. The tile size is the caller's
+(`tile_units`, 4 by default; `autotune.best_units` picks one for a batch).
 
 A BatchCodec is built for one batch shape (string count, total bytes, output
 capacity). `run(src, src_off, alph_id)` copies nothing itself: the caller's

@@ -255,6 +255,16 @@ def job_throughput(bytes_per_rank_step: float, world_size: int, steps: int, max_
 
 # ---------------------------------------------------------------- reference arm
 
+def reference_sample_bytes(consumed_per_s: float, consumed_per_byte: float, steps: int,
+                           warmup: int, budget_s: float = 60.0) -> int:
+    """Bytes of the 1 GiB buffer one reference step takes: as many as let the
+    warm-up and timed steps finish in about budget_s at the probed rate,
+    between 1 MiB and 128 MiB, a multiple of 3."""
+    per_step_s = budget_s / max(1, steps + warmup)
+    want = int(consumed_per_s * per_step_s / consumed_per_byte)
+    return max(1 << 20, min(128 << 20, want)) // 3 * 3
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -262,8 +272,12 @@ def run_reference(args):
     from paper_1910_05109_gb300 import workloads as wl
     data = wl.random_bytes(N_BYTES, SEED)
     cores = len(os.sched_getaffinity(0))
-    # Each step: a bounded sample (the first 128 MiB) of the step's workload.
-    sample = data[: 128 << 20]
+    # Each step: a bounded sample (the start of the 1 GiB buffer) of the
+    # step's workload, sized from a probe pass so that the run takes about a
+    # minute whatever --steps is.
+    probe = data[: 16 << 20]
+    c, s = oracle_pass(probe, cores)
+    sample = data[: reference_sample_bytes(c / s, c / probe.size, args.steps, args.warmup)]
     for _ in range(args.warmup):
         oracle_pass(sample, cores)
     total, sec = 0, 0.0
@@ -279,8 +293,8 @@ def run_reference(args):
           "config": {"workload": WORKLOAD, "bytes": N_BYTES, "sample_bytes": sample.size},
           "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
                            "cpu": cpu_model(),
-                           "sample": "first 128 MiB of the 1 GiB buffer per step, both tables, "
-                                     f"split over {cores} threads"},
+                           "sample": f"first {sample.size} bytes of the 1 GiB buffer per "
+                                     f"step, both tables, split over {cores} threads"},
           "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
                   "d2h_bytes_per_step": 0}})
 

@@ -140,3 +140,16 @@ def test_kernel_digest_ignores_comments_only(tmp_path, monkeypatch):
     assert after["decode_body_kernel"] == before["decode_body_kernel"]
     assert bench.code_only('a = "/* x */ // y"; /* z */ b = \'/\'; // w') == \
         'a = "/* x */ // y";   b = \'/\';'
+
+
+def test_reference_sample_keeps_the_run_near_a_minute():
+    import bench
+    rate, per_byte = 9e9, 4.67                      # bytes consumed per second / per sample byte
+    big = bench.reference_sample_bytes(rate, per_byte, steps=3, warmup=3)
+    assert big == (128 << 20) // 3 * 3                # few steps: the 128 MiB cap
+    for steps in (100, 1000, 5000):
+        s = bench.reference_sample_bytes(rate, per_byte, steps=steps, warmup=5)
+        assert s % 3 == 0 and (1 << 20) - 3 <= s <= 128 << 20
+        run_s = (steps + 5) * s * per_byte / rate
+        assert run_s <= 61 or s == (1 << 20) // 3 * 3
+    assert bench.reference_sample_bytes(1e6, per_byte, steps=10_000, warmup=5) == (1 << 20) // 3 * 3

@@ -160,9 +160,96 @@ class ClockSampler:
                 if val.lower().startswith("active"):
                     reasons.add(name)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "source": "nvidia-smi"}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi"}
+
+
+class NvmlClockSampler:
+    """SM clock, power and clock-event reasons sampled in-process every
+    `interval_s` through NVML's read-only queries (the driver's
+    libnvidia-ml, called through ctypes), from a thread, while running.
+    Changes no GPU setting."""
+
+    CLOCK_SM = 1
+    # clock-event reason bits (nvml.h) -> names used in the bench line
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, gpu_id: str, interval_s: float = 0.002):
+        self.gpu_id = gpu_id
+        self.interval_s = interval_s
+        self.samples: list[tuple[int, int, int, int]] = []   # (sm MHz, max MHz, reasons, mW)
+        self._stop = threading.Event()
+        self._thread = None
+        self._nvml = None
+        self._dev = None
+
+    def open(self) -> bool:
+        """Loads NVML and finds the device; False if either is unavailable."""
+        import ctypes
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return False
+            dev = ctypes.c_void_p()
+            if nv.nvmlDeviceGetHandleByUUID(self.gpu_id.encode(), ctypes.byref(dev)) != 0:
+                return False
+            self._reasons_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        except (OSError, AttributeError):
+            return False
+        self._nvml, self._dev = nv, dev
+        return True
+
+    def _sample(self):
+        import ctypes
+        nv, dev = self._nvml, self._dev
+        sm, mx, pw = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_uint()
+        rs = ctypes.c_ulonglong()
+        if nv.nvmlDeviceGetClockInfo(dev, self.CLOCK_SM, ctypes.byref(sm)) != 0:
+            return
+        nv.nvmlDeviceGetMaxClockInfo(dev, self.CLOCK_SM, ctypes.byref(mx))
+        self._reasons_fn(dev, ctypes.byref(rs))
+        nv.nvmlDeviceGetPowerUsage(dev, ctypes.byref(pw))
+        self.samples.append((sm.value, mx.value, rs.value, pw.value))
+
+    def _run(self):
+        while not self._stop.is_set():
+            self._sample()
+            self._stop.wait(self.interval_s)
+
+    def __enter__(self):
+        self._thread = threading.Thread(target=self._run, daemon=True)
+        self._thread.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._thread.join(timeout=2)
+        self._sample()                   # one reading at the end of the region
+
+    def summary(self) -> dict:
+        sm = [s[0] for s in self.samples if s[0] > 0]
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "source": "nvml"}
+        reasons = set()
+        for s in self.samples:
+            for bit, name in self.REASONS.items():
+                if s[2] & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(s[1] for s in self.samples),
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvml",
+                "interval_ms": self.interval_s * 1e3,
+                "power_w_median": statistics.median(s[3] for s in self.samples) / 1e3}
+
+
+def clock_sampler(gpu_id: str):
+    """In-process NVML sampling where NVML loads, else nvidia-smi's."""
+    s = NvmlClockSampler(gpu_id)
+    return s if s.open() else ClockSampler(gpu_id)
 
 
 def gpu_uuid(dev=0) -> str:
@@ -356,7 +443,7 @@ def run_gpu(args):
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
     gpu_id = gpu_id if gpu_id.startswith("GPU-") else f"GPU-{gpu_id}"
-    with ClockSampler(gpu_id) as clocks:
+    with clock_sampler(gpu_id) as clocks:
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -490,6 +577,8 @@ def finish(args, v):
         "gpu_launches": 8 * K,
         "clocks": clocks.summary(),
     }
+    if ws == 1 and not args.no_workloads:
+        out["workloads"] = other_workloads(args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(data)
     if rank == 0:
@@ -498,13 +587,46 @@ def finish(args, v):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- other workloads
+
+# The default run's settings for the other workloads: enough timed calls for
+# a few dozen clock samples, the serving stream at its stated rate for 10 s,
+# then a short sweep of higher rates for the engine's capacity.
+WORKLOAD_MIN_STEPS = 100
+SERVE_DURATION_S = 10.0
+SERVE_SWEEP = (40_000.0, 80_000.0, 160_000.0)
+
+
+def other_workloads(args) -> dict:
+    """The batched-strings, MIME and serving workloads, measured after the
+    single-buffer step in the same process (one GPU). A workload that fails
+    is reported with its error instead of its figures."""
+    import copy
+    import traceback
+    wargs = copy.copy(args)
+    wargs.steps = max(args.steps, WORKLOAD_MIN_STEPS)
+    wargs.warmup = max(args.warmup, 3)
+    out = {}
+    for name, fn in (("batch", lambda: batch_workload(wargs)),
+                     ("mime", lambda: mime_workload(wargs)),
+                     ("serve", lambda: serve_workload(wargs, args.rate, SERVE_DURATION_S,
+                                                      SERVE_SWEEP))):
+        try:
+            out[name] = fn()
+            out[name]["steps"] = wargs.steps if name != "serve" else out[name]["requests"]
+        except Exception as e:  # reported, not hidden: the figures are then absent
+            out[name] = {"error": f"{type(e).__name__}: {e}",
+                         "trace": traceback.format_exc(limit=3)}
+    return out
+
+
 # ---------------------------------------------------------------- batched workload
 
-def run_batch(args):
+def batch_workload(args) -> dict:
     """100,000 strings (lognormal lengths, median 1 KiB, sigma 1.5, 1 B..1 MiB,
     seed 2), 50/50 standard-padded / url-unpadded (seed 13): one persistent
     launch sequence per batch (CUDA-graph replay, autotuned tile) against one
-    launch per string, identical output required."""
+    launch per string, identical output required. Returns the measurements."""
     import torch
     from paper_1910_05109_gb300 import autotune
     from paper_1910_05109_gb300 import binding as b64
@@ -526,7 +648,7 @@ def run_batch(args):
 
     out = {}
     texts = None
-    clocks = ClockSampler(gpu_uuid(dev)).__enter__()   # sampled over both ops' timed loops
+    clocks = clock_sampler(gpu_uuid(dev)).__enter__()   # sampled over both ops' timed loops
     for op in ("encode", "decode"):
         if op == "encode":
             src, src_off = d_src, d_off
@@ -566,6 +688,11 @@ def run_batch(args):
         res = codec.results[:n].clone()
         batch_out = codec.dst[:cap].clone()
         in_bytes = src.numel()
+        # algorithmic bytes: the strings read, their encoded / decoded bytes written
+        alg = in_bytes + (cap if op == "encode" else total_in)
+        roof = {"bound": "hbm", "achieved": alg / (batch_ms / 1e3) / 1e9,
+                "peak": peaks()["hbm_gbs"], "unit": "GB/s", "traffic_alg_bytes": alg}
+        roof["frac"] = roof["achieved"] / roof["peak"]
         if op == "encode":
             texts = (batch_out, codec.dst_off.clone())
             assert torch.equal(res, codec.dst_off[1:] - codec.dst_off[:-1])
@@ -574,7 +701,8 @@ def run_batch(args):
 
         if args.no_per_string:
             out[op] = {"batch_ms": batch_ms, "input_gbps": in_bytes / (batch_ms / 1e3) / 1e9,
-                       "tile_units": units, "autotune_ms": timings, "offsets_ms": offsets_ms}
+                       "roofline": roof, "tile_units": units, "autotune_ms": timings,
+                       "offsets_ms": offsets_ms}
             continue
         # One launch per string through the single-buffer calls.
         hoff = codec.src_off.cpu().numpy()
@@ -634,7 +762,8 @@ def run_batch(args):
                     break
         del g
         out[op] = {"batch_ms": batch_ms, "input_gbps": in_bytes / (batch_ms / 1e3) / 1e9,
-                   "tile_units": units, "autotune_ms": timings, "offsets_ms": offsets_ms,
+                   "roofline": roof, "tile_units": units, "autotune_ms": timings,
+                   "offsets_ms": offsets_ms,
                    "per_string_eager_ms": eager_ms, "per_string_graph_ms": graph_ms,
                    "speedup_vs_eager": eager_ms / batch_ms,
                    "speedup_vs_graph": graph_ms / batch_ms, "identical_output": identical,
@@ -642,24 +771,38 @@ def run_batch(args):
     clocks.__exit__(None, None, None)
     step_ms = out["encode"]["batch_ms"] + out["decode"]["batch_ms"]
     step_in = total_in + texts[0].numel()
-    emit({"metric": METRIC, "workload": "batched varlen strings", "value":
-          step_in / (step_ms / 1e3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
-          "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-          "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-          "config": {"workload": f"{n} strings, lognormal lengths (median 1 KiB, sigma 1.5, "
-                                 "1 B..1 MiB, seed 2), 50/50 standard-padded / url-unpadded",
-                     "input_bytes": total_in, "encoded_bytes": int(texts[0].numel())},
-          "encode": out["encode"], "decode": out["decode"], "clocks": clocks.summary(),
-          # per step: encode results + tile kernel; decode tile + finalize kernel
-          "gpu_launches": 4 * args.steps})
+    return {"value": step_in / (step_ms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": step_ms,
+            "config": {"workload": f"{n} strings, lognormal lengths (median 1 KiB, sigma 1.5, "
+                                   "1 B..1 MiB, seed 2), 50/50 standard-padded / url-unpadded",
+                       "input_bytes": total_in, "encoded_bytes": int(texts[0].numel()),
+                       "l2": "batch input and output (314 MB + 419 MB) larger than L2; no flush"},
+            "encode": out["encode"], "decode": out["decode"], "clocks": clocks.summary(),
+            # per step: encode results + tile kernel; decode tile + finalize kernel
+            "gpu_launches": 4 * args.steps}
+
+
+def run_batch(args):
+    r = batch_workload(args)
+    emit({"metric": METRIC, "workload": "batched varlen strings", "value": r["value"],
+          "unit": r["unit"], "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+          "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+          "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": r["config"],
+          "encode": r["encode"], "decode": r["decode"], "clocks": r["clocks"],
+          "gpu_launches": r["gpu_launches"]})
 
 
 # ---------------------------------------------------------------- MIME workload
 
-def run_mime(args):
+# The kernels of one MIME decode call, and how many launches it makes.
+MIME_KERNELS = ("mime decode call (mime_count_kernel, mime_scan_kernel, mime_decode_kernel, "
+                "mime_finalize_kernel)")
+MIME_LAUNCHES_PER_CALL = 4
+
+def mime_workload(args) -> dict:
     """256 MiB of seed-3 random bytes, encoded with the standard table and
     wrapped as 76-character lines with CRLF (367,332,730 bytes), decoded with
-    CR/LF/space skipped; against a D2D memcpy of the same bytes."""
+    CR/LF/space skipped; against a D2D memcpy of the same bytes. Returns the
+    measurements."""
     import torch
     from paper_1910_05109_gb300 import binding as b64
     from paper_1910_05109_gb300 import build as gpu_build
@@ -683,7 +826,7 @@ def run_mime(args):
     torch.cuda.synchronize()
     assert int(res.item()) == n and torch.equal(dst[:n], d)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(gpu_uuid()) as clocks:
+    with clock_sampler(gpu_uuid()) as clocks:
         e0.record(stream)
         for _ in range(args.steps):
             b64.mime_decode_async(src, dst, res, std, ws)
@@ -725,27 +868,32 @@ def run_mime(args):
     del dsrc, ddst, dws
     pk = peaks()
     dram = (m + n) / (ms / 1e3) / 1e9
-    emit({"metric": METRIC, "workload": "MIME line-wrapped decode", "value": m / (ms / 1e3) / 1e9,
-          "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-          "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-          "dtype": "u8", "data": "synthetic",
-          "config": {"workload": f"{n} random bytes (seed 3), standard table, 76-char lines + "
-                                 "CRLF, no trailing CRLF", "input_bytes": m, "output_bytes": n},
-          "memcpy_gbps": m / (mc / 1e3) / 1e9, "frac_of_memcpy": mc / ms,
-          # the whole call (count, scan, decode and finalize kernels) against the
-          # bytes it must move: the wrapped input read, the decoded bytes written
-          "roofline": {"bound": "hbm", "kernel": "mime decode call (mime_count_kernel, "
-                                                 "mime_scan_kernel, mime_decode_kernel, "
-                                                 "mime_finalize_kernel)",
-                       "achieved": dram, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                       "frac": dram / pk["hbm_gbs"], "peak_source": pk["source"],
-                       "traffic": None},
-          "clocks": clocks.summary(),
-          "documents_batched": {"documents": 256, "bytes_each": per,
-                                "input_bytes": int(doff[-1]), "ms": docs_ms,
-                                "input_gbps": int(doff[-1]) / (docs_ms / 1e3) / 1e9},
-          # per step: count, scan, decode and finalize kernels
-          "gpu_launches": 4 * args.steps})
+    return {"value": m / (ms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": ms,
+            "config": {"workload": f"{n} random bytes (seed 3), standard table, 76-char lines "
+                                   "+ CRLF, no trailing CRLF", "input_bytes": m,
+                       "output_bytes": n,
+                       "l2": "input and output (367 MB + 268 MB) larger than L2; no flush"},
+            "memcpy_gbps": m / (mc / 1e3) / 1e9, "frac_of_memcpy": mc / ms,
+            # the whole call (count, scan, decode and finalize kernels) against the
+            # bytes it must move: the wrapped input read, the decoded bytes written
+            "roofline": {"bound": "hbm", "kernel": MIME_KERNELS, "achieved": dram,
+                         "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": dram / pk["hbm_gbs"],
+                         "peak_source": pk["source"], "traffic": None},
+            "clocks": clocks.summary(),
+            "documents_batched": {"documents": 256, "bytes_each": per,
+                                  "input_bytes": int(doff[-1]), "ms": docs_ms,
+                                  "input_gbps": int(doff[-1]) / (docs_ms / 1e3) / 1e9},
+            "gpu_launches": MIME_LAUNCHES_PER_CALL * args.steps}
+
+
+def run_mime(args):
+    r = mime_workload(args)
+    emit({"metric": METRIC, "workload": "MIME line-wrapped decode", "value": r["value"],
+          "unit": r["unit"], "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+          "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+          "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": r["config"],
+          **{k: r[k] for k in ("memcpy_gbps", "frac_of_memcpy", "roofline", "clocks",
+                               "documents_batched", "gpu_launches")}})
 
 
 # ---------------------------------------------------------------- Table 2 sizes
@@ -769,7 +917,7 @@ def run_table2(args):
     stream = torch.cuda.Stream()
     rows = []
     launches = 0
-    clocks = ClockSampler(gpu_uuid()).__enter__()   # sampled over every size's timed calls
+    clocks = clock_sampler(gpu_uuid()).__enter__()   # sampled over every size's timed calls
     for name, n in (("lena.jpg", 141_020), ("mandril.jpg", 247_222), ("google logo png", 2_357),
                     ("large.zip", 34_904_444)):
         data = torch.from_numpy(wl.random_bytes(n, 2)).cuda()
@@ -834,11 +982,58 @@ def run_table2(args):
 
 # ---------------------------------------------------------------- serving workload
 
-def run_serve(args):
-    """Poisson arrivals (mean 20,000 req/s, seed 4) over `--duration` seconds,
+def serve_payloads(b64, wl):
+    """The payload pools: 1 GiB of seed-5 random bytes (encode requests) and
+    its standard encoding (decode requests)."""
+    import torch
+    raw = wl.random_bytes(1 << 30, 5)
+    d_raw = torch.from_numpy(raw).cuda()
+    text = b64.encode(d_raw, b64.Alphabet.standard()).cpu().numpy()
+    del d_raw
+    return [(raw, 1), (text, 4)]
+
+
+def serve_once(b64, serve, pools, rate: float, duration: float, streams: int) -> dict:
+    """One open-loop run at `rate` req/s for `duration` s through a fresh
+    engine (4 GiB device budget): latency percentiles, throughput, and the
+    length of every result checked."""
+    arrivals, ops, sizes, pick = serve.poisson_requests(rate, duration, 4, 5)
+    srv = serve.Server(4 << 30, [b64.Alphabet.standard()], n_streams=streams)
+    try:
+        import torch
+        with clock_sampler(gpu_uuid(torch.cuda.current_device())) as clocks:
+            lat, results, wall, _ = serve.run_open_loop(srv, arrivals, ops, sizes, pick, pools,
+                                                        8 << 30)
+        batches = srv.batches()
+    finally:
+        srv.close()
+    n = arrivals.size
+    want = np.where(ops == 0, (sizes + 2) // 3 * 4, sizes // 4 * 3)   # no padding in payloads
+    in_bytes = int(sizes.sum())
+    return {"rate_req_per_s": rate, "duration_s": duration, "requests": n,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "max_ms": float(lat.max() * 1e3),
+            "aggregate_gbps": in_bytes / wall / 1e9,
+            "offered_gbps": in_bytes / duration / 1e9,
+            "achieved_req_per_s": n / wall, "wall_s": wall, "batches": batches,
+            "results_correct": int((results == want).sum()),
+            "results_checked": "output length of every request",
+            "clocks": clocks.summary(),
+            # per batch: encode results + tile kernel, or decode tile + finalize kernel
+            "gpu_launches": 2 * batches}
+
+
+SERVE_P99_BOUND_MS = 5.0
+
+
+def serve_workload(args, rate: float, duration: float, sweep=()) -> dict:
+    """Poisson arrivals (mean `rate` req/s, seed 4) over `duration` seconds,
     60% decode / 40% encode, sizes clip(lognormal(10.62, 2.0), 100 B, 16 MiB)
     (seed 5), served under a 4 GiB device budget with continuous batching;
-    latency = arrival -> result back on the host."""
+    latency = arrival -> result back on the host. `sweep`: further rates, run
+    for --sweep-duration seconds each, to find the engine's capacity (the
+    highest rate whose p99 stays within SERVE_P99_BOUND_MS)."""
     import torch
     from paper_1910_05109_gb300 import binding as b64
     from paper_1910_05109_gb300 import build as gpu_build
@@ -847,37 +1042,34 @@ def run_serve(args):
 
     gpu_build.build()
     torch.cuda.set_device(0)
-    raw = wl.random_bytes(1 << 30, 5)
-    d_raw = torch.from_numpy(raw).cuda()
-    text = b64.encode(d_raw, b64.Alphabet.standard()).cpu().numpy()   # decode payloads
-    del d_raw
-    arrivals, ops, sizes, pick = serve.poisson_requests(args.rate, args.duration, 4, 5)
-    srv = serve.Server(4 << 30, [b64.Alphabet.standard()], n_streams=args.streams)
-    with ClockSampler(gpu_uuid()) as clocks:
-        lat, results, wall, _ = serve.run_open_loop(srv, arrivals, ops, sizes, pick,
-                                                    [(raw, 1), (text, 4)], 8 << 30)
-    n = arrivals.size
-    want = np.where(ops == 0, (sizes + 2) // 3 * 4, sizes // 4 * 3)   # no padding in payloads
-    ok = int((results == want).sum())
-    in_bytes = int(sizes.sum())
-    emit({"metric": METRIC, "workload": "serving loop", "value": float(np.percentile(lat, 99) * 1e3),
-          "unit": "ms (p99 latency)", "n_gpus": 1, "steps": n, "warmup": 0,
-          "ms_per_step": wall / n * 1e3, "higher_is_better": False, "scaling": "weak",
-          "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-          "config": {"workload": f"Poisson {args.rate:.0f} req/s for {args.duration:.0f} s, 60% "
-                                 "decode / 40% encode, sizes clip(lognormal(10.62, 2.0), 100 B, "
-                                 "16 MiB), 4 GiB device budget, continuous batching",
-                     "requests": n, "streams": args.streams},
-          "p50_ms": float(np.percentile(lat, 50) * 1e3),
-          "p99_ms": float(np.percentile(lat, 99) * 1e3),
-          "max_ms": float(lat.max() * 1e3),
-          "aggregate_gbps": in_bytes / wall / 1e9,
-          "offered_gbps": in_bytes / args.duration / 1e9,
-          "achieved_req_per_s": n / wall, "batches": srv.batches(),
-          "results_correct": ok, "clocks": clocks.summary(),
-          # per batch: encode results + tile kernel, or decode tile + finalize kernel
-          "gpu_launches": 2 * srv.batches()})
-    srv.close()
+    pools = serve_payloads(b64, wl)
+    main = serve_once(b64, serve, pools, rate, duration, args.streams)
+    main["config"] = {"workload": f"Poisson {rate:.0f} req/s for {duration:.0f} s, 60% "
+                                  "decode / 40% encode, sizes clip(lognormal(10.62, 2.0), 100 B, "
+                                  "16 MiB), 4 GiB device budget, continuous batching",
+                      "requests": main["requests"], "streams": args.streams}
+    if sweep:
+        rows = [serve_once(b64, serve, pools, r, args.sweep_duration, args.streams)
+                for r in sweep]
+        keep = ("rate_req_per_s", "requests", "p50_ms", "p99_ms", "max_ms", "aggregate_gbps",
+                "offered_gbps", "achieved_req_per_s", "results_correct")
+        main["serve_sweep"] = [{k: row[k] for k in keep} for row in rows]
+        ok = [row["rate_req_per_s"] for row in rows + [main]
+              if row["p99_ms"] <= SERVE_P99_BOUND_MS and row["results_correct"] == row["requests"]]
+        main["capacity"] = {"p99_bound_ms": SERVE_P99_BOUND_MS,
+                            "highest_rate_within_bound": max(ok) if ok else None,
+                            "sweep_duration_s": args.sweep_duration}
+    return main
+
+
+def run_serve(args):
+    rates = [float(x) for x in args.rates.split(",") if x] if args.rates else []
+    r = serve_workload(args, args.rate, args.duration, rates)
+    emit({"metric": METRIC, "workload": "serving loop", "value": r["p99_ms"],
+          "unit": "ms (p99 latency)", "n_gpus": 1, "steps": r["requests"], "warmup": 0,
+          "ms_per_step": r["wall_s"] / r["requests"] * 1e3, "higher_is_better": False,
+          "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+          **{k: v for k, v in r.items() if k not in ("requests", "wall_s")}})
 
 
 def main():
@@ -901,6 +1093,12 @@ def main():
     ap.add_argument("--strings", type=int, default=100_000)
     ap.add_argument("--rate", type=float, default=20_000.0)
     ap.add_argument("--duration", type=float, default=30.0)
+    ap.add_argument("--rates", default="",
+                    help="serve workload: comma-separated further rates (req/s) to sweep")
+    ap.add_argument("--sweep-duration", type=float, default=3.0,
+                    help="serve workload: seconds per sweep rate")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="default run: skip the batch, MIME and serving measurements")
     ap.add_argument("--streams", type=int, default=4)
     ap.add_argument("--mime-bytes", type=int, default=256 << 20)
     ap.add_argument("--tile-units", type=int, default=0,

@@ -233,13 +233,17 @@ int b64_decode_batch(const uint8_t* src, const int64_t* src_off, int64_t n, uint
  * they decode (a plugin handed only its buffers, a process whose memory budget
  * another component owns, a path that must never enter an allocator). The
  * paper has no counterpart; this is b64_decode_batch with its workspace in a
- * device array the library reserves at load time (512 KiB on every GPU
- * that loads it, kept until exit) instead of caller memory. Same arguments
- * and results as b64_decode_batch, without workspace. At most 65536 strings
- * per call (more returns B64_ERR_INVALID_ARGUMENT). Calls no allocator. All
- * calls share the one array: calls whose work overlaps on the GPU race, so
- * serialise them (e.g. one stream). The first call on each device looks up
- * the array's device address; make it before any stream capture. */
+ * file-scope device array of the library (512 KiB on every GPU that loads the
+ * library's device code, kept until exit) instead of caller memory. Same
+ * arguments and results as b64_decode_batch, without workspace. At most 65536
+ * strings per call (more returns B64_ERR_INVALID_ARGUMENT). The call itself
+ * calls no allocator. All calls share the one array: calls whose work
+ * overlaps on the GPU race, so serialise them (e.g. one stream). The first
+ * call on each device looks up the array's device address, and under CUDA's
+ * default lazy loading it is also where the driver loads the library's
+ * device code (the array and the kernels), which takes device memory: make
+ * that first call early, before the device-memory budget is spent, and
+ * outside any stream capture. */
 int b64_decode_batch_noalloc(const uint8_t* src, const int64_t* src_off, int64_t n,
                              uint8_t* dst, const int64_t* dst_off,
                              const b64_alphabet* const* alphabets, int n_alphabets,

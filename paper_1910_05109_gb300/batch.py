@@ -49,10 +49,13 @@ class BatchCodec:
             self.src_off.copy_(src_off, non_blocking=True)
             if alph_id is not None:
                 self.alph_id[:self.n].copy_(alph_id, non_blocking=True)
+            else:
+                self.alph_id[:self.n].zero_()    # every string takes alphabet 0
             off = b64.batch_offsets(self.src_off, self.alphabets, self.alph_id[:self.n],
                                     decode=self.op == "decode", stream=self.stream)
             self.dst_off.copy_(off, non_blocking=True)
         self.stream.synchronize()
+        b64.check_batch_totals(self.src, int(self.src_off[-1]))
         total = int(self.dst_off[-1])
         if self.dst is None or self.dst.numel() < total:
             self.dst = torch.empty(max(total, 1), dtype=torch.uint8, device=self.device)
@@ -60,18 +63,21 @@ class BatchCodec:
         return total
 
     def run(self) -> None:
-        """Enqueues the batch on the codec's stream (graph replay after the
-        first call)."""
+        """Enqueues the batch on the codec's stream. The first call after
+        load() runs the launch sequence directly (which also sets the kernels
+        up outside any capture) and then records it as a graph, which runs
+        nothing; later calls replay the graph. Each call codes the batch once."""
         if not self.use_graph:
             self._enqueue()
             return
         if self.graph is None:
-            self._enqueue()                      # first call: set-up outside capture
+            self._enqueue()
             self.stream.synchronize()
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=self.stream):
                 self._enqueue()
             self.graph = g
+            return
         with torch.cuda.stream(self.stream):
             self.graph.replay()
 

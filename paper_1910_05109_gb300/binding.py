@@ -242,6 +242,29 @@ def _dev(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
     return t
 
 
+def check_batch_counts(n: int, results=None, alph_id=None, dst_off=None,
+                       what: str = "string") -> None:
+    """Refuses per-string arrays shorter than the batch's n entries (the
+    kernels index them by string with no bound): results and alph_id hold n
+    entries each, dst_off at least n. Raises B64Error before anything runs."""
+    for name, t, need in (("results", results, n), ("alph_id", alph_id, n),
+                          ("dst_off", dst_off, n)):
+        if t is not None and t.numel() < need:
+            raise B64Error(f"{name} holds {t.numel()} entries; the batch has {n} {what}s "
+                           f"and needs {need}")
+
+
+def check_batch_totals(src: torch.Tensor, src_total: int, dst: torch.Tensor | None = None,
+                       dst_total: int | None = None) -> None:
+    """Refuses buffers smaller than the offsets say (src_off[n] input bytes,
+    dst_off[n] output bytes), for callers that already hold those totals on
+    the host."""
+    if src.numel() < src_total:
+        raise B64Error(f"src holds {src.numel()} bytes; src_off[n] is {src_total}")
+    if dst is not None and dst_total is not None and dst.numel() < dst_total:
+        raise B64Error(f"dst holds {dst.numel()} bytes; dst_off[n] is {dst_total}")
+
+
 def batch_workspace(n: int, device=None) -> torch.Tensor:
     nbytes = lib().b64_batch_workspace_size(n)
     # torch's caching allocator returns blocks aligned to at least 512 bytes
@@ -251,8 +274,9 @@ def batch_workspace(n: int, device=None) -> torch.Tensor:
 def batch_offsets(src_off: torch.Tensor, alphabets, alph_id: torch.Tensor | None,
                   decode: bool, stream=None) -> torch.Tensor:
     """Device int64[n+1]: exclusive scan of per-string output capacities."""
-    src_off = _dev(src_off, torch.int64, "src_off")
     n = src_off.numel() - 1
+    check_batch_counts(n, alph_id=alph_id)
+    src_off = _dev(src_off, torch.int64, "src_off")
     arr, na = _alphabet_array(alphabets)
     out = torch.empty(n + 1, dtype=torch.int64, device=src_off.device)
     aid = 0 if alph_id is None else _dev(alph_id, torch.uint8, "alph_id").data_ptr()
@@ -265,12 +289,17 @@ def batch_offsets(src_off: torch.Tensor, alphabets, alph_id: torch.Tensor | None
 
 def _batch(fn, src, src_off, dst, dst_off, alphabets, alph_id, results, tile_units, workspace,
            stream):
+    n = src_off.numel() - 1
+    check_batch_counts(n, results, alph_id, dst_off)
+    if workspace is not None:
+        need = lib().b64_batch_workspace_size(n)
+        if workspace.numel() < need:
+            raise B64Error(f"workspace holds {workspace.numel()} bytes, {need} needed")
     src = _dev_u8(src, "src")
     dst = _dev_u8(dst, "dst")
     src_off = _dev(src_off, torch.int64, "src_off")
     dst_off = _dev(dst_off, torch.int64, "dst_off")
     results = _dev(results, torch.int64, "results")
-    n = src_off.numel() - 1
     arr, na = _alphabet_array(alphabets)
     aid = 0 if alph_id is None else _dev(alph_id, torch.uint8, "alph_id").data_ptr()
     if workspace is None:
@@ -419,10 +448,11 @@ def mime_decode_batch(src: torch.Tensor, src_off: torch.Tensor, dst: torch.Tenso
                       stream=None) -> torch.Tensor:
     """Enqueues the whitespace-skipping strict decode of every document;
     returns the device int64 results."""
+    n = src_off.numel() - 1
+    check_batch_counts(n, results, alph_id, dst_off, what="document")
     src, dst = _dev_u8(src, "src"), _dev_u8(dst, "dst")
     src_off = _dev(src_off, torch.int64, "src_off")
     dst_off = _dev(dst_off, torch.int64, "dst_off")
-    n = src_off.numel() - 1
     arr, na = _alphabet_array(alphabets)
     if results is None:
         results = torch.empty(max(n, 1), dtype=torch.int64, device=src_off.device)

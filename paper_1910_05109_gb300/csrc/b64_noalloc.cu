@@ -7,19 +7,22 @@
 // while another component owns the whole device-memory budget (a fixed pool,
 // or a serving process whose memory is already spent), and latency-critical
 // paths that must never enter an allocator. This entry point gives them the
-// same decode with its workspace in a device array that is reserved when the
-// library is loaded.
+// same decode with its workspace in a file-scope device array of the library.
 //
 // Limits and rules:
 //   - at most kNoAllocMaxStrings strings per call; larger batches are refused
 //     with an error (use b64_decode_batch with your own workspace);
-//   - every GPU that loads the library keeps this array (512 KiB) until
-//     the process exits;
+//   - every GPU that loads the library's device code keeps this array
+//     (512 KiB) until the process exits;
 //   - all calls share the one array, so calls whose work overlaps on the GPU
 //     (different streams, or different host threads) race and corrupt each
 //     other's results: serialise them, e.g. on one stream;
 //   - the first call on each device looks up the array's device address
-//     (cudaGetSymbolAddress) with that device current; make that first call
+//     (cudaGetSymbolAddress) with that device current. Under CUDA's default
+//     lazy loading, that first call is also when the driver loads this
+//     library's device code (the array and the kernels) onto the device,
+//     which takes device memory; the calls after it allocate nothing. Make
+//     that first call early, before the device-memory budget is spent, and
 //     before any stream capture on the device.
 #include <cinttypes>
 #include <mutex>

@@ -190,3 +190,37 @@ def test_binding_rejects_host_and_mistyped_tensors(L):
         b._alphabet_array([b.Alphabet.standard()] * 5)
     with pytest.raises(ValueError):
         b._host_u8(torch.zeros(4, dtype=torch.int16), "src")
+
+
+def test_batch_wrappers_refuse_short_per_string_arrays(L):
+    """The batched kernels index results, alph_id and dst_off by string with
+    no bound of their own, so the wrappers refuse arrays shorter than the
+    batch (before any device check, so this runs on the CPU) and the resident
+    batch codec refuses an input buffer shorter than src_off[n]."""
+    import torch
+    from paper_1910_05109_gb300 import binding as b
+    n = 10
+    buf = torch.zeros(64, dtype=torch.uint8)
+    off = torch.zeros(n + 1, dtype=torch.int64)
+    alphs = [b.Alphabet.standard()]
+    short_res = torch.zeros(n - 1, dtype=torch.int64)
+    short_aid = torch.zeros(n - 1, dtype=torch.uint8)
+    short_doff = torch.zeros(n - 1, dtype=torch.int64)
+    ok_res = torch.zeros(n, dtype=torch.int64)
+    for fn in (b.encode_batch, b.decode_batch, b.mime_decode_batch):
+        with pytest.raises(b.B64Error, match="results holds 9 entries"):
+            fn(buf, off, buf, off, alphs, None, short_res)
+        with pytest.raises(b.B64Error, match="alph_id holds 9 entries"):
+            fn(buf, off, buf, off, alphs, short_aid, ok_res)
+        with pytest.raises(b.B64Error, match="dst_off holds 9 entries"):
+            fn(buf, off, buf, short_doff, alphs, None, ok_res)
+    with pytest.raises(b.B64Error, match="alph_id holds 9 entries"):
+        b.batch_offsets(off, alphs, short_aid, decode=False)
+    with pytest.raises(b.B64Error, match="workspace holds 8 bytes"):
+        b.decode_batch(buf, off, buf, off, alphs, None, ok_res,
+                       workspace=torch.zeros(8, dtype=torch.uint8))
+    with pytest.raises(b.B64Error, match="src holds 64 bytes; src_off"):
+        b.check_batch_totals(buf, 65)
+    with pytest.raises(b.B64Error, match="dst holds 64 bytes; dst_off"):
+        b.check_batch_totals(buf, 64, buf, 100)
+    b.check_batch_totals(buf, 64, buf, 64)

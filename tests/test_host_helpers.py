@@ -112,9 +112,29 @@ def test_clock_sampler_summary_parses_nvidia_smi_lines():
     ]
     s = c.summary()
     assert s == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
-                 "samples": 3}
+                 "samples": 3, "source": "nvidia-smi"}
     c.lines = []
     assert c.summary()["samples"] == 0 and c.summary()["sm_mhz"] is None
+
+
+def test_nvml_clock_sampler_summary():
+    """The in-process sampler's summary: median SM clock over readable
+    samples, the highest maximum clock, and every clock-event reason bit seen
+    (power cap 0x4, hardware slowdown 0x8, software thermal 0x20, hardware
+    thermal 0x40), named as in the nvidia-smi summary."""
+    import bench
+    c = bench.NvmlClockSampler("GPU-0")
+    c.samples = [(2070, 2070, 0x0, 900_000), (1980, 2070, 0x4, 1_390_000),
+                 (2055, 2070, 0x1, 1_000_000), (0, 2070, 0x0, 0)]     # last one unreadable
+    s = c.summary()
+    assert s["sm_mhz"] == 2055 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"] and s["source"] == "nvml"
+    c.samples = [(1500, 2070, 0x8 | 0x40 | 0x20, 1)]
+    assert c.summary()["reasons"] == ["hw_slowdown", "hw_thermal_slowdown",
+                                      "sw_thermal_slowdown"]
+    c.samples = []
+    assert c.summary()["samples"] == 0 and c.summary()["sm_mhz"] is None
+    assert not bench.NvmlClockSampler("GPU-no-such-device").open()   # no NVML, or no such GPU
 
 
 def test_kernel_digest_ignores_comments_only(tmp_path, monkeypatch):

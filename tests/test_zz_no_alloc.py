@@ -3,11 +3,13 @@
 It exists for callers that cannot allocate device memory where they decode
 (a plugin given only its buffers, a process whose memory budget belongs to
 someone else, a path that must not enter an allocator): its workspace is a
-device array the library reserves when it is loaded. These tests call it
-through the C ABI and check that it returns exactly what b64_decode_batch
-(with a caller workspace) returns, on two different batches in a row, so a
-second call cannot see what the first left in the shared array; and that a
-batch over the array's limit is refused with a clear message.
+file-scope device array of the library. These tests call it through the C ABI
+and check that it returns exactly what the oracle and b64_decode_batch (with a
+caller workspace) return, on two different batches in a row, so a second call
+cannot see what the first left in the shared array; that a batch of exactly
+the array's limit of strings decodes correctly; that a call after the first
+leaves the device's free memory unchanged; and that a batch over the limit is
+refused with a clear message.
 """
 import ctypes
 
@@ -53,6 +55,27 @@ def encoded_batch(orc, count, seed, error_rate):
     return text, eoff, aid
 
 
+def oracle_decode(orc, text, eoff, aid):
+    """The oracle's results and decoded bytes, at b64_batch_offsets' layout
+    (capacity 3 * ceil(len / 4) per string)."""
+    lens = eoff[1:] - eoff[:-1]
+    doff = wl.offsets_from_lengths((lens + 3) // 4 * 3)
+    padded = (aid == 0).astype(np.int32)
+    dst, res = orc.decode_batch(text, eoff, doff, orc.standard_alphabet() + orc.url_alphabet(),
+                                aid.astype(np.int32), padded, int(doff[-1]))
+    return res, dst, doff
+
+
+def check_against_oracle(orc, text, eoff, aid, got_res, got_dst):
+    want_res, want_dst, doff = oracle_decode(orc, text, eoff, aid)
+    res = got_res.cpu().numpy()
+    assert np.array_equal(res, want_res)
+    out = got_dst.cpu().numpy()
+    for i in np.nonzero(res > 0)[0]:
+        o = int(doff[i])
+        assert np.array_equal(out[o:o + res[i]], want_dst[o:o + res[i]]), i
+
+
 def run_both(b64, text, eoff, aid, units):
     alphs = [b64.Alphabet.standard(), b64.Alphabet.url()]
     src = torch.from_numpy(text).cuda()
@@ -81,7 +104,43 @@ def test_noalloc_equals_workspace_call_twice_in_a_row(b64, orc):
         want_res, got_res, want_dst, got_dst = run_both(b64, text, eoff, aid, units)
         assert torch.equal(got_res, want_res)
         assert torch.equal(got_dst, want_dst)
+        check_against_oracle(orc, text, eoff, aid, got_res, got_dst)
     assert int((want_res < 0).sum()) == 0
+
+
+def test_noalloc_at_its_limit_and_without_new_device_memory(b64, orc):
+    """Exactly 65,536 strings (the largest batch it accepts), decoded
+    twice: both calls give the oracle's results, and the second call, made
+    once every buffer exists and the first call has loaded the kernels,
+    leaves the device's free memory as it was."""
+    text, eoff, aid = encoded_batch(orc, LIMIT, seed=63, error_rate=0.05)
+    alphs = [b64.Alphabet.standard(), b64.Alphabet.url()]
+    src = torch.from_numpy(text).cuda()
+    off = torch.from_numpy(eoff).cuda()
+    d_aid = torch.from_numpy(aid).cuda()
+    dst_off = b64.batch_offsets(off, alphs, d_aid, decode=True)
+    dst = torch.zeros(int(dst_off[-1]) + 64, dtype=torch.uint8, device="cuda")
+    res = torch.zeros(LIMIT, dtype=torch.int64, device="cuda")
+    arr = (ctypes.c_void_p * 2)(alphs[0].handle, alphs[1].handle)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def call():
+        rc = b64.lib().b64_decode_batch_noalloc(
+            src.data_ptr(), off.data_ptr(), LIMIT, dst.data_ptr(), dst_off.data_ptr(), arr, 2,
+            d_aid.data_ptr(), res.data_ptr(), 0, stream)
+        assert rc == b64.B64_SUCCESS, b64.last_error()
+        torch.cuda.synchronize()
+
+    call()
+    check_against_oracle(orc, text, eoff, aid, res, dst)
+    res.fill_(7)
+    dst.fill_(0)
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    call()
+    assert torch.cuda.mem_get_info()[0] == free_before
+    check_against_oracle(orc, text, eoff, aid, res, dst)
+    assert int((res < 0).sum()) > 0
 
 
 def test_noalloc_refuses_batches_over_its_limit(b64):

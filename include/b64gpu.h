@@ -38,7 +38,10 @@
  *     where a call says it synchronises.
  *   - The library writes nothing past the output length it returns; on a
  *     decode error the content of dst is unspecified but nothing past
- *     b64_decoded_max_length(len) is written.
+ *     b64_decoded_max_length(len) is written. One exception, stated at
+ *     b64_mime_decode_async: a MIME input whose line layout breaks part way
+ *     may leave bytes past the returned length (within
+ *     b64_decoded_max_length(len)) overwritten.
  *   - src and dst must not overlap.
  *   - Any alignment is accepted; 16-byte aligned src and dst take the fast
  *     path.
@@ -153,11 +156,19 @@ int64_t b64_decode(const uint8_t* src, size_t len, uint8_t* dst, const b64_alpha
  * Sec. 1). The remaining characters are decoded exactly as b64_decode_async
  * decodes them (Sec. 2, Sec. 3.2, and the rules at the top of this file);
  * error offsets are offsets into the original input, and a bad length is
- * reported at offset len. Four kernels on `stream`: a count of the data
- * characters of every 4 KiB segment, a scan of those counts, the decode of
- * every segment at its known output offset, and a one-thread kernel that
- * writes *d_result: the decoded length, -(offset+1), or B64_E_TIMEOUT (a
- * bounded wait ran out).
+ * reported at offset len. Five kernels on `stream`. First a one-pass decode:
+ * if the input starts with a line of L data characters (L a multiple of 4,
+ * below 1024) and a CR LF or LF break, every 4 KiB segment is decoded at
+ * the output offset that this line layout gives it, and checks that its
+ * whitespace sits exactly where the layout puts breaks. Only if a segment
+ * does not (or there is no layout) do the next three kernels run: a count of
+ * the data characters of every segment, a scan of those counts, and the
+ * decode of every segment at its counted output offset; otherwise they
+ * return at once. A one-thread kernel then writes *d_result: the decoded
+ * length, -(offset+1), or B64_E_TIMEOUT (a bounded wait ran out). When the
+ * layout breaks part way, the one-pass kernel may already have written the
+ * segments after the break at their layout offsets: bytes past the returned
+ * length, within b64_decoded_max_length(len), can then be overwritten.
  * workspace: device memory of b64_mime_workspace_size(len) bytes, 8-byte
  * aligned, caller-owned, busy until the work completes (one call at a time per
  * workspace). dst needs b64_decoded_max_length(len) bytes. */

@@ -65,6 +65,11 @@ constexpr uint32_t kSpace = 0xC0u;                      // table class of CR, LF
 // the segment.
 constexpr uint64_t kCountMask = (uint64_t(1) << 54) - 1;
 
+// status[7] of the single-document call: the first segment whose whitespace
+// does not sit where the line layout puts it (the one-pass kernel's check),
+// or kNoSegment; the count, scan and decode kernels run only when it is set.
+constexpr uint64_t kNoSegment = ~uint64_t(0);
+
 __device__ uint32_t g_fault;
 
 __host__ __device__ __forceinline__ uint64_t make_state(uint64_t flag, uint32_t last,
@@ -191,8 +196,10 @@ __device__ __forceinline__ uint32_t warp_scan_max32(uint32_t v, int lane) {
 __global__ void __launch_bounds__(kCountThreads, 4)
     mime_count_kernel(const uint8_t* __restrict__ src, uint64_t m,
                       unsigned long long* __restrict__ states,
-                      unsigned long long* __restrict__ totals, uint64_t nseg) {
+                      unsigned long long* __restrict__ totals, uint64_t nseg,
+                      const unsigned long long* __restrict__ status) {
     __shared__ uint32_t s_cnt[kSegsPerBlock], s_key[kSegsPerBlock];
+    if (status[7] == kNoSegment) return;  // the one-pass kernel decoded everything
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool aligned = (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
     const uint64_t first = uint64_t(blockIdx.x) * kSegsPerBlock;
@@ -252,6 +259,10 @@ __global__ void __launch_bounds__(kScanThreads)
     __shared__ uint64_t warp_key[kScanThreads / 32];
     __shared__ uint32_t first_space;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (status[7] == kNoSegment) return;  // the one-pass kernel decoded everything
+    // the decode kernel recomputes the error and '=' words: what the one-pass
+    // kernel left there came from counts that may be wrong past status[7]
+    if (tid < 3) status[tid] = kNoError;
     // status[6] = the line layout word if the input starts with a line of L
     // data characters and CR LF or LF, L a multiple of 4 below 1024 (the
     // decode kernel's fast path, checked there segment by segment), else 0
@@ -517,13 +528,15 @@ __device__ __forceinline__ void copy_out(const uint8_t* buf, uint32_t skip, uint
 // (not '=', not whitespace) and every byte it skips is whitespace. Only then
 // does it copy the output out (kLinesDone). If the count of data characters
 // before the segment does not fit the layout it returns kLinesNo at once,
-// the staged bytes untouched; if a check fails it returns kLinesSpoilt:
-// nothing has been written to global memory, but the staged bytes are
-// spoilt and the caller stages the segment again for the general path
-// (which also finds the segment's errors). S: the segment's raw start in the
-// document; P: the data characters before it; prev_last: the last data byte
-// before it.
-enum LinesResult { kLinesNo, kLinesDone, kLinesSpoilt };
+// the staged bytes untouched; if a check fails it returns kLinesSpoilt
+// (whitespace sits where the layout has it, but some data byte is outside the
+// alphabet or is '=') or kLinesIrregular (a whitespace byte where the layout
+// has data, or a break position holding something else): nothing has been
+// written to global memory, but the staged bytes are spoilt and the caller
+// stages the segment again for the general path (which also finds the
+// segment's errors). S: the segment's raw start in the document; P: the data
+// characters before it; prev_last: the last data byte before it.
+enum LinesResult { kLinesNo, kLinesDone, kLinesSpoilt, kLinesIrregular };
 
 // The line layout's constants (L = 0: the input does not start with it).
 // word: L | eol << 16 (eol = 2 for CR LF, 1 for LF), 0 for none.
@@ -569,14 +582,16 @@ __device__ LinesResult decode_lines(uint8_t* buf, const uint8_t* lut, int lane,
         const uint32_t t = rP + d, line = __umulhi(t, ly.inv);
         return uint32_t(off0) + line * eol + t;  // line Q + (t - line L)
     };
-    uint32_t bad = 0;
+    // bad: bit 7 of every data value OR-ed (outside the alphabet, '=' or
+    // whitespace), bit 6 also for whitespace (kSpace); viol: a layout violation
+    uint32_t bad = 0, viol = 0;
     // the skipped bytes: break j at raw offsets L - r + j Q (and one more
     // for CR LF)
     for (int32_t rel = int32_t(L) - int32_t(r) + lane * int32_t(Q); rel < int32_t(kSeg);
          rel += 32 * int32_t(Q)) {
-        if (rel >= 0 && lut[raw[rel]] != kSpace) bad = 0x80u;
+        if (rel >= 0 && lut[raw[rel]] != kSpace) viol = 1u;
         if (kCrLf && rel + 1 >= 0 && rel + 1 < int32_t(kSeg) && lut[raw[rel + 1]] != kSpace)
-            bad = 0x80u;
+            viol = 1u;
     }
     // groups: the one holding P (edge A: it started before the segment), the
     // whole ones, the one holding P1 - 1 (edge B: it ends after the segment)
@@ -590,12 +605,12 @@ __device__ LinesResult decode_lines(uint8_t* buf, const uint8_t* lut, int lane,
     if (lane < 4 && rA && uint32_t(lane) + 1 >= rA) {
         const uint32_t t = uint32_t(lane);
         const uint32_t v = t + 1 == rA ? lut[prev_last] : lut[raw[raw_of(t - rA)]];
-        if (t + 1 != rA) bad |= v & 0x80u;
+        if (t + 1 != rA) bad |= v & 0xC0u;
         ea = (v & 63u) << (6 * (3 - t));
     } else if (lane >= 4 && lane < 8 && rB >= 2 && uint32_t(lane) - 4 < rB) {
         const uint32_t t = uint32_t(lane) - 4;
         const uint32_t v = lut[raw[raw_of(cA + 4 * nfull + t)]];
-        bad |= v & 0x80u;
+        bad |= v & 0xC0u;
         eb = (v & 63u) << (6 * (3 - t));
     }
     const uint32_t wA = __reduce_or_sync(0xffffffffu, ea);
@@ -642,6 +657,7 @@ __device__ LinesResult decode_lines(uint8_t* buf, const uint8_t* lut, int lane,
     const uint32_t nwhole = nfull / (32 * kPer) * (32 * kPer);
     for (uint32_t i0 = 0; i0 < nwhole; i0 += 32 * kPer) round(i0, std::false_type{});
     if (nwhole < nfull) round(nwhole, std::true_type{});
+    if (__any_sync(0xffffffffu, viol != 0 || (bad & 0x40u) != 0)) return kLinesIrregular;
     if (__any_sync(0xffffffffu, bad & 0x80u)) return kLinesSpoilt;
     if (uint32_t(lane) < cA)  // bytes rA - 1 .. 2 of edge A
         buf[base - cA + lane] = uint8_t(wA >> (16 - 8 * (rA - 1 + lane)));
@@ -682,6 +698,7 @@ __global__ void __launch_bounds__(kThreads, 6)
         fence_mbar_init();
     }
     __syncthreads();  // the only block-wide barrier: tables and barriers ready
+    if (status[7] == kNoSegment) return;  // the one-pass kernel decoded everything
     const bool aligned = (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
     unsigned long long* timeout = status + 4;
     const LineLayout ly{uint32_t(status[6])};
@@ -756,7 +773,7 @@ __global__ void __launch_bounds__(kThreads, 6)
             ++lk;
         }
         if (fast != kLinesDone) {
-            if (fast == kLinesSpoilt) {  // stage the segment again
+            if (fast == kLinesSpoilt || fast == kLinesIrregular) {  // stage the segment again
                 uint4 v[kRows];
                 load_rows(src + base, len, aligned, lane, v);
 #pragma unroll
@@ -765,6 +782,165 @@ __global__ void __launch_bounds__(kThreads, 6)
                 __syncwarp();
             }
             decode_segment(buf, lut, flags, lane, P, prev_last, base, dst, status);
+        }
+        by_copy = next_by_copy;
+    }
+}
+
+// ---------------------------------------------------------------- 0. one pass
+// Inputs laid out as lines of L data characters and a fixed break (the layout
+// of the first line, as the scan kernel detects it): the data characters
+// before a segment that starts at raw position k Q + r are then P = k L +
+// min(r, L), with no count, so every segment is decoded from one read of the
+// input. Each whole segment takes the line-layout fast path with that P;
+// the path also tells a segment whose whitespace sits elsewhere than the
+// layout's breaks (kLinesIrregular) from one that only holds bad bytes or '='
+// (kLinesSpoilt, decoded by the general path with the same P). The last,
+// shorter segment is checked byte by byte against the layout and decoded by
+// the general path. The first irregular segment is recorded in status[7]:
+// its own P is right, but those of later segments may not be, so the count,
+// scan and decode kernels then decode the whole input again. Without a
+// layout status[7] = 0 at once. The one-pass kernel writes output only at
+// the positions its P gives, inside b64_decoded_max_length(m).
+__device__ __forceinline__ uint32_t block_line_layout(const uint8_t* __restrict__ src, uint64_t m,
+                                                      uint32_t* s_first, uint32_t* s_word) {
+    const int tid = threadIdx.x;
+    if (tid == 0) *s_first = kScanThreads;
+    __syncthreads();
+    for (int i = tid; i < kScanThreads; i += blockDim.x) {
+        if (uint64_t(i) < m) {
+            const uint32_t c = src[i];
+            if (c == '\r' || c == '\n' || c == ' ') atomicMin(s_first, uint32_t(i));
+        }
+    }
+    __syncthreads();
+    if (tid == 0) *s_word = line_layout_word(src, m, *s_first);
+    __syncthreads();
+    return *s_word;
+}
+
+// Whether the whitespace of a segment's first len bytes (staged at raw,
+// starting at layout column r of its line) is exactly at the layout's
+// break positions. Warp-collective.
+__device__ __forceinline__ bool segment_fits_layout(const uint8_t* raw, uint32_t len,
+                                                    const LineLayout& ly, uint32_t r, int lane) {
+    bool ok = true;
+    for (uint32_t i = lane; i < len; i += 32) {
+        const uint32_t col = (r + i) % ly.Q;
+        const uint32_t c = raw[i];
+        const bool space = c == '\r' || c == '\n' || c == ' ';
+        if (space != (col >= ly.L)) ok = false;
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+__global__ void __launch_bounds__(kThreads, 6)
+    mime_onepass_kernel(const uint8_t* __restrict__ src, uint64_t m, uint8_t* __restrict__ dst,
+                        const __grid_constant__ DecodeTable tab, int flags,
+                        unsigned long long* __restrict__ status, uint64_t nseg,
+                        uint64_t wait_limit_ns) {
+    __shared__ uint8_t lut[256];  // 0..63, 0x80 (bad or '='), kSpace
+    __shared__ __align__(16) uint8_t bufs[kWarps][2][kBuf];
+    __shared__ uint64_t bars[kWarps][2];
+    __shared__ uint32_t s_first, s_word;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < 64; i += kThreads) reinterpret_cast<uint32_t*>(lut)[i] = tab.w[i];
+    if (lane == 0) {
+        mbar_init(&bars[warp][0], 1);
+        mbar_init(&bars[warp][1], 1);
+        fence_mbar_init();
+    }
+    const uint32_t word = block_line_layout(src, m, &s_first, &s_word);  // synchronises
+    if (tid == 0) lut['\r'] = lut['\n'] = lut[' '] = uint8_t(kSpace);
+    if (blockIdx.x == 0 && tid == 0) status[6] = word;
+    if (!word) {  // no layout: the counting path decodes everything
+        if (blockIdx.x == 0 && tid == 0) atomicMin(status + 7, 0ull);
+        return;
+    }
+    __syncthreads();  // the table's whitespace entries
+    const LineLayout ly{word};
+    const bool aligned = (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
+    const uint64_t GW = uint64_t(gridDim.x) * kWarps;
+
+    // Whole aligned segments come by one bulk copy, with the 16 bytes before
+    // the segment (they hold the data byte before it) in the buffer's lead.
+    auto issue = [&](uint64_t seg, int k) -> bool {
+        const uint64_t base = seg * kSeg;
+        if (!aligned || m - base < kSeg) return false;
+        if (lane == 0) {
+            const uint32_t lead = seg ? kLead : 0u;
+            mbar_arrive_expect_tx(&bars[warp][k], kSeg + lead);
+            bulk_load(bufs[warp][k] + kLead - lead, src + base - lead, kSeg + lead,
+                      &bars[warp][k]);
+        }
+        return true;
+    };
+    auto stage_plain = [&](uint8_t* buf, uint64_t base, uint32_t len, bool lead) {
+        uint4 v[kRows];
+        load_rows(src + base, len, aligned, lane, v);
+#pragma unroll
+        for (int r = 0; r < kRows; ++r)
+            *reinterpret_cast<uint4*>(buf + kLead + kRow * r + 16 * lane) = v[r];
+        if (lead && lane < int(kLead)) buf[lane] = src[base - kLead + lane];
+        __syncwarp();
+    };
+
+    uint32_t phases = 0;
+    uint64_t seg = uint64_t(blockIdx.x) * kWarps + warp;
+    int k = 0;
+    bool by_copy = seg < nseg ? issue(seg, 0) : false;
+    // the segment's raw start as lk ly.Q + lr, stepped by dk ly.Q + dr
+    uint64_t lk = seg * kSeg / ly.Q;
+    uint32_t lr = uint32_t(seg * kSeg - lk * ly.Q);
+    const uint64_t dk = GW * kSeg / ly.Q;
+    const uint32_t dr = uint32_t(GW * kSeg - dk * ly.Q);
+    for (; seg < nseg; seg += GW, k ^= 1) {
+        const uint64_t next = seg + GW;
+        fence_proxy_async_smem();  // this lane's accesses to buffer k^1 before the copy below
+        __syncwarp();
+        const bool next_by_copy = next < nseg ? issue(next, k ^ 1) : false;
+        uint8_t* buf = bufs[warp][k];
+        const uint64_t base = seg * kSeg;
+        const uint32_t len = uint32_t(m - base < kSeg ? m - base : kSeg);
+        if (by_copy) {
+            const bool ok = __all_sync(0xffffffffu,
+                                       wait_copy(&bars[warp][k], (phases >> k) & 1u, wait_limit_ns));
+            phases ^= 1u << k;
+            if (!ok) {
+                if (next_by_copy)  // let the copy in flight land before the block can exit
+                    wait_copy(&bars[warp][k ^ 1], (phases >> (k ^ 1)) & 1u, wait_limit_ns);
+                if (lane == 0) {
+                    atomicExch(status + 4, 1ull);
+                    atomicOr(&g_fault, 1u);
+                }
+                return;
+            }
+        } else {
+            stage_plain(buf, base, len, seg > 0);
+        }
+        // the layout's count before the segment, and its last data byte
+        const uint64_t P = lk * ly.L + (lr < ly.L ? lr : ly.L);
+        const uint32_t back = lr == 0 ? 1 + ly.eol : lr > ly.L ? lr - ly.L + 1 : 1u;
+        const uint32_t prev_last = P ? buf[kLead - back] : 0u;
+        bool irregular = false;
+        if (len == kSeg) {
+            const LinesResult r =
+                decode_segment_lines(buf, lut, lane, ly, lk, lr, P, prev_last, dst);
+            irregular = r == kLinesIrregular || r == kLinesNo;
+            if (r == kLinesSpoilt) {  // bad bytes or '=': the general path, same P
+                stage_plain(buf, base, len, false);
+                decode_segment(buf, lut, flags, lane, P, prev_last, base, dst, status);
+            }
+        } else {
+            irregular = !segment_fits_layout(buf + kLead, len, ly, lr, lane);
+            if (!irregular) decode_segment(buf, lut, flags, lane, P, prev_last, base, dst, status);
+        }
+        if (irregular && lane == 0) atomicMin(status + 7, (unsigned long long)seg);
+        lk += dk;
+        lr += dr;
+        if (lr >= ly.Q) {
+            lr -= ly.Q;
+            ++lk;
         }
         by_copy = next_by_copy;
     }
@@ -818,7 +994,18 @@ __global__ void mime_finalize_kernel(const uint8_t* __restrict__ src, uint64_t m
         *d_result = B64_E_TIMEOUT;
         return;
     }
-    *d_result = mime_result(src, m, flags, tab, status[5], status);
+    uint64_t whole = status[5];
+    if (status[7] == kNoSegment && status[6]) {
+        // one pass, every segment in the layout: the data characters and the
+        // last one follow from it
+        const LineLayout ly{uint32_t(status[6])};
+        const uint64_t k = m / ly.Q, r = m - k * ly.Q;
+        const uint64_t mc = k * ly.L + (r < ly.L ? r : ly.L);
+        const uint64_t j = mc - 1;
+        const uint32_t last = mc ? src[j / ly.L * ly.Q + j % ly.L] : 0u;
+        whole = make_state(mc != 0, last, mc);
+    }
+    *d_result = mime_result(src, m, flags, tab, whole, status);
 }
 
 // ---------------------------------------------------------------- batched documents
@@ -1148,7 +1335,7 @@ __global__ void __launch_bounds__(32 * kDocWarps, 6)
             fast = decode_segment_lines(buf, luts[a], lane, ly, lk, uint32_t(S - lk * ly.Q), P,
                                         prev_last, dst + dst_off[ds.d]);
         }
-        if (fast == kLinesSpoilt) stage_plain();
+        if (fast == kLinesSpoilt || fast == kLinesIrregular) stage_plain();
         if (fast != kLinesDone)
             decode_segment(buf, luts[a], flags, lane, P, prev_last, ds.k * kSeg,
                            dst + dst_off[ds.d], st3);
@@ -1203,7 +1390,7 @@ struct Occ {
     std::once_flag once;
     int ctas = 1;
 };
-Occ g_occ[64], g_cd_occ[64], g_dd_occ[64];
+Occ g_occ[64], g_op_occ[64], g_cd_occ[64], g_dd_occ[64];
 
 template <class K>
 int occupancy(K kernel, int threads, Occ& occ) {
@@ -1233,22 +1420,31 @@ cudaError_t launch_mime_decode(const uint8_t* src, uint64_t m, uint8_t* dst,
     unsigned long long* states = status + 8;
     unsigned long long* totals = states + nseg;
     // status[0..2] (first bad byte, first '=' raw and compacted) start at
-    // "none"; status[3..7] (status[4]: the timeout word; status[5]: the whole
-    // input's state) at zero.
+    // "none"; status[3..6] (status[4]: the timeout word; status[5]: the whole
+    // input's state; status[6]: the line layout) at zero; status[7] (the
+    // first segment off the layout) at "none".
     cudaError_t e = cudaMemsetAsync(status, 0xFF, 3 * sizeof(uint64_t), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(status + 3, 0, 5 * sizeof(uint64_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status + 3, 0, 4 * sizeof(uint64_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status + 7, 0xFF, sizeof(uint64_t), st);
     if (e != cudaSuccess) return e;
     if (nseg) {
         const DeviceInfo& di = device_info();
-        mime_count_kernel<<<unsigned(nblk), kCountThreads, 0, st>>>(src, m, states, totals, nseg);
+        uint64_t grid = uint64_t(di.sm_count) *
+                        occupancy(mime_onepass_kernel, kThreads, g_op_occ[di.device & 63]);
+        const uint64_t need = (nseg + kWarps - 1) / kWarps;
+        if (need < grid) grid = need;
+        mime_onepass_kernel<<<unsigned(grid), kThreads, 0, st>>>(src, m, dst, tab, flags, status,
+                                                                 nseg, wait_limit_ns);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        mime_count_kernel<<<unsigned(nblk), kCountThreads, 0, st>>>(src, m, states, totals, nseg,
+                                                                    status);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         mime_scan_kernel<<<1, kScanThreads, 0, st>>>(totals, nblk, status, src, m);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        uint64_t grid = uint64_t(di.sm_count) *
-                        occupancy(mime_decode_kernel, kThreads, g_occ[di.device & 63]);
-        const uint64_t need = (nseg + kWarps - 1) / kWarps;
+        grid = uint64_t(di.sm_count) * occupancy(mime_decode_kernel, kThreads, g_occ[di.device & 63]);
         if (need < grid) grid = need;
         mime_decode_kernel<<<unsigned(grid), kThreads, 0, st>>>(
             src, m, dst, tab, flags, status, states, totals, nseg, wait_limit_ns);

@@ -177,7 +177,7 @@ class NvmlClockSampler:
     REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, gpu_id: str, interval_s: float = 0.002):
+    def __init__(self, gpu_id: str, interval_s: float = 0.0005):
         self.gpu_id = gpu_id
         self.interval_s = interval_s
         self.samples: list[tuple[int, int, int, int]] = []   # (sm MHz, max MHz, reasons, mW)
@@ -200,20 +200,24 @@ class NvmlClockSampler:
                 nv.nvmlDeviceGetCurrentClocksThrottleReasons
         except (OSError, AttributeError):
             return False
-        self._nvml, self._dev = nv, dev
+        mx = ctypes.c_uint()
+        nv.nvmlDeviceGetMaxClockInfo(dev, self.CLOCK_SM, ctypes.byref(mx))
+        self._nvml, self._dev, self._max = nv, dev, mx.value
+        self._sm, self._rs, self._pw = ctypes.c_uint(), ctypes.c_ulonglong(), ctypes.c_uint()
+        self._power = 0
         return True
 
     def _sample(self):
+        # two queries a sample (SM clock, event reasons); power every 16th
         import ctypes
         nv, dev = self._nvml, self._dev
-        sm, mx, pw = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_uint()
-        rs = ctypes.c_ulonglong()
-        if nv.nvmlDeviceGetClockInfo(dev, self.CLOCK_SM, ctypes.byref(sm)) != 0:
+        if nv.nvmlDeviceGetClockInfo(dev, self.CLOCK_SM, ctypes.byref(self._sm)) != 0:
             return
-        nv.nvmlDeviceGetMaxClockInfo(dev, self.CLOCK_SM, ctypes.byref(mx))
-        self._reasons_fn(dev, ctypes.byref(rs))
-        nv.nvmlDeviceGetPowerUsage(dev, ctypes.byref(pw))
-        self.samples.append((sm.value, mx.value, rs.value, pw.value))
+        self._reasons_fn(dev, ctypes.byref(self._rs))
+        if len(self.samples) % 16 == 0:
+            nv.nvmlDeviceGetPowerUsage(dev, ctypes.byref(self._pw))
+            self._power = self._pw.value
+        self.samples.append((self._sm.value, self._max, self._rs.value, self._power))
 
     def _run(self):
         while not self._stop.is_set():
@@ -646,6 +650,24 @@ def batch_workload(args) -> dict:
     d_aid = torch.from_numpy(aid).to(dev)
     total_in = int(off[-1])
 
+    align16 = args.batch_layout == "align16"
+    # the strings' encoded lengths (packed output offsets)
+    enc_len = b64.batch_offsets(d_off, alphs, d_aid, decode=False)
+    enc_len = enc_len[1:] - enc_len[:-1]
+    total_enc = int(enc_len.sum())
+
+    def time_codec(codec, steps):
+        for _ in range(max(args.warmup, 3)):
+            codec.run()
+        codec.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(codec.stream)
+        for _ in range(steps):
+            codec.run()
+        e1.record(codec.stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+
     out = {}
     texts = None
     clocks = clock_sampler(gpu_uuid(dev)).__enter__()   # sampled over both ops' timed loops
@@ -654,7 +676,7 @@ def batch_workload(args) -> dict:
             src, src_off = d_src, d_off
         else:
             src, src_off = texts
-        codec = BatchCodec(op, n, src.numel(), alphs, dev)
+        codec = BatchCodec(op, n, src.numel(), alphs, dev, align16=align16)
         cap = codec.load(src, src_off, d_aid)
         # output offsets (b64_batch_offsets), timed on their own
         with torch.cuda.stream(codec.stream):
@@ -675,34 +697,38 @@ def batch_workload(args) -> dict:
             units, timings = autotune.best_units(op, codec.src, codec.src_off, codec.dst,
                                                  codec.dst_off, alphs, codec.alph_id[:n])
         codec.tile_units = units
-        for _ in range(max(args.warmup, 3)):
-            codec.run()
+        batch_ms = time_codec(codec, args.steps)
+        with torch.cuda.stream(codec.stream):
+            codec.dst.zero_()   # the bytes between aligned strings stay zero
+        codec.run()
         codec.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(codec.stream)
-        for _ in range(args.steps):
-            codec.run()
-        e1.record(codec.stream)
-        e1.synchronize()
-        batch_ms = e0.elapsed_time(e1) / args.steps
         res = codec.results[:n].clone()
         batch_out = codec.dst[:cap].clone()
         in_bytes = src.numel()
+        # the same batch with packed output offsets (the other layout), for comparison
+        pcodec = BatchCodec(op, n, src.numel(), alphs, dev, tile_units=units, align16=False)
+        pcap = pcodec.load(src, src_off, d_aid)
+        packed_ms = time_codec(pcodec, args.steps)
         # algorithmic bytes: the strings read, their encoded / decoded bytes written
-        alg = in_bytes + (cap if op == "encode" else total_in)
+        alg = in_bytes + (total_enc if op == "encode" else total_in)
         roof = {"bound": "hbm", "achieved": alg / (batch_ms / 1e3) / 1e9,
                 "peak": peaks()["hbm_gbs"], "unit": "GB/s", "traffic_alg_bytes": alg}
         roof["frac"] = roof["achieved"] / roof["peak"]
+        packed = {"batch_ms": packed_ms, "input_gbps": in_bytes / (packed_ms / 1e3) / 1e9,
+                  "roofline_frac": alg / (packed_ms / 1e3) / 1e9 / roof["peak"]}
         if op == "encode":
-            texts = (batch_out, codec.dst_off.clone())
-            assert torch.equal(res, codec.dst_off[1:] - codec.dst_off[:-1])
+            assert torch.equal(res, enc_len)
+            texts = (pcodec.dst[:pcap].clone(), pcodec.dst_off.clone())   # packed text
         else:
             assert torch.equal(res, d_off[1:] - d_off[:-1])
+        assert torch.equal(pcodec.results[:n], res)
+        del pcodec
 
         if args.no_per_string:
             out[op] = {"batch_ms": batch_ms, "input_gbps": in_bytes / (batch_ms / 1e3) / 1e9,
-                       "roofline": roof, "tile_units": units, "autotune_ms": timings,
-                       "offsets_ms": offsets_ms}
+                       "roofline": roof, "tile_units": units,
+                       "tile": autotune.describe(units), "autotune_ms": timings,
+                       "offsets_ms": offsets_ms, "packed_offsets": packed}
             continue
         # One launch per string through the single-buffer calls.
         hoff = codec.src_off.cpu().numpy()
@@ -748,6 +774,7 @@ def batch_workload(args) -> dict:
         e1.synchronize()
         graph_ms = e0.elapsed_time(e1)
         if op == "encode":
+            # both outputs start from zeros, and neither call writes between strings
             identical = bool(torch.equal(per_dst, batch_out))
         else:
             # same results; decoded bytes compared string by string (a string's
@@ -762,11 +789,13 @@ def batch_workload(args) -> dict:
                     break
         del g
         out[op] = {"batch_ms": batch_ms, "input_gbps": in_bytes / (batch_ms / 1e3) / 1e9,
-                   "roofline": roof, "tile_units": units, "autotune_ms": timings,
+                   "roofline": roof, "tile_units": units, "tile": autotune.describe(units),
+                   "autotune_ms": timings,
                    "offsets_ms": offsets_ms,
                    "per_string_eager_ms": eager_ms, "per_string_graph_ms": graph_ms,
                    "speedup_vs_eager": eager_ms / batch_ms,
                    "speedup_vs_graph": graph_ms / batch_ms, "identical_output": identical,
+                   "packed_offsets": packed,
                    "launches_per_batch": 2 if op == "encode" else 3}
     clocks.__exit__(None, None, None)
     step_ms = out["encode"]["batch_ms"] + out["decode"]["batch_ms"]
@@ -775,6 +804,9 @@ def batch_workload(args) -> dict:
             "config": {"workload": f"{n} strings, lognormal lengths (median 1 KiB, sigma 1.5, "
                                    "1 B..1 MiB, seed 2), 50/50 standard-padded / url-unpadded",
                        "input_bytes": total_in, "encoded_bytes": int(texts[0].numel()),
+                       "output_offsets": ("b64_batch_offsets with B64_OFFSETS_ALIGN16 (16-byte "
+                                          "aligned string starts); packed offsets timed beside"
+                                          if align16 else "b64_batch_offsets, packed"),
                        "l2": "batch input and output (314 MB + 419 MB) larger than L2; no flush"},
             "encode": out["encode"], "decode": out["decode"], "clocks": clocks.summary(),
             # per step: encode results + tile kernel; decode tile + finalize kernel
@@ -1105,6 +1137,9 @@ def main():
                     help="batch workload: fixed tile size instead of the autotuner's")
     ap.add_argument("--no-per-string", action="store_true",
                     help="batch workload: skip the one-launch-per-string comparison")
+    ap.add_argument("--batch-layout", default="align16", choices=["align16", "packed"],
+                    help="batch workload: output offsets (16-byte aligned string starts, or "
+                         "packed); the other layout is timed beside")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

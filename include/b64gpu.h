@@ -218,7 +218,10 @@ int b64_mime_decode_batch(const uint8_t* src, const int64_t* src_off, int64_t n,
  * device int64, receiving what the single-buffer call returns for that string
  * (encode: output length; decode: length or -(offset+1), offset within the
  * string). tile_units: bytes per thread of a tile as 1, 2, 4 or 8 units of
- * 12 input bytes (encode) or 16 characters (decode); 0 picks 4. workspace:
+ * 12 input bytes (encode) or 16 characters (decode), 0 picks 4; optionally
+ * OR-ed with (b << 8), b resident blocks of 8 warps per SM (at most as many
+ * as fit; 0: as many as fit), the number of warps the batch is spread over.
+ * Both are the autotuner's choices; any value gives the same results. workspace:
  * device memory of at least b64_batch_workspace_size(n) bytes, 256-byte
  * aligned, owned by the caller and busy until the enqueued work completes.
  * Strings may start at any alignment; src and dst may be NULL only if every
@@ -262,10 +265,19 @@ int b64_decode_batch_noalloc(const uint8_t* src, const int64_t* src_off, int64_t
                              void* stream);
 
 /* dst_off[0..n] (n+1 device int64) = exclusive scan of each string's output
- * capacity: its encoded length (decode == 0) or 3*ceil(len/4) (decode != 0).
- * dst_off[n] is the total. One kernel on `stream`. */
+ * capacity: its encoded length, or 3*ceil(len/4) with B64_OFFSETS_DECODE.
+ * With B64_OFFSETS_ALIGN16 each capacity is rounded up to a multiple of 16
+ * bytes, so that with a 16-byte aligned dst every string's output starts
+ * 16-byte aligned; the batched kernels then store each string's output
+ * straight from registers (with any other layout they realign it through
+ * shared memory first). The bytes between one string's output and the next
+ * string are left untouched. dst_off[n] is the total. flags: 0 or the two
+ * flags OR-ed (0 and 1 as the encode / decode switch of earlier versions);
+ * other bits are B64_ERR_INVALID_ARGUMENT. Three kernels on `stream`. */
+#define B64_OFFSETS_DECODE 1
+#define B64_OFFSETS_ALIGN16 2
 int b64_batch_offsets(const int64_t* src_off, int64_t n, const b64_alphabet* const* alphabets,
-                      int n_alphabets, const uint8_t* alph_id, int decode, int64_t* dst_off,
+                      int n_alphabets, const uint8_t* alph_id, int flags, int64_t* dst_off,
                       void* stream);
 
 /* ---------------------------------------------------------------- host buffers

@@ -1,12 +1,17 @@
-"""Autotuner for the batched kernels' tile size.
+"""Autotuner for the batched kernels' tile shape.
 
-A tile is one warp; its size is 32 threads x U units, a unit being 12 input
-bytes (encode) or 16 characters (decode), so U is the bytes-per-thread knob
-and a string of L bytes gets ceil(L / (32*12*U)) warps (the threads-per-string
-knob follows from it). The tuner times every U in {1, 2, 4, 8} on the
-caller's own batch with CUDA events, keeps the fastest, and caches the choice
-in a JSON file keyed by GPU name, SM count, operation and the batch's size
-buckets (log2 of the string count and of the mean string length).
+Two axes, both passed to the kernels in `tile_units`:
+- bytes per thread: a tile is 32 threads x U units, a unit being 12 input
+  bytes (encode) or 16 characters (decode), U in {2, 4, 8};
+- threads per batch: B resident blocks of 8 warps per SM (0 = as many as fit,
+  1 or 2), i.e. how many warps the batch is spread over. Within a tile a
+  string's units are coded 32 at a time, one a thread, so a string of L bytes
+  meets up to min(32, ceil(L / 12)) threads at once and ceil(L / (32 * 12 * U))
+  tiles.
+The tuner times every (U, B) on the caller's own batch with CUDA events,
+keeps the fastest, and caches it in a JSON file keyed by GPU name, SM count,
+operation and the batch's size buckets (log2 of the string count and of the
+mean string length). The value returned (and cached) is U | B << 8.
 
 The cache lives in $B64GPU_CACHE, else $XDG_CACHE_HOME/b64gpu/autotune.json,
 else ~/.cache/b64gpu/autotune.json.
@@ -22,7 +27,14 @@ import torch
 
 from . import binding as b64
 
-UNITS = (1, 2, 4, 8)
+UNITS = (2, 4, 8)
+BLOCKS = (0, 1, 2)          # resident blocks an SM (0: as many as fit)
+CHOICES = tuple(u | (b << 8) for b in BLOCKS for u in UNITS)
+
+
+def describe(tile: int) -> dict:
+    """The two axes of a tile_units value."""
+    return {"units": tile & 0xFF, "blocks_per_sm": (tile >> 8) & 0xFF}
 _lock = threading.Lock()
 
 
@@ -79,8 +91,9 @@ def time_units(op: str, src, src_off, dst, dst_off, alphabets, alph_id, units: i
 
 def best_units(op: str, src, src_off, dst, dst_off, alphabets, alph_id=None,
                path: str | None = None, retune: bool = False) -> tuple[int, dict]:
-    """The tile size for this batch: from the cache, else measured and stored.
-    Returns (units, {units: ms} measured now, or {} on a cache hit)."""
+    """The tile shape for this batch: from the cache, else measured and
+    stored. Returns (tile_units, {tile_units: ms} measured now, or {} on a
+    cache hit)."""
     path = path or cache_path()
     n = src_off.numel() - 1
     total = int(src_off[-1].item() - src_off[0].item())
@@ -88,13 +101,14 @@ def best_units(op: str, src, src_off, dst, dst_off, alphabets, alph_id=None,
     with _lock:
         table = _load(path)
         if not retune and k in table:
-            return int(table[k]["units"]), {}
+            return int(table[k]["tile_units"]), {}
     ws = b64.batch_workspace(n, src.device)
     timings = {u: time_units(op, src, src_off, dst, dst_off, alphabets, alph_id, u, ws)
-               for u in UNITS}
+               for u in CHOICES}
     best = min(timings, key=timings.get)
     with _lock:
         table = _load(path)
-        table[k] = {"units": best, "ms": timings}
+        table[k] = {"tile_units": best, **describe(best),
+                    "ms": {str(u): t for u, t in timings.items()}}
         _store(path, table)
     return best, timings

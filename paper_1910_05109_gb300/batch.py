@@ -3,7 +3,9 @@ recorded once as a CUDA graph and replayed. The tile size is the caller's
 (`tile_units`, 4 by default; `autotune.best_units` picks one for a batch).
 
 A BatchCodec is built for one batch shape (string count, total bytes, output
-capacity). `run(src, src_off, alph_id)` copies nothing itself: the caller's
+capacity). With align16 its output offsets give every string a 16-byte aligned
+start (b64_batch_offsets' B64_OFFSETS_ALIGN16), which the kernels store
+straight from registers. `run(src, src_off, alph_id)` copies nothing itself: the caller's
 device tensors are copied into the codec's resident input buffers (one
 device-to-device copy each, captured in the graph too), so every replay reads
 the same addresses.
@@ -17,7 +19,8 @@ from . import binding as b64
 
 class BatchCodec:
     def __init__(self, op: str, n: int, src_bytes: int, alphabets, device=None,
-                 tile_units: int | None = None, use_graph: bool = True, stream=None):
+                 tile_units: int | None = None, use_graph: bool = True, stream=None,
+                 align16: bool = False):
         if op not in ("encode", "decode"):
             raise ValueError("op must be 'encode' or 'decode'")
         self.op, self.n = op, n
@@ -34,6 +37,7 @@ class BatchCodec:
         self.dst = None
         self.tile_units = tile_units or 4
         self.use_graph = use_graph
+        self.align16 = align16  # output offsets with 16-byte aligned string starts
         self.graph = None
 
     def _enqueue(self):
@@ -52,7 +56,8 @@ class BatchCodec:
             else:
                 self.alph_id[:self.n].zero_()    # every string takes alphabet 0
             off = b64.batch_offsets(self.src_off, self.alphabets, self.alph_id[:self.n],
-                                    decode=self.op == "decode", stream=self.stream)
+                                    decode=self.op == "decode", stream=self.stream,
+                                    align16=self.align16)
             self.dst_off.copy_(off, non_blocking=True)
         self.stream.synchronize()
         b64.check_batch_totals(self.src, int(self.src_off[-1]))

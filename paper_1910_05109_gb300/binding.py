@@ -271,16 +271,22 @@ def batch_workspace(n: int, device=None) -> torch.Tensor:
     return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device or "cuda")
 
 
+OFFSETS_DECODE = 1
+OFFSETS_ALIGN16 = 2
+
+
 def batch_offsets(src_off: torch.Tensor, alphabets, alph_id: torch.Tensor | None,
-                  decode: bool, stream=None) -> torch.Tensor:
-    """Device int64[n+1]: exclusive scan of per-string output capacities."""
+                  decode: bool, stream=None, align16: bool = False) -> torch.Tensor:
+    """Device int64[n+1]: exclusive scan of per-string output capacities
+    (align16: each rounded up to 16 bytes, so outputs start 16-byte aligned)."""
     n = src_off.numel() - 1
     check_batch_counts(n, alph_id=alph_id)
     src_off = _dev(src_off, torch.int64, "src_off")
     arr, na = _alphabet_array(alphabets)
     out = torch.empty(n + 1, dtype=torch.int64, device=src_off.device)
     aid = 0 if alph_id is None else _dev(alph_id, torch.uint8, "alph_id").data_ptr()
-    rc = lib().b64_batch_offsets(src_off.data_ptr(), n, arr, na, aid, int(decode),
+    flags = (OFFSETS_DECODE if decode else 0) | (OFFSETS_ALIGN16 if align16 else 0)
+    rc = lib().b64_batch_offsets(src_off.data_ptr(), n, arr, na, aid, flags,
                                  out.data_ptr(), _stream_ptr(stream))
     if rc != B64_SUCCESS:
         raise B64Error(last_error())

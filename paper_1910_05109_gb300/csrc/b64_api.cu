@@ -273,9 +273,14 @@ static int batch_common(bool decode, const uint8_t* src, const int64_t* src_off,
     // src and dst may be NULL when every string is empty (nothing reads them).
     if (!src_off || !dst_off || !results || !workspace)
         return set_error(B64_ERR_INVALID_ARGUMENT, "%s: NULL pointer argument", fn);
-    if (tile_units == 0) tile_units = 4;
-    if (tile_units != 1 && tile_units != 2 && tile_units != 4 && tile_units != 8)
-        return set_error(B64_ERR_INVALID_ARGUMENT, "%s: tile_units must be 0, 1, 2, 4 or 8", fn);
+    int units = tile_units & 0xFF;
+    if (units == 0) units = 4;
+    if ((units != 1 && units != 2 && units != 4 && units != 8) || tile_units < 0 ||
+        tile_units > 0xFFFF)
+        return set_error(B64_ERR_INVALID_ARGUMENT,
+                         "%s: tile_units must be 0, 1, 2, 4 or 8, optionally OR-ed with "
+                         "(blocks per SM << 8)", fn);
+    tile_units = units | (tile_units & 0xFF00);
     if (workspace_bytes < batch_workspace_bytes(n))
         return set_error(B64_ERR_INVALID_ARGUMENT, "%s: workspace holds %zu bytes, %zu needed", fn,
                          workspace_bytes, batch_workspace_bytes(n));
@@ -305,15 +310,18 @@ int b64_decode_batch(const uint8_t* src, const int64_t* src_off, int64_t n, uint
 }
 
 int b64_batch_offsets(const int64_t* src_off, int64_t n, const b64_alphabet* const* alphabets,
-                      int n_alphabets, const uint8_t* alph_id, int decode, int64_t* dst_off,
+                      int n_alphabets, const uint8_t* alph_id, int flags, int64_t* dst_off,
                       void* stream) {
     if (n < 0 || !src_off || !dst_off)
         return set_error(B64_ERR_INVALID_ARGUMENT, "b64_batch_offsets: bad argument");
+    if (flags & ~(B64_OFFSETS_DECODE | B64_OFFSETS_ALIGN16))
+        return set_error(B64_ERR_INVALID_ARGUMENT, "b64_batch_offsets: unknown flags %d", flags);
     BatchTables tabs;
     const int rc = batch_tables("b64_batch_offsets", alphabets, n_alphabets, &tabs);
     if (rc != B64_SUCCESS) return rc;
-    const cudaError_t e = launch_batch_offsets(decode != 0, src_off, n, tabs, alph_id, dst_off,
-                                               static_cast<cudaStream_t>(stream));
+    const cudaError_t e =
+        launch_batch_offsets((flags & B64_OFFSETS_DECODE) != 0, (flags & B64_OFFSETS_ALIGN16) != 0,
+                             src_off, n, tabs, alph_id, dst_off, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess)
         return set_error(B64_ERR_CUDA, "b64_batch_offsets: %s", cudaGetErrorString(e));
     return B64_SUCCESS;

@@ -3,31 +3,42 @@
 // per string; batching itself is not in the paper).
 //
 // String i is src[src_off[i] .. src_off[i+1]) and goes to dst + dst_off[i],
-// with its own alphabet (one of up to kMaxAlphabets passed by value). Work is
-// cut into tiles of one warp each: 32 x U units of 12 input bytes (encode) or
-// 16 characters (decode), U chosen at launch (the autotuner's tile size).
+// with its own alphabet (one of up to kMaxAlphabets passed by value). A warp
+// codes a tile of 32 x U units of 12 input bytes (encode) or 16 characters
+// (decode) at a time, U chosen at launch (the autotuner's tile size).
 //
 // Launch sequence (all on one stream, so it can be recorded in a CUDA graph):
 //   1. encode: one thread per string writes the string's output length to
 //      results; decode: the per-string error words in the caller's workspace
 //      are set to "none" (a memset);
-//   2. tile kernel (persistent): the concatenated input is split into equal
-//      byte ranges, one per warp. A warp finds the strings that hold its
-//      range ends with a 32-way search over src_off and moves both ends up to
-//      the next 3-byte (encode) or 4-character (decode) group boundary of
-//      their string, so neighbouring warps meet without talking to each other
-//      and no per-string scan is needed. It then walks its range string by
-//      string in tiles of at most 32 x U units. A tile is brought into the
-//      warp's shared memory by a bulk (TMA) copy of its 16-byte aligned span
-//      (the next tile's copy is started before the current one is coded), or
-//      staged with aligned loads where the span would leave the source
-//      buffer, re-aligned with funnel shifts, coded with the same per-unit
-//      steps as the single-buffer kernels, and copied out with aligned 16-byte
-//      stores and byte stores at the edges. Decode tiles fold bad-byte offsets
-//      into the string's error word with an atomic minimum;
+//   2. tile kernel (persistent, 8-warp blocks): the concatenated
+//      input is split into equal byte ranges, one per warp. A warp finds the
+//      strings that hold its range ends with a 32-way search over src_off and
+//      moves both ends up to the next 3-byte (encode) or 4-character (decode)
+//      group boundary of their string, so neighbouring warps meet without
+//      talking to each other and no per-string scan is needed. Within its
+//      range a string's part is cut into units of 12 bytes (encode) or 16
+//      characters (decode), the last one possibly shorter. The warp walks its
+//      range in tiles of TB consecutive unit start positions; a tile's bytes
+//      come into the warp's shared-memory ring by one bulk (TMA) copy, the
+//      next tiles' copies started before the current one is coded (or aligned
+//      loads where the span would leave the source buffer). The strings are
+//      known from a window of 32 strings' metadata (their units counted by a
+//      warp scan). A tile's units of one string (a piece) are coded in rounds
+//      of 32, one a lane, with uniform addressing (a round never mixes
+//      strings; a whole tile of full units of one string runs as one unrolled
+//      block), the string's last unit finished by its lane with the padding
+//      rules. A string whose output is aligned for a unit's stores (16 bytes
+//      encode, 4 decode; b64_batch_offsets' B64_OFFSETS_ALIGN16 layout gives
+//      every string that) is stored straight from registers; any other
+//      string's output is appended to a pending run in shared memory, written
+//      out with aligned 16-byte stores once the run breaks, fills, or ends
+//      past a string's last unit. Decode rounds fold bad-byte offsets into
+//      the string's error word with an atomic minimum;
 //   3. decode only: one thread per string applies the padding and length
 //      rules to the string's last 2..5 characters and writes its result.
 #include <mutex>
+#include <type_traits>
 
 #include "b64_internal.h"
 #include "b64_smem.cuh"
@@ -37,28 +48,29 @@ namespace {
 
 
 #ifndef B64_BATCH_STAGES
-#define B64_BATCH_STAGES 2
+#define B64_BATCH_STAGES 3
 #endif
 
-// The tile kernels' shape for U units a lane: 8 warps a block (4 for U = 8,
-// measured faster there), each with a ring of kStages input staging buffers
-// (kStages - 1 tiles in flight while one is coded) and one output buffer, in
-// dynamic shared memory. Two stages: three and four measured no faster (the
-// kernels are bound by instruction issue, not by the latency of the copies)
-// and cost resident blocks. The encoder keeps the 64-entry table: the
-// character-pair table of the single-buffer encoder measured slower here
-// (its 8 KiB a block cost resident blocks).
+// The tile kernels' shape for tiles of 32 x U units: 8 warps a block, as many
+// blocks an SM as fit (three for U <= 4); each warp has a ring of kStages staging buffers
+// (kStages - 1 tiles in flight while one is coded) and a buffer for its
+// pending output run, in dynamic shared memory. A staging buffer holds a
+// tile's span: up to TB + G - 1 bytes, 15 more on each side for 16-byte
+// alignment, and slack for a unit's word reads past its last byte.
 template <int U, bool kDecode>
 struct TileShape {
-    static constexpr int kWarps = U >= 8 ? 4 : 8;
+    static constexpr int kWarps = 8;
+    static constexpr int kMinBlocks = U >= 8 ? 1 : 3;  // blocks an SM the registers allow
     static constexpr int kThreads = 32 * kWarps;
     static constexpr int kStages = B64_BATCH_STAGES;
-    static constexpr uint32_t T = kDecode ? 32 * U * 16 : 32 * U * 12;  // input per tile
-    static constexpr uint32_t TO = kDecode ? T / 4 * 3 : T / 3 * 4 + 4;  // output (+ padding)
-    static constexpr uint32_t SIN = T + 32;                    // room for a ragged start
-    static constexpr uint32_t SOUT = (TO + 16 + 15) & ~15u;     // rows stay 16-byte aligned
+    static constexpr uint32_t G = kDecode ? 16 : 12;        // input bytes of a full unit
+    static constexpr uint32_t O = kDecode ? 12 : 16;        // output bytes of a full unit
+    static constexpr uint32_t TB = 32 * U * G;              // unit start positions per tile
+    static constexpr uint32_t SIN = (TB + G + 48 + 15) & ~15u;
+    static constexpr uint32_t RUN = 32 * U * O;             // pending-run capacity
+    static constexpr uint32_t SOUT = RUN + 32;              // + the copy-out's read slack
     static constexpr size_t kSmem = size_t(kWarps) * (size_t(kStages) * SIN + SOUT);
-    static_assert(SIN % 16 == 0 && kStages >= 2 && kStages <= 32, "staging ring");
+    static_assert(SIN % 16 == 0 && RUN % 16 == 0 && kStages >= 2 && kStages <= 8, "shape");
 };
 
 __host__ __device__ __forceinline__ uint64_t dec_body_length(uint64_t m) {
@@ -166,10 +178,12 @@ __device__ __forceinline__ int64_t warp_find_string(const int64_t* __restrict__ 
 }
 
 // Where a warp's range boundary at byte x (src_off coordinates) really falls:
-// rounded up to the next group boundary (3 bytes for encode, 4 characters for
-// decode) of the string that holds x, but not past the end of the string's
-// coded part (its end; for decode, its body). Every warp rounds the same way,
-// so neighbouring ranges meet exactly.
+// rounded up to the next unit boundary (12 bytes for encode, 16 characters
+// for decode, counted from the start of the string that holds x), but not
+// past the end of the string's coded part (its end; for decode, its body).
+// Every warp rounds the same way, so neighbouring ranges meet exactly, and a
+// segment's output starts a multiple of 16 (encode) or 12 (decode) bytes
+// into its string's output.
 template <bool kDecode>
 __device__ __forceinline__ int64_t round_boundary(const int64_t* __restrict__ src_off, int64_t n,
                                                   int64_t x, int lane) {
@@ -178,134 +192,121 @@ __device__ __forceinline__ int64_t round_boundary(const int64_t* __restrict__ sr
     const int64_t s0 = src_off[s];
     const int64_t len = src_off[s + 1] - s0;
     const int64_t lim = kDecode ? int64_t(dec_body_length(uint64_t(len))) : len;
-    constexpr int64_t g = kDecode ? 4 : 3;
+    constexpr int64_t g = kDecode ? 16 : 12;  // whole units: a unit never spans two warps
     const int64_t r = (x - s0 + g - 1) / g * g;
     return s0 + (r < lim ? r : lim);
 }
 
-// The per-string metadata of strings [w0, w0 + 32), one string per lane
-// (loaded with one coalesced round, read back by shuffles).
-struct Window {
-    int64_t w0 = INT64_MIN / 2;     // no string loaded yet
-    int64_t lo = 0, hi = 0, d = 0;  // src_off[i], src_off[i + 1], dst_off[i]
-    uint32_t id = 0;                // alphabet of string i
-    __device__ __forceinline__ void load(int64_t s, const int64_t* __restrict__ src_off,
-                                         const int64_t* __restrict__ dst_off,
-                                         const uint8_t* __restrict__ alph_id, int64_t n,
-                                         int lane) {
-        w0 = s;
-        const int64_t i = s + lane;
-        lo = i < n ? src_off[i] : 0;
-        hi = i < n ? src_off[i + 1] : 0;
-        d = i < n ? dst_off[i] : 0;
-        id = (i < n && alph_id) ? uint32_t(alph_id[i] & (kMaxAlphabets - 1)) : 0u;
-    }
+// ------------------------------------------------------------------ string window
+// The metadata of 32 consecutive strings w0 .. w0 + 31, one string a lane,
+// as their parts in the warp's range [P0, end): the segment [seg_lo, seg_hi)
+// of string i is its coded part (encode: all of it; decode: all but its last
+// 2..5 characters) clipped to the range. Each segment is cut into units of G
+// bytes (the last one possibly shorter); units are numbered through the
+// warp's range in order, so a segment's units are us .. us + un - 1.
+// Positions are kept relative to P0 (a warp's range is far below 4 GiB). The
+// lane that holds a string keeps its counts in registers (for the ballots)
+// and writes the rest to the warp's record in shared memory, where every
+// lane reads the record of the string it works on.
+struct WinRec {
+    int64_t dst[32];  // where the segment's output starts (dst offset)
+    int64_t rel[32];  // segment start within its string (decode error offsets)
+    uint32_t lo[32];  // segment start, relative to P0
+    uint32_t us[32];  // first unit
+    uint32_t un[32];  // units
+    uint32_t fl[32];  // bytes of the last unit | alphabet << 8 | padded << 16
 };
 
-// One tile: bytes [a, b) of string s, with the string's metadata.
-struct Tile {
-    int64_t s = 0, a = 0, b = 0, s0 = 0, s1 = 0, d0 = 0;
+struct Win {
+    int64_t w0;       // first string of the window
+    int64_t next;     // where string w0 + 32 starts, relative to P0 (src_off[min(w0 + 32, n)])
+    uint32_t lo;      // this lane's string: segment start (relative to P0)
+    uint32_t us, un;  // this lane's string: first unit, units
+    uint32_t base;    // units of the warp's range before the window
+    uint32_t end_u;   // units up to the window's end
+};
+
+template <bool kDecode, uint32_t G>
+__device__ __forceinline__ void load_window(Win& w, WinRec& r, int64_t s, uint32_t base,
+                                            const int64_t* __restrict__ src_off,
+                                            const int64_t* __restrict__ dst_off,
+                                            const uint8_t* __restrict__ alph_id,
+                                            const BatchTables& tabs, int64_t n, int64_t P0,
+                                            int64_t end, int lane) {
+    __syncwarp();  // every lane is done with the previous window's records
+    const int64_t i = s + lane;
+    const bool valid = i < n;
+    int64_t lo = 0, hi = 0, d = 0;
     uint32_t id = 0;
-};
+    if (valid) {
+        lo = src_off[i];
+        hi = src_off[i + 1];
+        d = dst_off[i];
+        id = alph_id ? uint32_t(alph_id[i] & (kMaxAlphabets - 1)) : 0u;
+    }
+    const int64_t lim = lo + (kDecode ? int64_t(dec_body_length(uint64_t(hi - lo))) : hi - lo);
+    const int64_t sl = lo > P0 ? lo : P0;
+    const int64_t sh = lim < end ? lim : end;
+    const uint32_t nb = (valid && sh > sl) ? uint32_t(sh - sl) : 0u;
+    const uint32_t un = (nb + G - 1) / G;
+    uint32_t incl = un;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    w.w0 = s;
+    w.base = base;
+    w.us = base + incl - un;
+    w.un = un;
+    w.lo = uint32_t(sl - P0);
+    w.end_u = base + __shfl_sync(0xffffffffu, incl, 31);
+    w.next = src_off[s + 32 < n ? s + 32 : n] - P0;
+    r.lo[lane] = w.lo;
+    r.dst[lane] = d + (kDecode ? (sl - lo) / 4 * 3 : (sl - lo) / 3 * 4);
+    r.rel[lane] = sl - lo;
+    r.us[lane] = w.us;
+    r.un[lane] = un;
+    const uint32_t nbl = un ? nb - (un - 1) * G : 0u;
+    r.fl[lane] = nbl | (id << 8) | (tabs.padded[id] ? 1u << 16 : 0u);
+    __syncwarp();
+}
 
-// The warp's walk over its range [pos, end): strings in order, tiles of at
-// most T bytes, each starting on a group boundary of its string.
-// Warp-collective (every lane holds the same state).
-template <bool kDecode>
-struct Cursor {
-    int64_t s, pos, end;
-    Window win;
-    __device__ __forceinline__ bool next(const int64_t* __restrict__ src_off,
-                                         const int64_t* __restrict__ dst_off,
-                                         const uint8_t* __restrict__ alph_id, int64_t n, int64_t T,
-                                         int lane, Tile* t) {
-        for (;;) {
-            if (pos >= end || s >= n) return false;
-            if (s < win.w0 || s >= win.w0 + 32) win.load(s, src_off, dst_off, alph_id, n, lane);
-            const int k = int(s - win.w0);
-            const int64_t s0 = __shfl_sync(0xffffffffu, win.lo, k);
-            const int64_t s1 = __shfl_sync(0xffffffffu, win.hi, k);
-            const int64_t len = s1 - s0;
-            const int64_t lim = s0 + (kDecode ? int64_t(dec_body_length(uint64_t(len))) : len);
-            if (pos < s0) pos = s0;
-            if (pos >= end) return false;
-            if (pos >= lim) {  // string done (or empty): on to the next one
-                ++s;
-                continue;
-            }
-            int64_t b = pos + T;
-            if (b > lim) b = lim;
-            if (b > end) b = end;
-            t->s = s;
-            t->a = pos;
-            t->b = b;
-            t->s0 = s0;
-            t->s1 = s1;
-            t->d0 = __shfl_sync(0xffffffffu, win.d, k);
-            t->id = __shfl_sync(0xffffffffu, win.id, k);
-            pos = b;
-            return true;
-        }
+// Units of the window whose start lies below position q (relative to P0).
+template <uint32_t G>
+__device__ __forceinline__ uint32_t units_below(const Win& w, uint32_t q) {
+    uint32_t c = 0;
+    if (w.un > 0 && q > w.lo) {
+        const uint32_t u = (q - w.lo + G - 1) / G;
+        c = u < w.un ? u : w.un;
     }
-};
+    return w.base + __reduce_add_sync(0xffffffffu, c);
+}
 
-// The warp's walk over its tiles with a ring of S staging buffers: the next
-// S - 1 tiles are described (by the warp-uniform cursor) and their bulk
-// copies started before the current one is coded; lane 0 keeps each tile's
-// description in the warp's ring in shared memory. process(t, sin) codes
-// one staged tile. Returns false if a bulk copy did not arrive in time.
-template <bool kDecode, int S, class Process>
-__device__ __forceinline__ bool walk_tiles(Cursor<kDecode>& cur, const uint8_t* __restrict__ src,
-                                           const int64_t* __restrict__ src_off,
-                                           const int64_t* __restrict__ dst_off,
-                                           const uint8_t* __restrict__ alph_id, int64_t n,
-                                           int64_t T, uint64_t src_end, uint8_t* sin_base,
-                                           uint32_t sin_stride, uint64_t* bars, Tile* ring,
-                                           uint32_t* ring_copy, int lane, Process process) {
-    bool more = true;
-    int64_t issued = 0;
-    auto issue = [&](int slot) {
-        Tile nt;
-        if (!cur.next(src_off, dst_off, alph_id, n, T, lane, &nt)) return false;
-        if (lane == 0) {
-            ring_copy[slot] = issue_tile_load(sin_base + size_t(slot) * sin_stride, src,
-                                              uint64_t(nt.a), uint64_t(nt.b), src_end, &bars[slot]);
-            ring[slot] = nt;
-        }
-        return true;
-    };
-    for (int k = 0; k < S - 1 && more; ++k) {
-        more = issue(k);
-        issued += more;
+// Bytes b .. 3 of word w cleared (b <= 0: all of them).
+__device__ __forceinline__ uint32_t keep_bytes(uint32_t w, int b) {
+    return b >= 4 ? w : (b <= 0 ? 0u : (w & ((1u << (8 * b)) - 1u)));
+}
+
+// A string's last unit when it is shorter than a whole one: nb (1..11)
+// bytes in x (bytes past them read as zero, Sec. 2: a partial final group is
+// completed with zero bits), coded with the string's padding rule. Returns
+// the characters; *nout = their count.
+__device__ __forceinline__ uint4 encode_last_unit(uint4 x, uint32_t nb, bool padded,
+                                                  const uint8_t* lut, uint32_t* nout) {
+    uint4 ch = encode12(keep_bytes(x.x, int(nb)), keep_bytes(x.y, int(nb) - 4),
+                        keep_bytes(x.z, int(nb) - 8), lut);
+    const uint32_t t3 = nb / 3, r = nb - 3 * t3;
+    *nout = 4 * t3 + (r == 0 ? 0u : padded ? 4u : r + 1);
+    if (r && padded) {  // '=' after the last group's characters
+        const uint32_t m = r == 1 ? 0x0000FFFFu : 0x00FFFFFFu;
+        const uint32_t pad = r == 1 ? 0x3D3D0000u : 0x3D000000u;
+        if (t3 == 0) ch.x = (ch.x & m) | pad;
+        else if (t3 == 1) ch.y = (ch.y & m) | pad;
+        else if (t3 == 2) ch.z = (ch.z & m) | pad;
+        else ch.w = (ch.w & m) | pad;
     }
-    uint32_t phases = 0;
-    for (int64_t it = 0; it < issued; ++it) {
-        const int k = int(it % S);
-        fence_proxy_async_smem();  // this lane's reads of tile it - 1 before the copy below
-        __syncwarp();              // every lane is done with tile it - 1's buffer and ring slot
-        if (more) {
-            more = issue(int((it + S - 1) % S));
-            issued += more;
-        }
-        __syncwarp();              // ring writes of lane 0 are visible
-        const Tile t = ring[k];
-        const bool by_copy = ring_copy[k] != 0;
-        uint8_t* sin = sin_base + size_t(k) * sin_stride;
-        if (!tile_ready(by_copy, sin, &bars[k], phases, k, src, uint64_t(t.a), uint64_t(t.b),
-                        src_end, lane)) {
-            // let this copy and the later ones in flight land (bounded) before
-            // the block can exit; this tile's wait already flipped its parity
-            if (lane == 0)
-                for (int64_t i = it; i < issued; ++i) {
-                    const int kk = int(i % S);
-                    if (ring_copy[kk])
-                        mbar_wait(&bars[kk], ((phases >> kk) & 1u) ^ (i == it ? 1u : 0u));
-                }
-            return false;
-        }
-        process(t, sin);
-    }
-    return true;
+    return ch;
 }
 
 // Each string's encoded length (encode results), one thread per string.
@@ -319,206 +320,314 @@ __global__ void encode_results_kernel(const int64_t* __restrict__ src_off, int64
     results[i] = int64_t(enc_length(uint64_t(src_off[i + 1] - src_off[i]), tabs.padded[a]));
 }
 
-// ------------------------------------------------------------------ encode tiles
-template <int U>
-__global__ void __launch_bounds__(TileShape<U, false>::kThreads)
-    encode_batch_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
-                        int64_t n, uint8_t* __restrict__ dst, const int64_t* __restrict__ dst_off,
-                        const __grid_constant__ BatchTables tabs,
-                        const uint8_t* __restrict__ alph_id) {
-    using Sh = TileShape<U, false>;
-    constexpr int kWarps = Sh::kWarps, kThreads = Sh::kThreads, S = Sh::kStages;
-    constexpr uint32_t T = Sh::T, SIN = Sh::SIN, SOUT = Sh::SOUT;
-    extern __shared__ __align__(16) uint8_t smem[];  // [warp][stage] inputs, then [warp] outputs
-    __shared__ __align__(16) uint8_t luts[kMaxAlphabets][64];
-    __shared__ uint64_t bars[kWarps][S];
-    __shared__ Tile ring[kWarps][S];
-    __shared__ uint32_t ring_copy[kWarps][S];
+// A flag that is a run-time bool in one copy of a loop and a compile-time
+// constant (std::true_type / std::false_type) in others.
+__device__ __forceinline__ bool flag_value(bool b) { return b; }
+template <bool B>
+__device__ __forceinline__ constexpr bool flag_value(std::integral_constant<bool, B>) { return B; }
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < kMaxAlphabets * 16; i += kThreads)
-        reinterpret_cast<uint32_t*>(luts)[i] = tabs.enc[i / 16].w[i % 16];
-    if (lane == 0) {
-        for (int k = 0; k < S; ++k) mbar_init(&bars[warp][k], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    uint8_t* sin_base = smem + size_t(warp) * S * SIN;
-    uint8_t* sout = smem + size_t(kWarps) * S * SIN + size_t(warp) * SOUT;
-
-    const int64_t origin = src_off[0], bytes = src_off[n] - origin;
-    const int64_t GW = int64_t(gridDim.x) * kWarps;
-    const int64_t gw = int64_t(blockIdx.x) * kWarps + warp;
-    if (bytes <= 0) return;
-    const int64_t x0 = origin + bytes * gw / GW, x1 = origin + bytes * (gw + 1) / GW;
-    Cursor<false> cur{0, round_boundary<false>(src_off, n, x0, lane),
-                      gw + 1 == GW ? src_off[n] : round_boundary<false>(src_off, n, x1, lane)};
-    if (cur.pos >= cur.end) return;
-    cur.s = cur.pos < src_off[n] ? warp_find_string(src_off, n, cur.pos, lane) : n;
-    const uint64_t src_end = uint64_t(src_off[n]);
-
-    auto process = [&](const Tile& t, const uint8_t* sin) {
-        const uint64_t a = uint64_t(t.a), b = uint64_t(t.b);
-        const bool last = t.b == t.s1;
-        const int ai = int(t.id);
-        const uint8_t* lut = luts[ai];
-        const uint32_t nbytes = uint32_t(b - a);
-        const uint32_t triples = nbytes / 3;
-        const uint32_t delta = uint32_t((reinterpret_cast<uintptr_t>(src + a)) & 15);
-        const uint32_t sh = delta & 3;
-        if (nbytes == T) {  // a whole tile: every unit is whole, no tests
+// Writes bytes 0 .. n-1 (n <= 16) of v (little-endian words) to q, which is
+// 4-byte aligned: whole words, then a 16-bit and an 8-bit store for the rest.
+__device__ __forceinline__ void store_head_aligned(uint8_t* q, uint4 v, uint32_t n) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t j = lane + 32 * u;
-                const uint4 x = load16_shifted(sin, delta + 12 * j, sh);
-                reinterpret_cast<uint4*>(sout)[j] = encode12(x.x, x.y, x.z, lut);
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t j = lane + 32 * u;
-                if (4 * j + 4 <= triples) {
-                    const uint4 x = load16_shifted(sin, delta + 12 * j, sh);
-                    reinterpret_cast<uint4*>(sout)[j] = encode12(x.x, x.y, x.z, lut);
-                } else if (4 * j < triples) {
-                    for (uint32_t q = 4 * j; q < triples; ++q) {
-                        const uint32_t p = delta + 3 * q;
-                        const uint32_t s1b = sin[p], s2b = sin[p + 1], s3b = sin[p + 2];
-                        reinterpret_cast<uint32_t*>(sout)[q] =
-                            encode_gathered(s2b | (s1b << 8) | (s3b << 16) | (s2b << 24), lut);
-                    }
-                }
-            }
+    for (uint32_t k = 0; k < 4; ++k) {
+        if (4 * k + 4 <= n) {
+            reinterpret_cast<uint32_t*>(q)[k] = w[k];
+        } else if (4 * k < n) {
+            const uint32_t r = n - 4 * k;  // 1..3
+            if (r >= 2) *reinterpret_cast<uint16_t*>(q + 4 * k) = uint16_t(w[k]);
+            if (r & 1u) q[4 * k + (r & 2u)] = uint8_t(w[k] >> (8 * (r & 2u)));
         }
-        uint32_t nout = 4 * triples;
-        const uint32_t r = nbytes - 3 * triples;  // only the string's last tile has r != 0
-        if (last && r) {
-            if (lane == 0) {
-                const uint32_t p = delta + 3 * triples;
-                const uint32_t s1b = sin[p], s2b = r == 2 ? sin[p + 1] : 0u;
-                const uint32_t g = s2b | (s1b << 8) | (s2b << 24);
-                sout[nout] = lut[(g >> 10) & 63u];
-                sout[nout + 1] = lut[(g >> 4) & 63u];
-                if (r == 2) sout[nout + 2] = lut[(g >> 22) & 63u];
-                if (tabs.padded[ai]) {
-                    sout[nout + 3] = '=';
-                    if (r == 1) sout[nout + 2] = '=';
-                }
-            }
-            nout += tabs.padded[ai] ? 4 : r + 1;
-        }
-        __syncwarp();
-        const uint64_t rel = a - uint64_t(t.s0);  // a multiple of 3
-        warp_stage_out(dst + t.d0 + rel / 3 * 4, sout, nout, lane);
-        __syncwarp();  // sout is rewritten by the next tile
-    };
-    if (!walk_tiles<false, S>(cur, src, src_off, dst_off, alph_id, n, T, src_end, sin_base, SIN,
-                              bars[warp], ring[warp], ring_copy[warp], lane, process)) {
-        if (lane == 0) atomicOr(&g_fault, 1u);
     }
 }
 
-// ------------------------------------------------------------------ decode tiles
-template <int U>
-__global__ void __launch_bounds__(TileShape<U, true>::kThreads)
-    decode_batch_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
-                        int64_t n, uint8_t* __restrict__ dst, const int64_t* __restrict__ dst_off,
-                        const __grid_constant__ BatchTables tabs,
-                        const uint8_t* __restrict__ alph_id,
-                        unsigned long long* __restrict__ err) {
-    using Sh = TileShape<U, true>;
+// ------------------------------------------------------------------ tile kernels
+// One persistent kernel for both directions (see the file comment).
+template <int U, bool kDecode>
+__global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
+                                  TileShape<U, kDecode>::kMinBlocks)
+    batch_tile_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
+                      int64_t n, uint8_t* __restrict__ dst, const int64_t* __restrict__ dst_off,
+                      const __grid_constant__ BatchTables tabs,
+                      const uint8_t* __restrict__ alph_id, unsigned long long* __restrict__ err) {
+    using Sh = TileShape<U, kDecode>;
     constexpr int kWarps = Sh::kWarps, kThreads = Sh::kThreads, S = Sh::kStages;
-    constexpr uint32_t T = Sh::T, SIN = Sh::SIN, SOUT = Sh::SOUT;
-    extern __shared__ __align__(16) uint8_t smem[];  // [warp][stage] inputs, then [warp] outputs
-    __shared__ __align__(16) uint8_t luts[kMaxAlphabets][256];
+    constexpr uint32_t G = Sh::G, O = Sh::O, TB = Sh::TB, SIN = Sh::SIN, RUN = Sh::RUN,
+                       SOUT = Sh::SOUT;
+    constexpr uint32_t A = kDecode ? 4u : 16u;  // alignment a unit's output store needs
+    constexpr int LUT = kDecode ? 256 : 64;
+    extern __shared__ __align__(16) uint8_t smem[];  // [warp][stage] inputs, then [warp] runs
+    __shared__ __align__(16) uint8_t luts[kMaxAlphabets][LUT];
     __shared__ uint64_t bars[kWarps][S];
-    __shared__ Tile ring[kWarps][S];
-    __shared__ uint32_t ring_copy[kWarps][S];
+    __shared__ WinRec recs[kWarps];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < kMaxAlphabets * 64; i += kThreads)
-        reinterpret_cast<uint32_t*>(luts)[i] = tabs.dec[i / 64].w[i % 64];
+    for (int i = tid; i < kMaxAlphabets * LUT / 4; i += kThreads)
+        reinterpret_cast<uint32_t*>(luts)[i] =
+            kDecode ? tabs.dec[i / 64].w[i % 64] : tabs.enc[i / 16].w[i % 16];
     if (lane == 0) {
         for (int k = 0; k < S; ++k) mbar_init(&bars[warp][k], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    uint8_t* sin_base = smem + size_t(warp) * S * SIN;
-    uint8_t* sout = smem + size_t(kWarps) * S * SIN + size_t(warp) * SOUT;
+    uint8_t* const sin_base = smem + size_t(warp) * S * SIN;
+    uint8_t* const sout = smem + size_t(kWarps) * S * SIN + size_t(warp) * SOUT;
+    WinRec& rec = recs[warp];
 
     const int64_t origin = src_off[0], bytes = src_off[n] - origin;
     const int64_t GW = int64_t(gridDim.x) * kWarps;
     const int64_t gw = int64_t(blockIdx.x) * kWarps + warp;
     if (bytes <= 0) return;
     const int64_t x0 = origin + bytes * gw / GW, x1 = origin + bytes * (gw + 1) / GW;
-    Cursor<true> cur{0, round_boundary<true>(src_off, n, x0, lane),
-                     gw + 1 == GW ? src_off[n] : round_boundary<true>(src_off, n, x1, lane)};
-    if (cur.pos >= cur.end) return;
-    cur.s = cur.pos < src_off[n] ? warp_find_string(src_off, n, cur.pos, lane) : n;
+    const int64_t P0 = round_boundary<kDecode>(src_off, n, x0, lane);
+    const int64_t end = gw + 1 == GW ? src_off[n] : round_boundary<kDecode>(src_off, n, x1, lane);
+    if (P0 >= end) return;
+    if (end - P0 > int64_t(0x7FFFFFFF)) {  // positions are kept in 32 bits
+        if (lane == 0) atomicOr(&g_fault, 2u);
+        return;
+    }
+    const uint32_t span = uint32_t(end - P0);
+    const uint32_t ntiles = (span + TB - 1) / TB;
     const uint64_t src_end = uint64_t(src_off[n]);
+    const uint8_t* const srcp = src + P0;  // positions below are relative to P0
 
-    auto process = [&](const Tile& t, const uint8_t* sin) {
-        const uint64_t a = uint64_t(t.a), b = uint64_t(t.b);
-        const uint8_t* lut = luts[t.id];
-        const uint32_t nchars = uint32_t(b - a);  // a multiple of 4
-        const uint32_t delta = uint32_t((reinterpret_cast<uintptr_t>(src + a)) & 15);
-        uint64_t first = kNoError;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint32_t j = lane + 32 * u;
-            if (16 * j + 16 <= nchars) {
-                const uint4 c = load16_shifted_u(sin, delta + 16 * j);
-                uint32_t e = 0;
-                const uint3 o = pack4x24(decode4(c.x, lut, e), decode4(c.y, lut, e),
-                                         decode4(c.z, lut, e), decode4(c.w, lut, e));
-                uint32_t* ow = reinterpret_cast<uint32_t*>(sout + 12 * j);
-                ow[0] = o.x;
-                ow[1] = o.y;
-                ow[2] = o.z;
-                if (e & kBad) {
-                    for (uint32_t i = 0; i < 16; ++i) {
-                        if (lut[sin[delta + 16 * j + i]] & kBad) {
-                            const uint64_t off = a - uint64_t(t.s0) + 16 * j + i;
-                            first = off < first ? off : first;
-                            break;
-                        }
-                    }
+    Win win;
+    load_window<kDecode, G>(win, rec, warp_find_string(src_off, n, P0, lane), 0u, src_off,
+                            dst_off, alph_id, tabs, n, P0, end, lane);
+
+    // Tile t holds the units that start in [t TB, min((t+1) TB, span)); their
+    // bytes end before min(q + G - 1, span). Lane 0 keeps a bit per ring
+    // stage: 1 if that stage's tile comes by bulk copy.
+    uint32_t copy_bits = 0, phases = 0;
+    auto issue = [&](uint32_t t) {
+        if (lane == 0) {
+            const int k = int(t % S);
+            const uint32_t p = t * TB, q = p + TB < span ? p + TB : span;
+            const uint32_t b = q + G - 1 < span ? q + G - 1 : span;
+            const bool c = issue_tile_load(sin_base + size_t(k) * SIN, src, uint64_t(P0) + p,
+                                           uint64_t(P0) + b, src_end, &bars[warp][k]);
+            copy_bits = (copy_bits & ~(1u << k)) | (c ? 1u << k : 0u);
+        }
+    };
+    for (uint32_t t = 0; t < S - 1 && t < ntiles; ++t) issue(t);
+
+    uint8_t* run_dst = nullptr;  // the pending run: sout[0 .. run_len) goes to run_dst
+    uint32_t run_len = 0;
+    auto flush = [&]() {
+        __syncwarp();
+        warp_stage_out(run_dst, sout, run_len, lane);
+        __syncwarp();
+        run_len = 0;
+    };
+    // makes the run end at d with room for `need` bytes and a store-aligned end
+    auto run_at = [&](uint8_t* d, uint32_t need) {
+        if (run_len && (run_dst + run_len != d || run_len % A != 0 || run_len + need > RUN))
+            flush();
+        if (run_len == 0) run_dst = d;
+    };
+
+    uint32_t R = 0;  // the next unit to code
+    for (uint32_t t = 0; t < ntiles; ++t) {
+        const int k = int(t % S);
+        fence_proxy_async_smem();  // this lane's reads of tile t - 1 before the copy below
+        __syncwarp();              // every lane is done with tile t - 1's buffer
+        if (t + S - 1 < ntiles) issue(t + S - 1);
+        const uint32_t p = t * TB, q = p + TB < span ? p + TB : span;
+        const uint32_t b = q + G - 1 < span ? q + G - 1 : span;
+        uint8_t* const sin = sin_base + size_t(k) * SIN;
+        const bool by_copy = ((__shfl_sync(0xffffffffu, copy_bits, 0) >> k) & 1u) != 0;
+        if (!tile_ready(by_copy, sin, &bars[warp][k], phases, k, src, uint64_t(P0) + p,
+                        uint64_t(P0) + b, src_end, lane)) {
+            // let the copies still in flight land (bounded) before the block can
+            // exit; this tile's wait already flipped its parity
+            if (lane == 0) {
+                for (uint32_t i = t; i < ntiles && i < t + S - 1; ++i) {
+                    const int kk = int(i % S);
+                    if ((copy_bits >> kk) & 1u)
+                        mbar_wait(&bars[warp][kk], ((phases >> kk) & 1u) ^ (i == t ? 1u : 0u));
                 }
-            } else if (16 * j < nchars) {
-                for (uint32_t q = 4 * j; q < nchars / 4; ++q) {
-                    const uint32_t p = delta + 4 * q;
-                    const uint32_t w = uint32_t(sin[p]) | (uint32_t(sin[p + 1]) << 8) |
-                                       (uint32_t(sin[p + 2]) << 16) | (uint32_t(sin[p + 3]) << 24);
-                    uint32_t e = 0;
-                    const uint32_t v = decode4(w, lut, e);
-                    sout[3 * q] = uint8_t(v >> 16);
-                    sout[3 * q + 1] = uint8_t(v >> 8);
-                    sout[3 * q + 2] = uint8_t(v);
-                    if (e & kBad) {
-                        for (uint32_t i = 0; i < 4; ++i) {
-                            if (lut[sin[p + i]] & kBad) {
-                                const uint64_t off = a - uint64_t(t.s0) + 4 * q + i;
-                                first = off < first ? off : first;
-                                break;
+                atomicOr(&g_fault, 1u);
+            }
+            return;
+        }
+        // the byte at position x sits at sin[x - p + delta]
+        const uint32_t delta = uint32_t(reinterpret_cast<uintptr_t>(srcp + p) & 15u);
+        for (;;) {
+            const uint32_t Rq = units_below<G>(win, q);
+            if (Rq - R == 32u * U) {
+                // ---- a whole tile of full units of one string: one record, U
+                //      rounds with uniform addressing and no per-round tests
+                const int k0 = 31 - __clz(__ballot_sync(0xffffffffu, win.un > 0 && win.us <= R));
+                const int kq =
+                    31 - __clz(__ballot_sync(0xffffffffu, win.un > 0 && win.us <= Rq - 1));
+                const uint32_t fl0 = rec.fl[k0], us0 = rec.us[k0];
+                const uint32_t full0 = rec.un[k0] - ((fl0 & 0xFFu) < G ? 1u : 0u);
+                if (k0 == kq && Rq - us0 <= full0) {
+                    const uint8_t* lut = luts[(fl0 >> 8) & 0xFFu];
+                    const uint32_t j0 = R - us0;
+                    const uint32_t o0 = rec.lo[k0] + G * j0 - p + delta;
+                    uint8_t* const d0 = dst + rec.dst[k0] + int64_t(O) * j0;
+                    // an aligned string output takes each unit's stores straight
+                    // from registers; any other goes through the run buffer
+                    const bool direct = (reinterpret_cast<uintptr_t>(d0) & (A - 1)) == 0;
+                    if (!direct) {
+                        if (run_len) flush();
+                        run_dst = d0;
+                    }
+                    // one copy of the loop for each store target (global memory or
+                    // the run buffer), so each keeps its own address space
+                    auto whole = [&](auto direct_tile) {
+                        const bool dd = flag_value(direct_tile);  // a constant in encode's copies
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const uint32_t i = 32 * u + lane;  // unit j0 + i
+                            const uint32_t o = o0 + G * i;
+                            if constexpr (kDecode) {
+                                const uint4 c = load16_shifted_u(sin, o);  // o mod 16 uniform
+                                uint32_t e = 0;
+                                const uint3 v =
+                                    pack4x24(decode4(c.x, lut, e), decode4(c.y, lut, e),
+                                             decode4(c.z, lut, e), decode4(c.w, lut, e));
+                                if (dd) {
+                                    uint32_t* ow = reinterpret_cast<uint32_t*>(d0 + 12 * i);
+                                    ow[0] = v.x;
+                                    ow[1] = v.y;
+                                    ow[2] = v.z;
+                                } else {
+                                    uint32_t* ow = reinterpret_cast<uint32_t*>(sout + 12 * i);
+                                    ow[0] = v.x;
+                                    ow[1] = v.y;
+                                    ow[2] = v.z;
+                                }
+                                if (e & kBad) {  // rare: the unit's first bad byte
+                                    for (uint32_t bb = 0; bb < 16; ++bb)
+                                        if (lut[sin[o + bb]] & kBad) {
+                                            atomicMin(&err[win.w0 + k0],
+                                                      (unsigned long long)(uint64_t(rec.rel[k0]) +
+                                                                           16ull * (j0 + i) + bb));
+                                            break;
+                                        }
+                                }
+                            } else {
+                                const uint4 x = load16_shifted(sin, o, o & 3u);  // o mod 4 uniform
+                                const uint4 ch = encode12(x.x, x.y, x.z, lut);
+                                if (dd) *reinterpret_cast<uint4*>(d0 + 16 * i) = ch;
+                                else *reinterpret_cast<uint4*>(sout + 16 * i) = ch;
                             }
                         }
-                    }
+                    };
+                    // encode: a copy of the loop for each store target; decode: one
+                    // copy with a uniform branch at its stores (smaller code measured
+                    // faster there)
+                    if constexpr (kDecode) whole(direct);
+                    else if (direct) whole(std::true_type{});
+                    else whole(std::false_type{});
+                    if (!direct) run_len = RUN;
+                    R = Rq;
                 }
             }
+            while (R < Rq) {
+                // ---- the units of one string in this tile (a piece), 32 a
+                //      round with uniform addressing; the string's last unit,
+                //      if shorter than G, is coded by its lane in the last round
+                const int ks = 31 - __clz(__ballot_sync(0xffffffffu, win.un > 0 && win.us <= R));
+                const uint32_t fl = rec.fl[ks], us = rec.us[ks], un = rec.un[ks];
+                const uint32_t nbl = fl & 0xFFu;
+                const bool padded = (fl & (1u << 16)) != 0;
+                const uint32_t pend = Rq < us + un ? Rq : us + un;
+                const uint8_t* lut = luts[(fl >> 8) & 0xFFu];
+                const uint32_t olo = rec.lo[ks] - p + delta;  // sin offset of the string's unit 0
+                uint8_t* const d_str = dst + rec.dst[ks];
+                const bool direct = (reinterpret_cast<uintptr_t>(d_str) & (A - 1)) == 0;
+                // output bytes of the string's last unit when it is shorter than G
+                const uint32_t out_last =
+                    kDecode ? nbl / 4 * 3
+                            : nbl / 3 * 4 + (nbl % 3 == 0 ? 0u : padded ? 4u : nbl % 3 + 1);
+                while (R < pend) {
+                    const uint32_t cnt = pend - R < 32u ? pend - R : 32u;
+                    const uint32_t j0 = R - us;
+                    const bool ends = R + cnt == us + un && nbl < G;  // holds the short unit
+                    if (!direct) run_at(d_str + int64_t(O) * j0, 32 * O);
+                    // one unit a lane; kPart: the round holds the string's short
+                    // last unit (in its last lane), a uniform choice
+                    auto code_round = [&](auto part_round, auto direct_round) {
+                        constexpr bool kPart = decltype(part_round)::value;
+                        const bool direct = flag_value(direct_round);  // a constant in encode's copies
+                        if (uint32_t(lane) >= cnt) return;
+                        const uint32_t jj = j0 + lane;
+                        const uint32_t o = olo + G * jj;
+                        const bool part = kPart && uint32_t(lane) + 1 == cnt;
+                        // global or run-buffer target: separate stores (uniform branch)
+                        uint8_t* const qg = d_str + int64_t(O) * jj;
+                        uint8_t* const qs = sout + run_len + O * lane;
+                        if constexpr (kDecode) {
+                            const uint4 c = load16_shifted_u(sin, o);  // o mod 16 uniform
+                            uint32_t e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+                            const uint3 v = pack4x24(decode4(c.x, lut, e0), decode4(c.y, lut, e1),
+                                                     decode4(c.z, lut, e2), decode4(c.w, lut, e3));
+                            const uint32_t nbu = part ? nbl : 16u;
+                            // groups past a short unit's end are not the string's
+                            const uint32_t e = kPart ? e0 | (nbu > 4 ? e1 : 0u) |
+                                                           (nbu > 8 ? e2 : 0u) | (nbu > 12 ? e3 : 0u)
+                                                     : e0 | e1 | e2 | e3;
+                            if (e & kBad) {  // rare: the unit's first bad byte
+                                for (uint32_t bb = 0; bb < nbu; ++bb)
+                                    if (lut[sin[o + bb]] & kBad) {
+                                        atomicMin(&err[win.w0 + ks],
+                                                  (unsigned long long)(uint64_t(rec.rel[ks]) +
+                                                                       16ull * jj + bb));
+                                        break;
+                                    }
+                            }
+                            if (kPart && direct && part) {
+                                store_head_aligned(qg, make_uint4(v.x, v.y, v.z, 0u), out_last);
+                            } else if (direct) {
+                                uint32_t* ow = reinterpret_cast<uint32_t*>(qg);
+                                ow[0] = v.x;
+                                ow[1] = v.y;
+                                ow[2] = v.z;
+                            } else {
+                                uint32_t* ow = reinterpret_cast<uint32_t*>(qs);
+                                ow[0] = v.x;
+                                ow[1] = v.y;
+                                ow[2] = v.z;
+                            }
+                        } else {
+                            const uint4 x = load16_shifted(sin, o, o & 3u);  // o mod 4 uniform
+                            if (kPart && part) {
+                                uint32_t nout;
+                                const uint4 ch = encode_last_unit(x, nbl, padded, lut, &nout);
+                                if (direct) store_head_aligned(qg, ch, nout);
+                                else *reinterpret_cast<uint4*>(qs) = ch;
+                            } else {
+                                const uint4 ch = encode12(x.x, x.y, x.z, lut);
+                                if (direct) *reinterpret_cast<uint4*>(qg) = ch;
+                                else *reinterpret_cast<uint4*>(qs) = ch;
+                            }
+                        }
+                    };
+                    if constexpr (kDecode) {
+                        if (ends) code_round(std::true_type{}, direct);
+                        else code_round(std::false_type{}, direct);
+                    } else if (direct) {
+                        if (ends) code_round(std::true_type{}, std::true_type{});
+                        else code_round(std::false_type{}, std::true_type{});
+                    } else {
+                        if (ends) code_round(std::true_type{}, std::false_type{});
+                        else code_round(std::false_type{}, std::false_type{});
+                    }
+                    if (!direct) run_len += ends ? O * (cnt - 1) + out_last : O * cnt;
+                    R += cnt;
+                }
+            }
+            // more units below q can only be in later strings
+            if (Rq < win.end_u || win.w0 + 32 >= n || win.next >= int64_t(q)) break;
+            load_window<kDecode, G>(win, rec, win.w0 + 32, win.end_u, src_off, dst_off, alph_id,
+                                    tabs, n, P0, end, lane);
         }
-        if (__any_sync(0xffffffffu, first != kNoError)) {  // rare: a bad byte in the tile
-            const uint64_t wmin = warp_min_u64(first);
-            if (lane == 0) atomicMin(&err[t.s], (unsigned long long)wmin);
-        }
-        __syncwarp();
-        const uint64_t rel = a - uint64_t(t.s0);  // a multiple of 4
-        warp_stage_out(dst + t.d0 + rel / 4 * 3, sout, nchars / 4 * 3, lane);
-        __syncwarp();  // sout is rewritten by the next tile
-    };
-    if (!walk_tiles<true, S>(cur, src, src_off, dst_off, alph_id, n, T, src_end, sin_base, SIN,
-                             bars[warp], ring[warp], ring_copy[warp], lane, process)) {
-        if (lane == 0) atomicOr(&g_fault, 1u);
     }
+    if (run_len) flush();
 }
 
 // One thread per string: padding and length rules on the string's tail, its
@@ -595,9 +704,10 @@ struct Occ {
 template <class K>
 int occupancy(K kernel, int threads, size_t smem, size_t max_smem, Occ& occ, cudaError_t* err) {
     std::call_once(occ.once, [&] {
-        if (max_smem > 48 * 1024)
-            occ.err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           int(max_smem));
+        // always opted in: the static shared memory counts against the
+        // default 48 KiB too
+        occ.err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(max_smem));
         int c = 1;
         if (occ.err == cudaSuccess &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, kernel, threads, smem) != cudaSuccess)
@@ -612,29 +722,19 @@ Occ g_enc_occ[4][64], g_dec_occ[4][64];
 
 int unit_slot(int units) { return units == 1 ? 0 : units == 2 ? 1 : units == 4 ? 2 : 3; }
 
-template <int U>
-cudaError_t launch_encode_tiles(const BatchArgs& a, const BatchTables& t, cudaStream_t st) {
-    using Sh = TileShape<U, false>;
+template <int U, bool kDecode>
+cudaError_t launch_tiles(const BatchArgs& a, const BatchTables& t, unsigned long long* err,
+                         int blocks_per_sm, cudaStream_t st) {
+    using Sh = TileShape<U, kDecode>;
     const DeviceInfo& di = device_info();
     cudaError_t e = cudaSuccess;
-    const int occ = occupancy(encode_batch_kernel<U>, Sh::kThreads, Sh::kSmem, Sh::kSmem,
-                              g_enc_occ[unit_slot(U)][di.device & 63], &e);
+    Occ& slot = (kDecode ? g_dec_occ : g_enc_occ)[unit_slot(U)][di.device & 63];
+    const int occ = occupancy(batch_tile_kernel<U, kDecode>, Sh::kThreads, Sh::kSmem, Sh::kSmem,
+                              slot, &e);
     if (e != cudaSuccess) return e;
-    encode_batch_kernel<U><<<unsigned(di.sm_count * occ), Sh::kThreads, Sh::kSmem, st>>>(
-        a.src, a.src_off, a.n, a.dst, a.dst_off, t, a.alph_id);
-    return cudaGetLastError();
-}
-
-template <int U>
-cudaError_t launch_decode_tiles(const BatchArgs& a, const BatchTables& t,
-                                unsigned long long* err, cudaStream_t st) {
-    using Sh = TileShape<U, true>;
-    const DeviceInfo& di = device_info();
-    cudaError_t e = cudaSuccess;
-    const int occ = occupancy(decode_batch_kernel<U>, Sh::kThreads, Sh::kSmem, Sh::kSmem,
-                              g_dec_occ[unit_slot(U)][di.device & 63], &e);
-    if (e != cudaSuccess) return e;
-    decode_batch_kernel<U><<<unsigned(di.sm_count * occ), Sh::kThreads, Sh::kSmem, st>>>(
+    // blocks_per_sm (the tuner's second axis): fewer resident warps than fit
+    const int bps = blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ;
+    batch_tile_kernel<U, kDecode><<<unsigned(di.sm_count * bps), Sh::kThreads, Sh::kSmem, st>>>(
         a.src, a.src_off, a.n, a.dst, a.dst_off, t, a.alph_id, err);
     return cudaGetLastError();
 }
@@ -661,21 +761,29 @@ constexpr int kScanItems = 8;
 constexpr int kOffThreads = 256;
 constexpr int64_t kOffItems = int64_t(kOffThreads) * kScanItems;  // strings per block
 
+// A string's output capacity: its encoded length, or 3 ceil(len / 4) for
+// decode; rounded up to a multiple of 16 bytes with align16.
 template <bool kDecode>
 __device__ __forceinline__ int64_t capacity(const int64_t* __restrict__ src_off, int64_t i,
                                             const BatchTables& tabs,
-                                            const uint8_t* __restrict__ alph_id) {
+                                            const uint8_t* __restrict__ alph_id, bool align16) {
     const uint64_t len = uint64_t(src_off[i + 1] - src_off[i]);
-    if (kDecode) return int64_t((len + 3) / 4 * 3);
-    const int al = alph_id ? (alph_id[i] & (kMaxAlphabets - 1)) : 0;
-    return int64_t(enc_length(len, tabs.padded[al]));
+    uint64_t c;
+    if (kDecode) {
+        c = (len + 3) / 4 * 3;
+    } else {
+        const int al = alph_id ? (alph_id[i] & (kMaxAlphabets - 1)) : 0;
+        c = enc_length(len, tabs.padded[al]);
+    }
+    return int64_t(align16 ? (c + 15) & ~uint64_t(15) : c);
 }
 
 template <bool kDecode>
 __global__ void __launch_bounds__(kOffThreads)
     offsets_local_kernel(const int64_t* __restrict__ src_off, int64_t n,
                          const __grid_constant__ BatchTables tabs,
-                         const uint8_t* __restrict__ alph_id, int64_t* __restrict__ dst_off) {
+                         const uint8_t* __restrict__ alph_id, int64_t* __restrict__ dst_off,
+                         bool align16) {
     __shared__ int64_t warp_sum[kOffThreads / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t first = int64_t(blockIdx.x) * kOffItems;
@@ -683,7 +791,7 @@ __global__ void __launch_bounds__(kOffThreads)
     int64_t cap[kScanItems], sum = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        cap[j] = i0 + j < n ? capacity<kDecode>(src_off, i0 + j, tabs, alph_id) : 0;
+        cap[j] = i0 + j < n ? capacity<kDecode>(src_off, i0 + j, tabs, alph_id, align16) : 0;
         sum += cap[j];
     }
     const int64_t incl = warp_inclusive_scan(sum, lane);
@@ -753,28 +861,29 @@ size_t batch_workspace_bytes(int64_t n) {
     return size_t(n) * sizeof(uint64_t);
 }
 
-cudaError_t launch_batch(bool decode, const BatchArgs& a, const BatchTables& tabs, int units,
+cudaError_t launch_batch(bool decode, const BatchArgs& a, const BatchTables& tabs, int tile,
                          void* workspace, cudaStream_t st) {
+    const int units = tile & 0xFF, bps = (tile >> 8) & 0xFF;
     if (!decode) {
         encode_results_kernel<<<unsigned((a.n + 255) / 256), 256, 0, st>>>(a.src_off, a.n, tabs,
                                                                            a.alph_id, a.results);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         switch (units) {
-            case 1: return launch_encode_tiles<1>(a, tabs, st);
-            case 2: return launch_encode_tiles<2>(a, tabs, st);
-            case 4: return launch_encode_tiles<4>(a, tabs, st);
-            default: return launch_encode_tiles<8>(a, tabs, st);
+            case 1: return launch_tiles<1, false>(a, tabs, nullptr, bps, st);
+            case 2: return launch_tiles<2, false>(a, tabs, nullptr, bps, st);
+            case 4: return launch_tiles<4, false>(a, tabs, nullptr, bps, st);
+            default: return launch_tiles<8, false>(a, tabs, nullptr, bps, st);
         }
     }
     unsigned long long* err = static_cast<unsigned long long*>(workspace);
     cudaError_t e = cudaMemsetAsync(err, 0xFF, size_t(a.n) * sizeof(uint64_t), st);  // kNoError
     if (e != cudaSuccess) return e;
     switch (units) {
-        case 1: e = launch_decode_tiles<1>(a, tabs, err, st); break;
-        case 2: e = launch_decode_tiles<2>(a, tabs, err, st); break;
-        case 4: e = launch_decode_tiles<4>(a, tabs, err, st); break;
-        default: e = launch_decode_tiles<8>(a, tabs, err, st); break;
+        case 1: e = launch_tiles<1, true>(a, tabs, err, bps, st); break;
+        case 2: e = launch_tiles<2, true>(a, tabs, err, bps, st); break;
+        case 4: e = launch_tiles<4, true>(a, tabs, err, bps, st); break;
+        default: e = launch_tiles<8, true>(a, tabs, err, bps, st); break;
     }
     if (e != cudaSuccess) return e;
     const unsigned grid = unsigned((a.n + 255) / 256);
@@ -787,17 +896,17 @@ cudaError_t launch_batch(bool decode, const BatchArgs& a, const BatchTables& tab
 
 namespace b64 {
 
-cudaError_t launch_batch_offsets(bool decode, const int64_t* src_off, int64_t n,
+cudaError_t launch_batch_offsets(bool decode, bool align16, const int64_t* src_off, int64_t n,
                                  const BatchTables& tabs, const uint8_t* alph_id,
                                  int64_t* dst_off, cudaStream_t st) {
     const unsigned nblk = unsigned((n + kOffItems - 1) / kOffItems);
     if (nblk) {
         if (decode)
             offsets_local_kernel<true><<<nblk, kOffThreads, 0, st>>>(src_off, n, tabs, alph_id,
-                                                                     dst_off);
+                                                                     dst_off, align16);
         else
             offsets_local_kernel<false><<<nblk, kOffThreads, 0, st>>>(src_off, n, tabs, alph_id,
-                                                                      dst_off);
+                                                                      dst_off, align16);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

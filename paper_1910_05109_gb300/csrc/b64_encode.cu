@@ -219,10 +219,11 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ __align__(16) uint8_t lut[64];
     if (threadIdx.x < 16) reinterpret_cast<uint32_t*>(lut)[threadIdx.x] = tab.w[threadIdx.x];
     __syncthreads();
+    // the tail first: nothing of it then stays live across the loop below
+    if (blockIdx.x == 0 && threadIdx.x == 0) encode_tail(src, n, dst, lut, padded);
     const bool al4 = (reinterpret_cast<uintptr_t>(dst) & 3u) == 0;
     encode_triples_plain(src, 0, n / 3, dst, lut, uint64_t(blockIdx.x) * blockDim.x + threadIdx.x,
                          uint64_t(gridDim.x) * blockDim.x, al4);
-    if (blockIdx.x == 0 && threadIdx.x == 0) encode_tail(src, n, dst, lut, padded);
 }
 
 struct KernelSetup {

@@ -80,12 +80,14 @@ uint32_t batch_fault_flag(bool clear);
 // (later slots repeat alphabet 0). Returns B64_SUCCESS or sets the error.
 int batch_tables(const char* fn, const b64_alphabet* const* alphabets, int n_alphabets,
                  BatchTables* t);
-// Enqueues prep + tile kernel (+ decode finalize). `units` in {1, 2, 4, 8}.
-cudaError_t launch_batch(bool decode, const BatchArgs& a, const BatchTables& tabs, int units,
+// Enqueues prep + tile kernel (+ decode finalize). `tile`: units a lane
+// (1, 2, 4 or 8) in bits 0..7; resident blocks an SM in bits 8..15 (0: as
+// many as fit).
+cudaError_t launch_batch(bool decode, const BatchArgs& a, const BatchTables& tabs, int tile,
                          void* workspace, cudaStream_t stream);
 // dst_off[0..n] = exclusive scan of per-string output capacities (encoded
-// length, or 3*ceil(m/4) for decode).
-cudaError_t launch_batch_offsets(bool decode, const int64_t* src_off, int64_t n,
+// length, or 3*ceil(m/4) for decode; each rounded up to 16 bytes with align16).
+cudaError_t launch_batch_offsets(bool decode, bool align16, const int64_t* src_off, int64_t n,
                                  const BatchTables& tabs, const uint8_t* alph_id,
                                  int64_t* dst_off, cudaStream_t stream);
 

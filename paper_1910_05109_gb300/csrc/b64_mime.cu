@@ -1230,7 +1230,7 @@ __device__ __forceinline__ bool issue_doc_segment(uint8_t* stage, const DocSeg& 
     return true;
 }
 
-__global__ void __launch_bounds__(32 * kDocWarps, 6)
+__global__ void __launch_bounds__(32 * kDocWarps, 5)
     mime_decode_docs_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
                             int64_t n, uint8_t* __restrict__ dst,
                             const int64_t* __restrict__ dst_off,

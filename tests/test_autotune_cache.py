@@ -1,6 +1,7 @@
-"""Host logic of the tile-size autotuner (no GPU): the fastest tile size is
-chosen and stored, a second call is served from the cache file, retune
-measures again, and a damaged cache file is treated as empty."""
+"""Host logic of the tile-shape autotuner (no GPU): every (units, blocks per
+SM) pair is timed, the fastest is chosen and stored with both axes, a second
+call is served from the cache file, retune measures again, and a damaged cache
+file is treated as empty."""
 import json
 
 import torch
@@ -13,7 +14,7 @@ def fake_env(monkeypatch, timings):
 
     def time_units(op, src, src_off, dst, dst_off, alphabets, alph_id, units, workspace, reps=5):
         calls.append(units)
-        return timings[units]
+        return timings(units & 0xFF, units >> 8)
 
     monkeypatch.setattr(autotune, "time_units", time_units)
     monkeypatch.setattr(autotune, "key", lambda op, n, total, device=None: f"gpu|{op}|{n}|{total}")
@@ -26,31 +27,39 @@ def args(n=8, each=100):
     return "encode", src, off, None, None, [None]
 
 
-def test_measures_then_caches(monkeypatch, tmp_path):
-    calls = fake_env(monkeypatch, {1: 0.9, 2: 0.5, 4: 0.3, 8: 0.4})
+def grid(best_u, best_b):
+    """A timing surface whose minimum is at (best_u, best_b)."""
+    return lambda u, b: 0.1 + abs(u - best_u) + 0.5 * abs(b - best_b)
+
+
+def test_searches_both_axes_then_caches(monkeypatch, tmp_path):
+    calls = fake_env(monkeypatch, grid(4, 2))
     path = str(tmp_path / "tune.json")
-    units, t = autotune.best_units(*args(), path=path)
-    assert units == 4 and sorted(t) == [1, 2, 4, 8] and calls == [1, 2, 4, 8]
-    stored = json.load(open(path))
-    assert stored["gpu|encode|8|800"]["units"] == 4
-    units, t = autotune.best_units(*args(), path=path)
-    assert units == 4 and t == {} and calls == [1, 2, 4, 8]  # cache hit: nothing timed
+    tile, t = autotune.best_units(*args(), path=path)
+    assert tile == 4 | (2 << 8) and autotune.describe(tile) == {"units": 4, "blocks_per_sm": 2}
+    assert sorted(t) == sorted(autotune.CHOICES) and len(calls) == 9
+    assert {c & 0xFF for c in calls} == {2, 4, 8} and {c >> 8 for c in calls} == {0, 1, 2}
+    stored = json.load(open(path))["gpu|encode|8|800"]
+    assert stored["tile_units"] == tile and stored["units"] == 4 and stored["blocks_per_sm"] == 2
+    assert len(stored["ms"]) == 9
+    tile2, t2 = autotune.best_units(*args(), path=path)
+    assert tile2 == tile and t2 == {} and len(calls) == 9  # cache hit: nothing timed
 
 
 def test_retune_and_other_keys(monkeypatch, tmp_path):
     path = str(tmp_path / "tune.json")
-    fake_env(monkeypatch, {1: 0.9, 2: 0.2, 4: 0.3, 8: 0.4})
+    fake_env(monkeypatch, grid(2, 0))
     assert autotune.best_units(*args(), path=path)[0] == 2
-    calls = fake_env(monkeypatch, {1: 0.1, 2: 0.2, 4: 0.3, 8: 0.4})
-    assert autotune.best_units(*args(), path=path)[0] == 2           # cached
-    assert autotune.best_units(*args(), path=path, retune=True)[0] == 1
-    assert autotune.best_units(*args(n=16), path=path)[0] == 1       # another batch size
-    assert len(json.load(open(path))) == 2 and len(calls) == 8
+    calls = fake_env(monkeypatch, grid(8, 1))
+    assert autotune.best_units(*args(), path=path)[0] == 2              # cached
+    assert autotune.best_units(*args(), path=path, retune=True)[0] == 8 | (1 << 8)
+    assert autotune.best_units(*args(n=16), path=path)[0] == 8 | (1 << 8)   # another batch size
+    assert len(json.load(open(path))) == 2 and len(calls) == 18
 
 
 def test_damaged_cache_file(monkeypatch, tmp_path):
     path = tmp_path / "tune.json"
     path.write_text("{not json")
-    fake_env(monkeypatch, {1: 0.4, 2: 0.3, 4: 0.2, 8: 0.1})
+    fake_env(monkeypatch, grid(8, 0))
     assert autotune.best_units(*args(), path=str(path))[0] == 8
-    assert json.load(open(path))["gpu|encode|8|800"]["units"] == 8
+    assert json.load(open(path))["gpu|encode|8|800"]["tile_units"] == 8

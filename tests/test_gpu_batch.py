@@ -52,7 +52,7 @@ def oracle_encode(orc, tables, data, off, alph_id, padded):
     return enc, eoff, res
 
 
-def gpu_encode(b64, tables, data, off, alph_id, units, src_shift=0):
+def gpu_encode(b64, tables, data, off, alph_id, units, src_shift=0, align16=False):
     dev = "cuda"
     buf = torch.empty(data.size + src_shift + 16, dtype=torch.uint8, device=dev)
     src = buf[src_shift:src_shift + data.size]
@@ -60,7 +60,7 @@ def gpu_encode(b64, tables, data, off, alph_id, units, src_shift=0):
         src.copy_(torch.from_numpy(data))
     d_off = torch.from_numpy(off).to(dev)
     d_aid = torch.from_numpy(alph_id).to(dev)
-    dst_off = b64.batch_offsets(d_off, tables[0], d_aid, decode=False)
+    dst_off = b64.batch_offsets(d_off, tables[0], d_aid, decode=False, align16=align16)
     total = int(dst_off[-1])
     dst = torch.full((total + 64,), 0xA5, dtype=torch.uint8, device=dev)
     res = b64.encode_batch(src, d_off, dst, dst_off, tables[0], d_aid, tile_units=units)
@@ -70,7 +70,7 @@ def gpu_encode(b64, tables, data, off, alph_id, units, src_shift=0):
     return host[:total], dst_off.cpu().numpy(), res.cpu().numpy()
 
 
-def gpu_decode(b64, tables, text, toff, alph_id, units, src_shift=0):
+def gpu_decode(b64, tables, text, toff, alph_id, units, src_shift=0, align16=False):
     dev = "cuda"
     buf = torch.empty(text.size + src_shift + 16, dtype=torch.uint8, device=dev)
     src = buf[src_shift:src_shift + text.size]
@@ -78,7 +78,7 @@ def gpu_decode(b64, tables, text, toff, alph_id, units, src_shift=0):
         src.copy_(torch.from_numpy(text))
     d_off = torch.from_numpy(toff).to(dev)
     d_aid = torch.from_numpy(alph_id).to(dev)
-    dst_off = b64.batch_offsets(d_off, tables[0], d_aid, decode=True)
+    dst_off = b64.batch_offsets(d_off, tables[0], d_aid, decode=True, align16=align16)
     total = int(dst_off[-1])
     dst = torch.full((total + 64,), 0xA5, dtype=torch.uint8, device=dev)
     res = b64.decode_batch(src, d_off, dst, dst_off, tables[0], d_aid, tile_units=units)
@@ -114,6 +114,36 @@ def test_batch_parity_all_tiles(b64, orc, tables, units):
     want_dec, want_res = orc.decode_batch(want, eoff, doff, tables[1], aid.astype(np.int32),
                                           padded, int(doff[-1]))
     assert np.array_equal(want_res, off[1:] - off[:-1])
+    check_decoded(dec, doff, dres, want_res, want_dec)
+
+
+@pytest.mark.parametrize("units", [1, 4])
+def test_batch_parity_aligned_offsets(b64, orc, tables, units):
+    """Output offsets with 16-byte aligned string starts (the kernels store
+    such outputs straight from registers): every string equals the oracle's,
+    the bytes between strings are untouched, and decode results and bytes
+    (aligned offsets too, with injected bad bytes) equal the oracle's."""
+    data, off, aid, padded = make_batch(orc, 1500, seed=40 + units, hi=1 << 17,
+                                        extra_lengths=EDGE_LENGTHS)
+    want, eoff, wres = oracle_encode(orc, tables, data, off, aid, padded)
+    got, goff, gres = gpu_encode(b64, tables, data, off, aid, units, src_shift=units % 3,
+                                 align16=True)
+    assert np.array_equal(gres, wres)
+    assert (goff % 16 == 0).all()
+    for i in range(off.size - 1):
+        a, m = int(goff[i]), int(wres[i])
+        assert np.array_equal(got[a:a + m], want[eoff[i]:eoff[i] + m]), i
+        assert (got[a + m:int(goff[i + 1])] == 0xA5).all(), i
+    text = want.copy()
+    g = wl.rng(44 + units)
+    for i in np.nonzero(g.random(off.size - 1) < 0.05)[0]:
+        if eoff[i + 1] > eoff[i]:
+            text[eoff[i] + int(g.integers(0, eoff[i + 1] - eoff[i]))] = 0xFF
+    dec, doff, dres = gpu_decode(b64, tables, text, eoff, aid, units, align16=True)
+    assert (doff % 16 == 0).all()
+    want_dec, want_res = orc.decode_batch(text, eoff, doff, tables[1], aid.astype(np.int32),
+                                          padded, int(doff[-1]))
+    assert (want_res < 0).sum() > 10
     check_decoded(dec, doff, dres, want_res, want_dec)
 
 
@@ -186,16 +216,27 @@ def test_batch_tiny_strings_and_offset_origin(b64, orc, tables):
         check_decoded(dec, doff, dres, want_res, want_dec)
 
 
-def test_batch_config3_full_size(b64, orc, tables):
+@pytest.mark.parametrize("align16", [False, True])
+def test_batch_config3_full_size(b64, orc, tables, align16):
     """100,000 strings, lognormal lengths (median 1 KiB, sigma 1.5, 1 B..1 MiB),
     all three residues mod 3, 50/50 standard-padded / url-unpadded, 1% of the
-    decode inputs with one injected bad byte: every string against the oracle."""
+    decode inputs with one injected bad byte: every string against the oracle,
+    with packed output offsets and with 16-byte aligned string starts (the
+    benchmark's layout)."""
     data, off, aid, padded = make_batch(orc, 100_000, seed=2)
     lens = off[1:] - off[:-1]
     assert set(np.unique(lens % 3)) == {0, 1, 2}
     want, eoff, wres = oracle_encode(orc, tables, data, off, aid, padded)
-    got, goff, gres = gpu_encode(b64, tables, data, off, aid, 4)
-    assert np.array_equal(gres, wres) and np.array_equal(got, want)
+    got, goff, gres = gpu_encode(b64, tables, data, off, aid, 4, align16=align16)
+    assert np.array_equal(gres, wres)
+    if align16:
+        keep = np.zeros(got.size, bool)
+        for i in range(off.size - 1):
+            keep[goff[i]:goff[i] + wres[i]] = True
+        assert np.array_equal(got[keep], want)
+        assert (got[~keep] == 0xA5).all()
+    else:
+        assert np.array_equal(got, want)
     text = want.copy()
     g = wl.rng(12)
     bad = np.nonzero(g.random(off.size - 1) < 0.01)[0]
@@ -203,7 +244,7 @@ def test_batch_config3_full_size(b64, orc, tables):
         m = int(eoff[i + 1] - eoff[i])
         p = int(g.integers(0, m))
         text[eoff[i] + p] = 0xFF
-    dec, doff, dres = gpu_decode(b64, tables, text, eoff, aid, 4)
+    dec, doff, dres = gpu_decode(b64, tables, text, eoff, aid, 4, align16=align16)
     want_dec, want_res = orc.decode_batch(text, eoff, doff, tables[1], aid.astype(np.int32),
                                           padded, int(doff[-1]))
     assert (want_res < 0).sum() == bad.size
@@ -265,12 +306,13 @@ def test_batch_codec_graph_and_autotune_cache(b64, orc, tables, tmp_path):
     path = str(tmp_path / "autotune.json")
     args = (codec.src, codec.src_off, codec.dst, codec.dst_off, tables[0], codec.alph_id[:n])
     units, timings = autotune.best_units("encode", *args, path=path)
-    assert units in autotune.UNITS and set(timings) == set(autotune.UNITS)
+    assert units in autotune.CHOICES and set(timings) == set(autotune.CHOICES)
     again, t2 = autotune.best_units("encode", *args, path=path)
     assert again == units and t2 == {}          # served from the cache file
     codec.tile_units = units
     for _ in range(3):                          # first call direct, then graph replays
-        codec.dst.zero_()
+        with torch.cuda.stream(codec.stream):
+            codec.dst.zero_()
         codec.run()
         codec.synchronize()
         assert np.array_equal(codec.dst[:total].cpu().numpy(), want)

@@ -751,6 +751,7 @@ def batch_workload(args) -> dict:
 
         per_string()
         torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
         e0.record(stream)
         per_string()

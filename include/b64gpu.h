@@ -218,7 +218,7 @@ int b64_mime_decode_batch(const uint8_t* src, const int64_t* src_off, int64_t n,
  * device int64, receiving what the single-buffer call returns for that string
  * (encode: output length; decode: length or -(offset+1), offset within the
  * string). tile_units: bytes per thread of a tile as 1, 2, 4 or 8 units of
- * 12 input bytes (encode) or 16 characters (decode), 0 picks 4; optionally
+ * 12 input bytes (encode) or 16 characters (decode), 0 picks 8; optionally
  * OR-ed with (b << 8), b resident blocks of 8 warps per SM (at most as many
  * as fit; 0: as many as fit), the number of warps the batch is spread over.
  * Both are the autotuner's choices; any value gives the same results. workspace:

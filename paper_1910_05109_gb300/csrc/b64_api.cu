@@ -274,7 +274,7 @@ static int batch_common(bool decode, const uint8_t* src, const int64_t* src_off,
     if (!src_off || !dst_off || !results || !workspace)
         return set_error(B64_ERR_INVALID_ARGUMENT, "%s: NULL pointer argument", fn);
     int units = tile_units & 0xFF;
-    if (units == 0) units = 4;
+    if (units == 0) units = 8;
     if ((units != 1 && units != 2 && units != 4 && units != 8) || tile_units < 0 ||
         tile_units > 0xFFFF)
         return set_error(B64_ERR_INVALID_ARGUMENT,

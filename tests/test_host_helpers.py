@@ -173,3 +173,35 @@ def test_reference_sample_keeps_the_run_near_a_minute():
         run_s = (steps + 5) * s * per_byte / rate
         assert run_s <= 61 or s == (1 << 20) // 3 * 3
     assert bench.reference_sample_bytes(1e6, per_byte, steps=10_000, warmup=5) == (1 << 20) // 3 * 3
+
+
+def _unbound_globals(path):
+    """Names that a function of the module at `path` reads as globals but that
+    neither the module's top level nor the builtins define."""
+    import builtins
+    import symtable
+    top = symtable.symtable(open(path).read(), path, "exec")
+    defined = {s.get_name() for s in top.get_symbols() if s.is_assigned() or s.is_imported()}
+    defined |= set(dir(builtins)) | {"__file__", "__name__", "__doc__"}
+    missing = []
+
+    def walk(t):
+        for s in t.get_symbols():
+            if t.get_type() != "module" and s.is_global() and s.is_referenced() \
+                    and s.get_name() not in defined:
+                missing.append(f"{t.get_name()}:{s.get_name()}")
+        for c in t.get_children():
+            walk(c)
+
+    walk(top)
+    return missing
+
+
+def test_python_sources_read_no_unbound_names():
+    # the GPU-only branches of bench.py and the package never run on this
+    # host; a name read there that nothing defines would only show on the GPU
+    pkg = os.path.join(ROOT, "paper_1910_05109_gb300")
+    files = [os.path.join(ROOT, f) for f in ("bench.py", "__graft_entry__.py")]
+    files += [os.path.join(pkg, f) for f in sorted(os.listdir(pkg)) if f.endswith(".py")]
+    for f in files:
+        assert _unbound_globals(f) == [], f

@@ -69,6 +69,11 @@ namespace {
 #ifndef B64_BATCH_WIDE_STAGES
 #define B64_BATCH_WIDE_STAGES 2
 #endif
+// Rounds that mix strings, where every string in them is stored from
+// registers (0: a round never mixes strings).
+#ifndef B64_BATCH_MIXED
+#define B64_BATCH_MIXED 1
+#endif
 #ifndef B64_BATCH_WIDE_MIN_BLOCKS
 #define B64_BATCH_WIDE_MIN_BLOCKS 2
 #endif
@@ -91,7 +96,11 @@ struct TileShape {
     static constexpr uint32_t TB = 32 * U * G;              // unit start positions per tile
     static constexpr uint32_t SIN = (TB + G + 48 + 15) & ~15u;
     static constexpr uint32_t RUN = 32 * U * O;             // pending-run capacity
+#ifdef B64_BATCH_EXP_NORUN
+    static constexpr uint32_t SOUT = 0;
+#else
     static constexpr uint32_t SOUT = RUN + 32;              // + the copy-out's read slack
+#endif
     static constexpr size_t kSmem = size_t(kWarps) * (size_t(kStages) * SIN + SOUT);
     static_assert(SIN % 16 == 0 && RUN % 16 == 0 && kStages >= 2 && kStages <= 8, "shape");
 };
@@ -238,6 +247,7 @@ struct WinRec {
     uint32_t us[32];  // first unit
     uint32_t un[32];  // units
     uint32_t fl[32];  // bytes of the last unit | alphabet << 8 | padded << 16
+    uint8_t slot[32]; // mixed rounds: the string whose units start at round lane d
 };
 
 struct Win {
@@ -247,11 +257,13 @@ struct Win {
     uint32_t us, un;  // this lane's string: first unit, units
     uint32_t base;    // units of the warp's range before the window
     uint32_t end_u;   // units up to the window's end
+    uint32_t dirm;    // bit i: string w0 + i's segment output is aligned for a unit's stores
 };
 
-template <bool kDecode, uint32_t G>
+template <bool kDecode, uint32_t G, uint32_t A>
 __device__ __forceinline__ void load_window(Win& w, WinRec& r, int64_t s, uint32_t base,
                                             const int64_t* __restrict__ src_off,
+                                            const uint8_t* dst,
                                             const int64_t* __restrict__ dst_off,
                                             const uint8_t* __restrict__ alph_id,
                                             const BatchTables& tabs, int64_t n, int64_t P0,
@@ -286,7 +298,11 @@ __device__ __forceinline__ void load_window(Win& w, WinRec& r, int64_t s, uint32
     w.end_u = base + __shfl_sync(0xffffffffu, incl, 31);
     w.next = src_off[s + 32 < n ? s + 32 : n] - P0;
     r.lo[lane] = w.lo;
-    r.dst[lane] = d + (kDecode ? (sl - lo) / 4 * 3 : (sl - lo) / 3 * 4);
+    const int64_t seg_dst = d + (kDecode ? (sl - lo) / 4 * 3 : (sl - lo) / 3 * 4);
+    r.dst[lane] = seg_dst;
+    w.dirm = __ballot_sync(0xffffffffu,
+                           un == 0 || ((reinterpret_cast<uintptr_t>(dst) + uint64_t(seg_dst)) &
+                                       (A - 1)) == 0);
     r.rel[lane] = sl - lo;
     r.us[lane] = w.us;
     r.un[lane] = un;
@@ -361,6 +377,24 @@ __device__ __forceinline__ uint32_t decode4_at(uint32_t w, uint32_t base, uint32
     return ((a * 64u + b) * 64u + c) * 64u + d;
 }
 
+// The 16 staged characters at sbuf[off ..] of a decode unit: three 64-bit
+// loads from the 8-byte boundary at or below off, one level of selects for
+// off mod 8 >= 4, then funnel shifts for off mod 4. Lanes may differ in off.
+// (Measured on the 100k-string decode against two 128-bit loads with a
+// four-way choice of words: 190 -> 184 us; five 32-bit loads, whose
+// lanes meet four to a bank, 186 us.) Reads up to 24 bytes from off & ~7.
+__device__ __forceinline__ uint4 load_unit16(const uint8_t* sbuf, uint32_t off) {
+    const uint32_t A = off & ~7u, sb = 8 * (off & 3u);
+    const uint2 a = *reinterpret_cast<const uint2*>(sbuf + A);
+    const uint2 b = *reinterpret_cast<const uint2*>(sbuf + A + 8);
+    const uint2 c = *reinterpret_cast<const uint2*>(sbuf + A + 16);
+    const bool o1 = (off & 4u) != 0;
+    const uint32_t v0 = o1 ? a.y : a.x, v1 = o1 ? b.x : a.y, v2 = o1 ? b.y : b.x,
+                   v3 = o1 ? c.x : b.y, v4 = o1 ? c.y : c.x;
+    return make_uint4(__funnelshift_r(v0, v1, sb), __funnelshift_r(v1, v2, sb),
+                      __funnelshift_r(v2, v3, sb), __funnelshift_r(v3, v4, sb));
+}
+
 // The first bad byte among the n staged characters at sbuf[o ..] (one is
 // known to be there), folded into the string's error word as offset base + i.
 // Kept out of line: it is rare, and the hot loops stay smaller.
@@ -410,6 +444,7 @@ __global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
     constexpr uint32_t G = Sh::G, O = Sh::O, TB = Sh::TB, SIN = Sh::SIN, RUN = Sh::RUN,
                        SOUT = Sh::SOUT;
     constexpr uint32_t A = kDecode ? 4u : 16u;  // alignment a unit's output store needs
+    constexpr bool kMixed = B64_BATCH_MIXED != 0;
     constexpr int LUT = kDecode ? 256 : 64;
     extern __shared__ __align__(16) uint8_t smem[];  // [warp][stage] inputs, then [warp] runs
     __shared__ __align__(256) uint8_t luts[kMaxAlphabets][LUT];
@@ -447,8 +482,8 @@ __global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
     const uint8_t* const srcp = src + P0;  // positions below are relative to P0
 
     Win win;
-    load_window<kDecode, G>(win, rec, warp_find_string(src_off, n, P0, lane), 0u, src_off,
-                            dst_off, alph_id, tabs, n, P0, end, lane);
+    load_window<kDecode, G, A>(win, rec, warp_find_string(src_off, n, P0, lane), 0u, src_off,
+                               dst, dst_off, alph_id, tabs, n, P0, end, lane);
 
     // Tile t holds the units that start in [t TB, min((t+1) TB, span)); their
     // bytes end before min(q + G - 1, span). Lane 0 keeps a bit per ring
@@ -524,7 +559,11 @@ __global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
                     uint8_t* const d0 = dst + rec.dst[k0] + int64_t(O) * j0;
                     // an aligned string output takes each unit's stores straight
                     // from registers; any other goes through the run buffer
+#ifdef B64_BATCH_EXP_NORUN
+                    const bool direct = true;
+#else
                     const bool direct = (reinterpret_cast<uintptr_t>(d0) & (A - 1)) == 0;
+#endif
                     if (!direct) {
                         if (run_len) flush();
                         run_dst = d0;
@@ -538,7 +577,7 @@ __global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
                             const uint32_t i = 32 * u + lane;  // unit j0 + i
                             const uint32_t o = o0 + G * i;
                             if constexpr (kDecode) {
-                                const uint4 c = load16_shifted_u(sin, o);  // o mod 16 uniform
+                                const uint4 c = load_unit16(sin, o);  // o mod 16 uniform
                                 uint32_t e = 0;
                                 const uint32_t lb = smem_addr(lut);
                                 const uint3 v =
@@ -577,6 +616,71 @@ __global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
                 }
             }
             while (R < Rq) {
+                const uint32_t cnt = Rq - R < 32u ? Rq - R : 32u;
+                // the window's strings with units in [R, R + cnt)
+                const bool has = win.un > 0 && win.us < R + cnt && win.us + win.un > R;
+                if (kMixed && (__ballot_sync(0xffffffffu, has) & ~win.dirm) == 0) {
+                    // ---- a mixed round: units R .. R + cnt - 1, one a lane, of
+                    //      whichever strings hold them (all stored from
+                    //      registers). A lane finds its string as the last
+                    //      one starting at or below its unit: the strings
+                    //      that start inside the round post their lane offset
+                    //      to a 32-bit mask and their index to a slot.
+                    const int ks0 =
+                        31 - __clz(__ballot_sync(0xffffffffu, win.un > 0 && win.us <= R));
+                    const uint32_t d = win.us - R;
+                    const bool starts = has && win.us > R;
+                    __syncwarp();  // the previous round's slot reads are done
+                    if (starts) rec.slot[d] = uint8_t(lane);
+                    const uint32_t B = __reduce_or_sync(0xffffffffu, starts ? 1u << (d & 31u) : 0u);
+                    __syncwarp();
+                    const uint32_t m = B & (0xFFFFFFFFu >> (31 - lane));  // starts at lanes <= this
+                    const int k = m ? int(rec.slot[31 - __clz(m)]) : ks0;
+                    if (uint32_t(lane) < cnt) {
+                        const uint32_t fl = rec.fl[k], us = rec.us[k];
+                        const uint32_t j = R + uint32_t(lane) - us;
+                        const uint32_t o = rec.lo[k] - p + delta + G * j;
+                        const uint32_t nbl = fl & 0xFFu;
+                        const bool part = j + 1 == rec.un[k] && nbl < G;
+                        const uint8_t* lut = luts[(fl >> 8) & 0xFFu];
+                        uint8_t* const qg = dst + rec.dst[k] + int64_t(O) * j;
+                        if constexpr (kDecode) {
+                            const uint4 c = load_unit16(sin, o);
+                            uint32_t e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+                            const uint32_t lb = smem_addr(lut);
+                            const uint3 v =
+                                pack4x24(decode4_at(c.x, lb, e0), decode4_at(c.y, lb, e1),
+                                         decode4_at(c.z, lb, e2), decode4_at(c.w, lb, e3));
+                            const uint32_t nbu = part ? nbl : 16u;
+                            // groups past a short unit's end are not the string's
+                            const uint32_t e = e0 | (nbu > 4 ? e1 : 0u) | (nbu > 8 ? e2 : 0u) |
+                                               (nbu > 12 ? e3 : 0u);
+                            if (e & kBad)  // rare: the unit's first bad byte
+                                record_first_bad(sin, o, nbu, lut, &err[win.w0 + k],
+                                                 uint64_t(rec.rel[k]) + 16ull * j);
+                            if (part) {
+                                store_head_aligned(qg, make_uint4(v.x, v.y, v.z, 0u), nbl / 4 * 3);
+                            } else {
+                                uint32_t* ow = reinterpret_cast<uint32_t*>(qg);
+                                ow[0] = v.x;
+                                ow[1] = v.y;
+                                ow[2] = v.z;
+                            }
+                        } else {
+                            const uint4 x = load16_shifted(sin, o, o & 3u);
+                            if (part) {
+                                uint32_t nout;
+                                const uint4 ch = encode_last_unit(x, nbl, (fl & (1u << 16)) != 0,
+                                                                  lut, &nout);
+                                store_head_aligned(qg, ch, nout);
+                            } else {
+                                *reinterpret_cast<uint4*>(qg) = encode12(x.x, x.y, x.z, lut);
+                            }
+                        }
+                    }
+                    R += cnt;
+                    continue;
+                }
                 // ---- the units of one string in this tile (a piece), 32 a
                 //      round with uniform addressing; the string's last unit,
                 //      if shorter than G, is coded by its lane in the last round
@@ -588,7 +692,11 @@ __global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
                 const uint8_t* lut = luts[(fl >> 8) & 0xFFu];
                 const uint32_t olo = rec.lo[ks] - p + delta;  // sin offset of the string's unit 0
                 uint8_t* const d_str = dst + rec.dst[ks];
+#ifdef B64_BATCH_EXP_NORUN
+                const bool direct = true;
+#else
                 const bool direct = (reinterpret_cast<uintptr_t>(d_str) & (A - 1)) == 0;
+#endif
                 // output bytes of the string's last unit when it is shorter than G
                 const uint32_t out_last =
                     kDecode ? nbl / 4 * 3
@@ -611,7 +719,7 @@ __global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
                         uint8_t* const qg = d_str + int64_t(O) * jj;
                         uint8_t* const qs = sout + run_len + O * lane;
                         if constexpr (kDecode) {
-                            const uint4 c = load16_shifted_u(sin, o);  // o mod 16 uniform
+                            const uint4 c = load_unit16(sin, o);  // o mod 16 uniform
                             uint32_t e0 = 0, e1 = 0, e2 = 0, e3 = 0;
                             const uint32_t lb = smem_addr(lut);
                             const uint3 v =
@@ -668,8 +776,8 @@ __global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
             }
             // more units below q can only be in later strings
             if (Rq < win.end_u || win.w0 + 32 >= n || win.next >= int64_t(q)) break;
-            load_window<kDecode, G>(win, rec, win.w0 + 32, win.end_u, src_off, dst_off, alph_id,
-                                    tabs, n, P0, end, lane);
+            load_window<kDecode, G, A>(win, rec, win.w0 + 32, win.end_u, src_off, dst, dst_off,
+                                       alph_id, tabs, n, P0, end, lane);
         }
     }
     if (run_len) flush();

@@ -11,12 +11,16 @@ its last 2..5 characters, which the finalize kernel decodes).
 Within its range [P0, end) a warp cuts each string's part into units of G
 bytes (12 encode, 16 decode; the last one shorter), numbers them in order
 through a window of 32 strings (a warp scan of their unit counts), and walks
-tiles of TB = 32 U G consecutive unit start positions; a tile's units of one
-string are coded in rounds of 32, a lane each (a whole tile of full units of
-one string at once; a string's shorter last unit by one lane after its full
-ones), and their output is stored straight from registers when the string's
-output is aligned (16 bytes encode, 4 decode), else appended to a pending run
-that is flushed when it breaks, fills or ends past a string's last unit.
+tiles of TB = 32 U G consecutive unit start positions. A tile's units are
+coded in rounds of 32, a lane each: a whole tile of full units of one string
+at once; a round whose strings' outputs are all aligned for a unit's stores
+(16 bytes encode, 4 decode) as 32 consecutive units of whichever strings hold
+them, each lane finding its string from the strings that start inside the
+round, stored straight from registers; otherwise a string's units in the
+tile (a piece) in rounds of their own, a string's shorter last unit by one
+lane after its full ones, stored from registers when the string's output is
+aligned, else appended to a pending run that is flushed when it breaks,
+fills or ends past a string's last unit.
 Warp ranges end on whole units. Packed and 16-byte aligned output offsets are
 both run. The
 kernel's rules are restated here in Python and run over batches with empty,
@@ -121,7 +125,8 @@ def out_bytes(nbu, G, padded, decode):
     return nbu // 3 * 4 + (0 if r == 0 else 4 if padded else r + 1)
 
 
-def warp_walk(src_off, n, gw, GW, U, decode, align, padded_of=lambda s: True, dst_off=None):
+def warp_walk(src_off, n, gw, GW, U, decode, align, padded_of=lambda s: True, dst_off=None,
+              mixed=True):
     """Yields (string, unit j, bytes, start, uniform) for every unit the warp
     codes, in order, and checks the tile, staging and output-run bounds on
     the way (the run's flushed spans are checked against the units' outputs)."""
@@ -193,6 +198,35 @@ def warp_walk(src_off, n, gw, GW, U, decode, align, padded_of=lambda s: True, ds
                         run["len"] = RUN
                     R = Rq
             while R < Rq:
+                cnt = min(32, Rq - R)
+                has = [win.un[k] > 0 and win.us[k] < R + cnt and win.us[k] + win.un[k] > R
+                       for k in range(32)]
+                if mixed and all(win.un[k] == 0 or seg_dst(k) % A == 0
+                                 for k in range(32) if has[k]):
+                    # a mixed round: lane l codes unit R + l of whichever string
+                    # holds it, found from the strings starting inside the round
+                    ks0 = ballot_last(lambda kk: win.un[kk] > 0 and win.us[kk] <= R)
+                    slot, B = {}, 0
+                    for k in range(32):
+                        if has[k] and win.us[k] > R:
+                            d = win.us[k] - R
+                            slot[d] = k
+                            B |= 1 << d
+                    for lane in range(cnt):
+                        m = B & ((2 << lane) - 1)
+                        k = slot[m.bit_length() - 1] if m else ks0
+                        assert win.us[k] <= R + lane < win.us[k] + win.un[k]
+                        j = R + lane - win.us[k]
+                        part = j + 1 == win.un[k] and win.nbl[k] < G
+                        nbu = win.nbl[k] if part else G
+                        start = win.lo[k] + G * j
+                        assert p <= start < q and start + nbu <= b, (p, q, start, nbu, b)
+                        o = start - pbase
+                        assert 0 <= o and (o & ~7) + 24 <= SIN and o + 20 <= SIN
+                        assert (seg_dst(k) + O * j) % A == 0
+                        yield win.w0 + k, j, nbu, start, not part
+                    R += cnt
+                    continue
                 k = ballot_last(lambda kk: win.un[kk] > 0 and win.us[kk] <= R)
                 us, un, nbl = win.us[k], win.un[k], win.nbl[k]
                 pend = min(Rq, us + un)
@@ -272,12 +306,12 @@ def test_warps_code_every_unit_once(decode, seed, count, origin):
         layouts.append(dst_off)
     for GW, dst_off in [(gw, layouts[i % 2]) for i, gw in
                         enumerate(sorted({1, 2, 3, 31, 33, 608, max(1, total // 5)}))]:
-        for U, align in ((1, 0), (4, 5), (8, 12)):
+        for U, align, mixed in ((1, 0, True), (4, 5, False), (8, 12, True), (8, 3, False)):
             seen = [dict() for _ in range(n)]     # string -> {byte offset: bytes}
             uniform_rounds = 0
             for gw in range(GW):
                 for s, j, nbu, start, uniform in warp_walk(src_off, n, gw, GW, U, decode, align,
-                                                           lambda i: padded[i], dst_off):
+                                                           lambda i: padded[i], dst_off, mixed):
                     rel = start - src_off[s]
                     assert rel % g == 0
                     assert rel not in seen[s], (GW, U, s, rel)

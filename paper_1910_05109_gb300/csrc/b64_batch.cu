@@ -359,24 +359,6 @@ __global__ void encode_results_kernel(const int64_t* __restrict__ src_off, int64
     results[i] = int64_t(enc_length(uint64_t(src_off[i + 1] - src_off[i]), tabs.padded[a]));
 }
 
-// decode4 for a 256-entry table at a 256-byte aligned shared-memory address
-// `base`: the address of each character's entry is built by one byte permute
-// (the character as its low byte, the table's upper address bytes above it)
-// instead of an extract and an add.
-__device__ __forceinline__ uint32_t lds_u8(uint32_t addr) {
-    uint32_t v;
-    asm("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(addr));
-    return v;
-}
-__device__ __forceinline__ uint32_t decode4_at(uint32_t w, uint32_t base, uint32_t& err) {
-    const uint32_t a = lds_u8(__byte_perm(w, base, 0x7650u));
-    const uint32_t b = lds_u8(__byte_perm(w, base, 0x7651u));
-    const uint32_t c = lds_u8(__byte_perm(w, base, 0x7652u));
-    const uint32_t d = lds_u8(__byte_perm(w, base, 0x7653u));
-    err |= a | b | c | d;
-    return ((a * 64u + b) * 64u + c) * 64u + d;
-}
-
 // The 16 staged characters at sbuf[off ..] of a decode unit: three 64-bit
 // loads from the 8-byte boundary at or below off, one level of selects for
 // off mod 8 >= 4, then funnel shifts for off mod 4. Lanes may differ in off.
@@ -413,22 +395,6 @@ __device__ __noinline__ void record_first_bad(const uint8_t* sbuf, uint32_t o, u
 __device__ __forceinline__ bool flag_value(bool b) { return b; }
 template <bool B>
 __device__ __forceinline__ constexpr bool flag_value(std::integral_constant<bool, B>) { return B; }
-
-// Writes bytes 0 .. n-1 (n <= 16) of v (little-endian words) to q, which is
-// 4-byte aligned: whole words, then a 16-bit and an 8-bit store for the rest.
-__device__ __forceinline__ void store_head_aligned(uint8_t* q, uint4 v, uint32_t n) {
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (uint32_t k = 0; k < 4; ++k) {
-        if (4 * k + 4 <= n) {
-            reinterpret_cast<uint32_t*>(q)[k] = w[k];
-        } else if (4 * k < n) {
-            const uint32_t r = n - 4 * k;  // 1..3
-            if (r >= 2) *reinterpret_cast<uint16_t*>(q + 4 * k) = uint16_t(w[k]);
-            if (r & 1u) q[4 * k + (r & 2u)] = uint8_t(w[k] >> (8 * (r & 2u)));
-        }
-    }
-}
 
 // ------------------------------------------------------------------ tile kernels
 // One persistent kernel for both directions (see the file comment).

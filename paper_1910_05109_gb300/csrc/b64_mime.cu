@@ -44,6 +44,12 @@
 #include "b64_internal.h"
 #include "b64_smem.cuh"
 
+// Line-layout fast path: whole groups four a lane for lines of 16 or more
+// data characters (0: one group a lane for every line length).
+#ifndef B64_MIME_UNITS
+#define B64_MIME_UNITS 1
+#endif
+
 namespace b64 {
 namespace {
 
@@ -615,48 +621,114 @@ __device__ LinesResult decode_lines(uint8_t* buf, const uint8_t* lut, int lane,
     }
     const uint32_t wA = __reduce_or_sync(0xffffffffu, ea);
     const uint32_t wB = __reduce_or_sync(0xffffffffu, eb);
-    // whole groups, 128 a round: every read of a round comes before its
-    // writes, and a round's writes (below 384 (r + 1)) stay below the next
-    // round's reads (a group's raw offset is at least 4 times its index)
-    constexpr int kPer = 4;  // groups a lane per round, 32 apart
-    auto round = [&](uint32_t i0, auto checked) {
-        uint32_t q[kPer];
+    if (B64_MIME_UNITS && L >= 16) {
+        // whole groups four a lane: unit i holds the 16 data characters from
+        // cA + 16 i (the last unit possibly fewer groups). A unit starts at a
+        // column that is a multiple of 4, and L >= 16 is one too, so it
+        // crosses at most one line break, between two of its words: the words
+        // before the break are the 16 raw bytes at the unit's start, the rest
+        // the same bytes eol further on. Units go 32 a round; every read of a
+        // round comes before its writes (unit i's 12 output bytes at
+        // buf[base + 12 i]), and a round's writes (below base + 384 (r + 1))
+        // stay below the next round's reads (unit i's raw offset is at least
+        // 16 i, its first 8-byte load at most 7 below it).
+        const uint32_t nunits = (nfull + 3) / 4;
+        const uint32_t lb = smem_addr(lut);
+        auto unit_round = [&](uint32_t u0, auto checked) {
+            constexpr bool kChecked = decltype(checked)::value;
+            const uint32_t i = u0 + uint32_t(lane);
+            uint32_t ng = 4;  // groups of the lane's unit
+            if constexpr (kChecked) ng = i < nunits ? (nfull - 4 * i < 4 ? nfull - 4 * i : 4u) : 0u;
+            uint3 v = make_uint3(0u, 0u, 0u);
+            if (!kChecked || ng) {
+                const uint32_t t = rP + cA + 16 * i, line = __umulhi(t, ly.inv);
+                const uint32_t col = t - line * L;                    // a multiple of 4
+                const uint32_t ro = uint32_t(off0) + line * eol + t;  // raw_of(cA + 16 i)
+                const uint32_t A = ro & ~7u, sh = ro & 7u;
+                const uint2 x0 = *reinterpret_cast<const uint2*>(raw + A);
+                const uint2 x1 = *reinterpret_cast<const uint2*>(raw + A + 8);
+                const uint2 x2 = *reinterpret_cast<const uint2*>(raw + A + 16);
+                // W0..W3: raw bytes sh .. sh + 15; W4: the low bytes of sh + 16 ..
+                const bool o1 = sh >= 4;
+                const uint32_t sb = 8 * (sh & 3u);
+                const uint32_t a0 = o1 ? x0.y : x0.x, a1 = o1 ? x1.x : x0.y,
+                               a2 = o1 ? x1.y : x1.x, a3 = o1 ? x2.x : x1.y,
+                               a4 = o1 ? x2.y : x2.x;
+                const uint32_t w0 = __funnelshift_r(a0, a1, sb), w1 = __funnelshift_r(a1, a2, sb);
+                const uint32_t w2 = __funnelshift_r(a2, a3, sb), w3 = __funnelshift_r(a3, a4, sb);
+                const uint32_t w4 = a4 >> sb;  // its eol low bytes are loaded (sh + eol <= 8)
+                // past the break (after tb = L - col >= 4 data characters) the
+                // words are the same bytes eol further on
+                const uint32_t tb = L - col;
+                const uint32_t c1 = tb <= 4 ? __funnelshift_r(w1, w2, 8 * eol) : w1;
+                const uint32_t c2 = tb <= 8 ? __funnelshift_r(w2, w3, 8 * eol) : w2;
+                const uint32_t c3 = tb <= 12 ? __funnelshift_r(w3, w4, 8 * eol) : w3;
+                uint32_t e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+                v = pack4x24(decode4_at(w0, lb, e0), decode4_at(c1, lb, e1),
+                             decode4_at(c2, lb, e2), decode4_at(c3, lb, e3));
+                if constexpr (kChecked)
+                    bad |= e0 | (ng > 1 ? e1 : 0u) | (ng > 2 ? e2 : 0u) | (ng > 3 ? e3 : 0u);
+                else
+                    bad |= e0 | e1 | e2 | e3;
+            }
+            __syncwarp();
+            if constexpr (kChecked) {
+                if (ng) store_head_aligned(buf + base + 12 * i, make_uint4(v.x, v.y, v.z, 0u), 3 * ng);
+            } else {
+                uint32_t* ow = reinterpret_cast<uint32_t*>(buf + base + 12 * i);
+                ow[0] = v.x;
+                ow[1] = v.y;
+                ow[2] = v.z;
+            }
+            __syncwarp();
+        };
+        const uint32_t nwu = nfull / 128 * 32;  // units of the rounds of 32 whole units
+        for (uint32_t u0 = 0; u0 < nwu; u0 += 32) unit_round(u0, std::false_type{});
+        if (nwu < nunits) unit_round(nwu, std::true_type{});
+    } else {
+        // whole groups, 128 a round: every read of a round comes before its
+        // writes, and a round's writes (below 384 (r + 1)) stay below the next
+        // round's reads (a group's raw offset is at least 4 times its index)
+        constexpr int kPer = 4;  // groups a lane per round, 32 apart
+        auto round = [&](uint32_t i0, auto checked) {
+            uint32_t q[kPer];
 #pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            const uint32_t i = i0 + 32 * u + lane;
-            q[u] = 0;
-            if (!decltype(checked)::value || i < nfull) {
-                const uint32_t ro = raw_of(cA + 4 * i);
-                uint32_t x;
-                if constexpr (kCrLf) {  // even offsets: two 16-bit loads
-                    x = __byte_perm(*reinterpret_cast<const uint16_t*>(raw + ro),
-                                    *reinterpret_cast<const uint16_t*>(raw + ro + 2), 0x5410u);
-                } else {  // any offset: two aligned words, one shift
-                    const uint32_t* w = reinterpret_cast<const uint32_t*>(raw + (ro & ~3u));
-                    x = __funnelshift_r(w[0], w[1], 8 * (ro & 3u));
+            for (int u = 0; u < kPer; ++u) {
+                const uint32_t i = i0 + 32 * u + lane;
+                q[u] = 0;
+                if (!decltype(checked)::value || i < nfull) {
+                    const uint32_t ro = raw_of(cA + 4 * i);
+                    uint32_t x;
+                    if constexpr (kCrLf) {  // even offsets: two 16-bit loads
+                        x = __byte_perm(*reinterpret_cast<const uint16_t*>(raw + ro),
+                                        *reinterpret_cast<const uint16_t*>(raw + ro + 2), 0x5410u);
+                    } else {  // any offset: two aligned words, one shift
+                        const uint32_t* w = reinterpret_cast<const uint32_t*>(raw + (ro & ~3u));
+                        x = __funnelshift_r(w[0], w[1], 8 * (ro & 3u));
+                    }
+                    const uint32_t a = lut[x & 0xFFu], b = lut[(x >> 8) & 0xFFu];
+                    const uint32_t c = lut[(x >> 16) & 0xFFu], d = lut[x >> 24];
+                    bad |= a | b | c | d;
+                    q[u] = ((a * 64u + b) * 64u + c) * 64u + d;
                 }
-                const uint32_t a = lut[x & 0xFFu], b = lut[(x >> 8) & 0xFFu];
-                const uint32_t c = lut[(x >> 16) & 0xFFu], d = lut[x >> 24];
-                bad |= a | b | c | d;
-                q[u] = ((a * 64u + b) * 64u + c) * 64u + d;
             }
-        }
-        __syncwarp();
+            __syncwarp();
 #pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            const uint32_t i = i0 + 32 * u + lane;
-            if (!decltype(checked)::value || i < nfull) {
-                uint8_t* o = buf + base + 3 * i;
-                o[0] = uint8_t(q[u] >> 16);
-                o[1] = uint8_t(q[u] >> 8);
-                o[2] = uint8_t(q[u]);
+            for (int u = 0; u < kPer; ++u) {
+                const uint32_t i = i0 + 32 * u + lane;
+                if (!decltype(checked)::value || i < nfull) {
+                    uint8_t* o = buf + base + 3 * i;
+                    o[0] = uint8_t(q[u] >> 16);
+                    o[1] = uint8_t(q[u] >> 8);
+                    o[2] = uint8_t(q[u]);
+                }
             }
-        }
-        __syncwarp();
-    };
-    const uint32_t nwhole = nfull / (32 * kPer) * (32 * kPer);
-    for (uint32_t i0 = 0; i0 < nwhole; i0 += 32 * kPer) round(i0, std::false_type{});
-    if (nwhole < nfull) round(nwhole, std::true_type{});
+            __syncwarp();
+        };
+        const uint32_t nwhole = nfull / (32 * kPer) * (32 * kPer);
+        for (uint32_t i0 = 0; i0 < nwhole; i0 += 32 * kPer) round(i0, std::false_type{});
+        if (nwhole < nfull) round(nwhole, std::true_type{});
+    }
     if (__any_sync(0xffffffffu, viol != 0 || (bad & 0x40u) != 0)) return kLinesIrregular;
     if (__any_sync(0xffffffffu, bad & 0x80u)) return kLinesSpoilt;
     if (uint32_t(lane) < cA)  // bytes rA - 1 .. 2 of edge A
@@ -685,7 +757,7 @@ __global__ void __launch_bounds__(kThreads, 6)
                        const unsigned long long* __restrict__ states,
                        const unsigned long long* __restrict__ totals, uint64_t nseg,
                        uint64_t wait_limit_ns) {
-    __shared__ uint8_t lut[256];  // 0..63, 0x80 (bad or '='), kSpace
+    __shared__ __align__(256) uint8_t lut[256];  // 0..63, 0x80 (bad or '='), kSpace
     __shared__ __align__(16) uint8_t bufs[kWarps][2][kBuf];
     __shared__ uint64_t bars[kWarps][2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -839,7 +911,7 @@ __global__ void __launch_bounds__(kThreads, 6)
                         const __grid_constant__ DecodeTable tab, int flags,
                         unsigned long long* __restrict__ status, uint64_t nseg,
                         uint64_t wait_limit_ns) {
-    __shared__ uint8_t lut[256];  // 0..63, 0x80 (bad or '='), kSpace
+    __shared__ __align__(256) uint8_t lut[256];  // 0..63, 0x80 (bad or '='), kSpace
     __shared__ __align__(16) uint8_t bufs[kWarps][2][kBuf];
     __shared__ uint64_t bars[kWarps][2];
     __shared__ uint32_t s_first, s_word;
@@ -1239,7 +1311,7 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
                             unsigned long long* __restrict__ status_docs,
                             const unsigned long long* __restrict__ line_docs,
                             const unsigned long long* __restrict__ states, uint64_t slot_cap) {
-    __shared__ uint8_t luts[kMaxAlphabets][256];  // 0..63, 0x80, kSpace
+    __shared__ __align__(256) uint8_t luts[kMaxAlphabets][256];  // 0..63, 0x80, kSpace
     __shared__ __align__(16) uint8_t bufs[kDocWarps][kBuf];
     __shared__ __align__(16) uint8_t stages[kDocWarps][kStage];
     __shared__ uint64_t bars[kDocWarps];

@@ -184,8 +184,7 @@ def test_stale_tile_memory_does_not_leak_into_seams(b64, orc):
 # ---- documents laid out as lines of L data characters + CR LF (L a multiple
 #      of 4): the decode kernel's line fast path, and every way out of it
 
-
-@pytest.mark.parametrize("L", [4, 64, 76, 1020])
+@pytest.mark.parametrize("L", [4, 12, 16, 20, 28, 64, 76, 1020])
 @pytest.mark.parametrize("eol", [b"\r\n", b"\n"])
 @pytest.mark.parametrize("src_off", [0, 3])
 def test_line_layout_sizes(b64, orc, L, eol, src_off):
@@ -233,6 +232,8 @@ def test_line_layout_broken(b64, orc):
             p = base + off
             if p < m:
                 edits += [(p, 0x21), (p, ord("A")), (p, ord(" ")), (p, ord("="))]
+    for p in g.integers(0, m, 40):  # anywhere in a unit of four groups
+        edits += [(int(p), 0x21), (int(p), ord("="))]
     crs = np.nonzero(good == 13)[0]
     for p in crs[g.integers(0, crs.size, 20)]:
         edits += [(int(p), ord("Q")), (int(p) + 1, ord("Q")), (int(p), 0xC3), (int(p), ord("\n"))]

@@ -9,10 +9,14 @@ inv = floor((2^32 - 1) / L) + 1, valid for t < 2^13, and finds the raw offset
 of data character P + d of a segment that starts at raw position S = k Q + r
 as off0 + (t div L) e + t with t = rP + d (rP = r if r < L else 0; off0 = -r
 if r < L else Q - r), and the segment's end as (k, r) advanced by the
-segment's kSeg = 4096 raw bytes written as seg_q Q + seg_r. These are
-restated here with numpy and compared with the layout's definition over many
-segments of every accepted layout. The GPU tests run the kernel itself on
-L = 4, 64, 76 and 1020.
+segment's kSeg = 4096 raw bytes written as seg_q Q + seg_r. For L >= 16 a
+lane decodes a unit of four whole groups (16 data characters) from three
+8-byte loads at its raw offset rounded down to 8, taking each word either at
+that offset or, past the one line break the unit can cross, e bytes further
+on (that word shifted by e bytes into the next one, the next one past the 16
+bytes being the low bytes of the last loaded word). These are restated here with numpy and compared with the layout's
+definition over many segments of every accepted layout. The GPU tests run
+the kernel itself on L = 4, 64, 76 and 1020.
 """
 import numpy as np
 
@@ -74,3 +78,50 @@ def test_skipped_bytes_are_exactly_the_breaks():
             pos = np.arange(s, s + K_SEG)
             data = (pos % Q) < L
             assert breaks == set((np.nonzero(~data)[0]).tolist()), (L, e, s)
+
+
+def test_units_of_four_groups_take_their_characters_from_the_loaded_words():
+    """For L >= 16: every unit of 16 data characters (its last groups inside
+    the segment) is assembled from the 24 bytes loaded at its raw offset
+    rounded down to 8, word by word from that offset or from e bytes further
+    on (the words at or after the break, which falls between words), and the
+    bytes are exactly the raw positions of its data characters. Each round of
+    32 units writes its 12 output bytes a unit (at 12 i) below every load of
+    the next round, and no load leaves the staging buffer."""
+    for L, e in LAYOUTS:
+        if L < 16:
+            continue
+        Q = L + e
+        inv = 0xFFFFFFFF // L + 1
+        for s in range(0, 24 * K_SEG, K_SEG):
+            k, r = divmod(s, Q)
+            P = k * L + min(r, L)
+            k1, r1 = divmod(s + K_SEG, Q)
+            P1 = k1 * L + min(r1, L)
+            rP = r if r < L else 0
+            off0 = -r if r < L else Q - r
+            cA = (4 - P % 4) % 4
+            nfull = (P1 - P - cA) // 4
+            nunits = (nfull + 3) // 4
+            i = np.arange(nunits, dtype=np.int64)
+            ng = np.minimum(nfull - 4 * i, 4)
+            t = rP + cA + 16 * i
+            line = umulhi(t, inv).astype(np.int64)
+            col = t - line * L
+            assert np.all(col % 4 == 0)
+            ro = off0 + line * e + t
+            A, sh = ro & ~7, ro & 7
+            assert np.all(sh + e <= 8)          # the shifted words' bytes stay in the 24 loaded
+            assert np.all((sh & 3) + e <= 4)    # and the word past the 16 needs only its low word
+            assert np.all(A + 24 <= K_SEG + 48)  # the staging buffer's slack
+            tb = L - col
+            b = np.arange(16, dtype=np.int64)
+            got = ro[:, None] + b[None, :] + np.where(b[None, :] >= tb[:, None], e, 0)
+            j = P + cA + 16 * i[:, None] + b[None, :]
+            want = Q * (j // L) + j % L - s
+            used = b[None, :] < 4 * ng[:, None]
+            assert np.array_equal(got[used], want[used]), (L, e, s)
+            assert np.all(want[used] < K_SEG)   # whole groups inside the segment
+            for r0 in range(0, nunits - 32, 32):
+                wr_end = 12 * (r0 + 32)
+                assert wr_end <= A[r0 + 32:r0 + 64].min(), (L, e, s, r0)

@@ -96,11 +96,7 @@ struct TileShape {
     static constexpr uint32_t TB = 32 * U * G;              // unit start positions per tile
     static constexpr uint32_t SIN = (TB + G + 48 + 15) & ~15u;
     static constexpr uint32_t RUN = 32 * U * O;             // pending-run capacity
-#ifdef B64_BATCH_EXP_NORUN
-    static constexpr uint32_t SOUT = 0;
-#else
     static constexpr uint32_t SOUT = RUN + 32;              // + the copy-out's read slack
-#endif
     static constexpr size_t kSmem = size_t(kWarps) * (size_t(kStages) * SIN + SOUT);
     static_assert(SIN % 16 == 0 && RUN % 16 == 0 && kStages >= 2 && kStages <= 8, "shape");
 };
@@ -525,11 +521,7 @@ __global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
                     uint8_t* const d0 = dst + rec.dst[k0] + int64_t(O) * j0;
                     // an aligned string output takes each unit's stores straight
                     // from registers; any other goes through the run buffer
-#ifdef B64_BATCH_EXP_NORUN
-                    const bool direct = true;
-#else
                     const bool direct = (reinterpret_cast<uintptr_t>(d0) & (A - 1)) == 0;
-#endif
                     if (!direct) {
                         if (run_len) flush();
                         run_dst = d0;
@@ -658,11 +650,7 @@ __global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
                 const uint8_t* lut = luts[(fl >> 8) & 0xFFu];
                 const uint32_t olo = rec.lo[ks] - p + delta;  // sin offset of the string's unit 0
                 uint8_t* const d_str = dst + rec.dst[ks];
-#ifdef B64_BATCH_EXP_NORUN
-                const bool direct = true;
-#else
                 const bool direct = (reinterpret_cast<uintptr_t>(d_str) & (A - 1)) == 0;
-#endif
                 // output bytes of the string's last unit when it is shorter than G
                 const uint32_t out_last =
                     kDecode ? nbl / 4 * 3

@@ -24,17 +24,23 @@
 //      next tiles' copies started before the current one is coded (or aligned
 //      loads where the span would leave the source buffer). The strings are
 //      known from a window of 32 strings' metadata (their units counted by a
-//      warp scan). A tile's units of one string (a piece) are coded in rounds
-//      of 32, one a lane, with uniform addressing (a round never mixes
-//      strings; a whole tile of full units of one string runs as one unrolled
-//      block), the string's last unit finished by its lane with the padding
-//      rules. A string whose output is aligned for a unit's stores (16 bytes
-//      encode, 4 decode; b64_batch_offsets' B64_OFFSETS_ALIGN16 layout gives
-//      every string that) is stored straight from registers; any other
-//      string's output is appended to a pending run in shared memory, written
-//      out with aligned 16-byte stores once the run breaks, fills, or ends
-//      past a string's last unit. Decode rounds fold bad-byte offsets into
-//      the string's error word with an atomic minimum;
+//      warp scan). A whole tile of full units of one string runs as one
+//      unrolled block, U units a lane with uniform addressing. Other tiles
+//      go in rounds: where every string with units in the round has its
+//      output aligned for a unit's stores (16 bytes encode, 4 decode;
+//      b64_batch_offsets' B64_OFFSETS_ALIGN16 layout gives every string
+//      that), a mixed round codes consecutive units of whichever strings
+//      hold them, V a lane when the tile has 32 V units left (so that each
+//      lane has independent units in flight), else one a lane, each lane
+//      finding its units' strings from the strings that start inside the
+//      round, and stores them straight from registers; otherwise a string's
+//      units in the tile (a piece) go in rounds of 32 with uniform
+//      addressing, and an unaligned string's output is appended to a
+//      pending run in shared memory, written out with aligned 16-byte stores
+//      once the run breaks, fills, or ends past a string's last unit. A
+//      string's short last unit is finished by its lane with the padding
+//      rules. Decode rounds fold bad-byte offsets into the string's error
+//      word with an atomic minimum;
 //   3. decode only: one thread per string applies the padding and length
 //      rules to the string's last 2..5 characters and writes its result.
 #include <mutex>
@@ -73,6 +79,13 @@ namespace {
 // registers (0: a round never mixes strings).
 #ifndef B64_BATCH_MIXED
 #define B64_BATCH_MIXED 1
+#endif
+// Units a lane in a wide mixed round of the decoder with 8-unit tiles (1 to
+// 4; narrower tiles take at most 2). Wide rounds measured 187 -> 179 us on
+// 100,000 strings with aligned outputs; the encoder's measured slower (its
+// rounds stay one unit a lane).
+#ifndef B64_BATCH_MIXED_UNITS
+#define B64_BATCH_MIXED_UNITS 4
 #endif
 #ifndef B64_BATCH_WIDE_MIN_BLOCKS
 #define B64_BATCH_WIDE_MIN_BLOCKS 2
@@ -243,7 +256,7 @@ struct WinRec {
     uint32_t us[32];  // first unit
     uint32_t un[32];  // units
     uint32_t fl[32];  // bytes of the last unit | alphabet << 8 | padded << 16
-    uint8_t slot[32]; // mixed rounds: the string whose units start at round lane d
+    uint8_t slot[32 * B64_BATCH_MIXED_UNITS];  // mixed rounds: the string starting at unit R + d
 };
 
 struct Win {
@@ -327,10 +340,8 @@ __device__ __forceinline__ uint32_t keep_bytes(uint32_t w, int b) {
 // bytes in x (bytes past them read as zero, Sec. 2: a partial final group is
 // completed with zero bits), coded with the string's padding rule. Returns
 // the characters; *nout = their count.
-__device__ __forceinline__ uint4 encode_last_unit(uint4 x, uint32_t nb, bool padded,
-                                                  const uint8_t* lut, uint32_t* nout) {
-    uint4 ch = encode12(keep_bytes(x.x, int(nb)), keep_bytes(x.y, int(nb) - 4),
-                        keep_bytes(x.z, int(nb) - 8), lut);
+__device__ __forceinline__ uint4 pad_last_unit(uint4 ch, uint32_t nb, bool padded,
+                                               uint32_t* nout) {
     const uint32_t t3 = nb / 3, r = nb - 3 * t3;
     *nout = 4 * t3 + (r == 0 ? 0u : padded ? 4u : r + 1);
     if (r && padded) {  // '=' after the last group's characters
@@ -342,6 +353,12 @@ __device__ __forceinline__ uint4 encode_last_unit(uint4 x, uint32_t nb, bool pad
         else ch.w = (ch.w & m) | pad;
     }
     return ch;
+}
+__device__ __forceinline__ uint4 encode_last_unit(uint4 x, uint32_t nb, bool padded,
+                                                  const uint8_t* lut, uint32_t* nout) {
+    const uint4 ch = encode12(keep_bytes(x.x, int(nb)), keep_bytes(x.y, int(nb) - 4),
+                              keep_bytes(x.z, int(nb) - 8), lut);
+    return pad_last_unit(ch, nb, padded, nout);
 }
 
 // Each string's encoded length (encode results), one thread per string.
@@ -407,6 +424,10 @@ __global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
                        SOUT = Sh::SOUT;
     constexpr uint32_t A = kDecode ? 4u : 16u;  // alignment a unit's output store needs
     constexpr bool kMixed = B64_BATCH_MIXED != 0;
+    // units a lane in a wide mixed round (decode only; at most 2 under the
+    // 80-register bound of the narrower tiles)
+    constexpr uint32_t V = !kDecode ? 1u
+                           : U >= 8 || B64_BATCH_MIXED_UNITS < 2 ? B64_BATCH_MIXED_UNITS : 2u;
     constexpr int LUT = kDecode ? 256 : 64;
     extern __shared__ __align__(16) uint8_t smem[];  // [warp][stage] inputs, then [warp] runs
     __shared__ __align__(256) uint8_t luts[kMaxAlphabets][LUT];
@@ -574,57 +595,105 @@ __global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
                 }
             }
             while (R < Rq) {
-                const uint32_t cnt = Rq - R < 32u ? Rq - R : 32u;
+                // a mixed round: 32 V units (decode, V a lane) when the tile
+                // has that many left, else up to 32 (one a lane)
+                const uint32_t left = Rq - R;
+                // wide only where every string of the window has aligned output
+                const bool wide = kDecode && V > 1 && left >= 32u * V && win.dirm == 0xFFFFFFFFu;
+                const uint32_t cnt = wide ? 32u * V : (left < 32u ? left : 32u);
                 // the window's strings with units in [R, R + cnt)
                 const bool has = win.un > 0 && win.us < R + cnt && win.us + win.un > R;
                 if (kMixed && (__ballot_sync(0xffffffffu, has) & ~win.dirm) == 0) {
-                    // ---- a mixed round: units R .. R + cnt - 1, one a lane, of
+                    // ---- a mixed round: unit R + 32 v + lane for each v, of
                     //      whichever strings hold them (all stored from
-                    //      registers). A lane finds its string as the last
-                    //      one starting at or below its unit: the strings
-                    //      that start inside the round post their lane offset
-                    //      to a 32-bit mask and their index to a slot.
+                    //      registers). A lane finds each unit's string as the
+                    //      last one starting at or below it: the strings that
+                    //      start inside the round post their offset to one
+                    //      32-bit mask a v and their index to a slot.
                     const int ks0 =
                         31 - __clz(__ballot_sync(0xffffffffu, win.un > 0 && win.us <= R));
                     const uint32_t d = win.us - R;
                     const bool starts = has && win.us > R;
                     __syncwarp();  // the previous round's slot reads are done
                     if (starts) rec.slot[d] = uint8_t(lane);
-                    const uint32_t B = __reduce_or_sync(0xffffffffu, starts ? 1u << (d & 31u) : 0u);
-                    __syncwarp();
-                    const uint32_t m = B & (0xFFFFFFFFu >> (31 - lane));  // starts at lanes <= this
-                    const int k = m ? int(rec.slot[31 - __clz(m)]) : ks0;
-                    if (uint32_t(lane) < cnt) {
-                        const uint32_t fl = rec.fl[k], us = rec.us[k];
-                        const uint32_t j = R + uint32_t(lane) - us;
-                        const uint32_t o = rec.lo[k] - p + delta + G * j;
-                        const uint32_t nbl = fl & 0xFFu;
-                        const bool part = j + 1 == rec.un[k] && nbl < G;
-                        const uint8_t* lut = luts[(fl >> 8) & 0xFFu];
-                        uint8_t* const qg = dst + rec.dst[k] + int64_t(O) * j;
+                    auto round = [&](auto vc) {
+                        constexpr uint32_t NV = decltype(vc)::value;
+                        uint32_t B[NV];
+#pragma unroll
+                        for (uint32_t v = 0; v < NV; ++v)
+                            B[v] = __reduce_or_sync(
+                                0xffffffffu, starts && (d >> 5) == v ? 1u << (d & 31u) : 0u);
+                        __syncwarp();
+                        const uint32_t le = 0xFFFFFFFFu >> (31 - lane);  // lanes <= this
+                        int kv[NV];
+                        int carry = ks0;  // the string of the last start below block v
+#pragma unroll
+                        for (uint32_t v = 0; v < NV; ++v) {
+                            const uint32_t m = B[v] & le;
+                            kv[v] = m ? int(rec.slot[32 * v + 31 - __clz(m)]) : carry;
+                            if (v + 1 < NV && B[v])
+                                carry = int(rec.slot[32 * v + 31 - __clz(B[v])]);
+                        }
                         if constexpr (kDecode) {
-                            const uint4 c = load_unit16(sin, o);
-                            uint32_t e0 = 0, e1 = 0, e2 = 0, e3 = 0;
-                            const uint32_t lb = smem_addr(lut);
-                            const uint3 v =
-                                pack4x24(decode4_at(c.x, lb, e0), decode4_at(c.y, lb, e1),
-                                         decode4_at(c.z, lb, e2), decode4_at(c.w, lb, e3));
-                            const uint32_t nbu = part ? nbl : 16u;
-                            // groups past a short unit's end are not the string's
-                            const uint32_t e = e0 | (nbu > 4 ? e1 : 0u) | (nbu > 8 ? e2 : 0u) |
-                                               (nbu > 12 ? e3 : 0u);
-                            if (e & kBad)  // rare: the unit's first bad byte
-                                record_first_bad(sin, o, nbu, lut, &err[win.w0 + k],
-                                                 uint64_t(rec.rel[k]) + 16ull * j);
-                            if (part) {
-                                store_head_aligned(qg, make_uint4(v.x, v.y, v.z, 0u), nbl / 4 * 3);
-                            } else {
-                                uint32_t* ow = reinterpret_cast<uint32_t*>(qg);
-                                ow[0] = v.x;
-                                ow[1] = v.y;
-                                ow[2] = v.z;
+                            // the NV units are decoded first and stored after, so
+                            // their loads and table lookups overlap
+                            uint3 outv[NV];
+                            uint32_t nst[NV], eb[NV];
+                            uint8_t* qv[NV];
+#pragma unroll
+                            for (uint32_t v = 0; v < NV; ++v) {
+                                const uint32_t i = 32 * v + uint32_t(lane);
+                                const int k = kv[v];
+                                const uint32_t fl = rec.fl[k], us = rec.us[k];
+                                const uint32_t j = R + i - us;
+                                // an idle lane (i >= cnt) reads the buffer's
+                                // start and stores nothing
+                                const uint32_t o = i < cnt ? rec.lo[k] - p + delta + G * j : 0u;
+                                const uint32_t nbl = fl & 0xFFu;
+                                const bool part = j + 1 == rec.un[k] && nbl < G;
+                                const uint32_t nb = part ? nbl : G;
+                                qv[v] = dst + rec.dst[k] + int64_t(O) * j;
+                                const uint4 c = load_unit16(sin, o);
+                                uint32_t e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+                                const uint32_t lb = smem_addr(luts[(fl >> 8) & 0xFFu]);
+                                outv[v] = pack4x24(decode4_at(c.x, lb, e0), decode4_at(c.y, lb, e1),
+                                                   decode4_at(c.z, lb, e2), decode4_at(c.w, lb, e3));
+                                // groups past a short unit's end are not the string's
+                                eb[v] = e0 | (nb > 4 ? e1 : 0u) | (nb > 8 ? e2 : 0u) |
+                                        (nb > 12 ? e3 : 0u);
+                                nst[v] = i < cnt ? nb / 4 * 3 : 0u;  // a short unit: 3..9
                             }
-                        } else {
+#pragma unroll
+                            for (uint32_t v = 0; v < NV; ++v) {
+                                if (nst[v] == O) {
+                                    uint32_t* ow = reinterpret_cast<uint32_t*>(qv[v]);
+                                    ow[0] = outv[v].x;
+                                    ow[1] = outv[v].y;
+                                    ow[2] = outv[v].z;
+                                } else if (nst[v]) {
+                                    store_head_aligned(
+                                        qv[v], make_uint4(outv[v].x, outv[v].y, outv[v].z, 0u),
+                                        nst[v]);
+                                }
+                                if (nst[v] && (eb[v] & kBad)) {  // rare: the unit's first bad byte
+                                    const int k = kv[v];
+                                    const uint32_t fl = rec.fl[k];
+                                    const uint32_t j = R + 32 * v + uint32_t(lane) - rec.us[k];
+                                    record_first_bad(sin, rec.lo[k] - p + delta + G * j,
+                                                     nst[v] / 3 * 4, luts[(fl >> 8) & 0xFFu],
+                                                     &err[win.w0 + k],
+                                                     uint64_t(rec.rel[k]) + 16ull * j);
+                                }
+                            }
+                        } else if (uint32_t(lane) < cnt) {  // encode: one unit a lane
+                            const int k = kv[0];
+                            const uint32_t fl = rec.fl[k], us = rec.us[k];
+                            const uint32_t j = R + uint32_t(lane) - us;
+                            const uint32_t o = rec.lo[k] - p + delta + G * j;
+                            const uint32_t nbl = fl & 0xFFu;
+                            const bool part = j + 1 == rec.un[k] && nbl < G;
+                            const uint8_t* lut = luts[(fl >> 8) & 0xFFu];
+                            uint8_t* const qg = dst + rec.dst[k] + int64_t(O) * j;
                             const uint4 x = load16_shifted(sin, o, o & 3u);
                             if (part) {
                                 uint32_t nout;
@@ -635,7 +704,9 @@ __global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
                                 *reinterpret_cast<uint4*>(qg) = encode12(x.x, x.y, x.z, lut);
                             }
                         }
-                    }
+                    };
+                    if (wide) round(std::integral_constant<uint32_t, V>{});
+                    else round(std::integral_constant<uint32_t, 1>{});
                     R += cnt;
                     continue;
                 }

@@ -12,15 +12,18 @@ Within its range [P0, end) a warp cuts each string's part into units of G
 bytes (12 encode, 16 decode; the last one shorter), numbers them in order
 through a window of 32 strings (a warp scan of their unit counts), and walks
 tiles of TB = 32 U G consecutive unit start positions. A tile's units are
-coded in rounds of 32, a lane each: a whole tile of full units of one string
-at once; a round whose strings' outputs are all aligned for a unit's stores
-(16 bytes encode, 4 decode) as 32 consecutive units of whichever strings hold
-them, each lane finding its string from the strings that start inside the
-round, stored straight from registers; otherwise a string's units in the
-tile (a piece) in rounds of their own, a string's shorter last unit by one
-lane after its full ones, stored from registers when the string's output is
-aligned, else appended to a pending run that is flushed when it breaks,
-fills or ends past a string's last unit.
+coded in rounds: a whole tile of full units of one string at once; a round
+whose strings' outputs are all aligned for a unit's stores (16 bytes encode,
+4 decode) as consecutive units of whichever strings hold them (decode: 32 V
+units, V a lane 32 apart, V = 4 with 8-unit tiles, else 2, when the tile
+has that many left and every string of the window has aligned output;
+otherwise up to 32, one a lane), each lane finding each
+unit's string from the strings that start inside the round, stored straight
+from registers; otherwise a string's units in the tile (a piece) in rounds
+of their own, a string's shorter last unit by one lane after its full ones,
+stored from registers when the string's output is aligned, else appended to
+a pending run that is flushed when it breaks, fills or ends past a string's
+last unit.
 Warp ranges end on whole units. Packed and 16-byte aligned output offsets are
 both run. The
 kernel's rules are restated here in Python and run over batches with empty,
@@ -127,6 +130,7 @@ def out_bytes(nbu, G, padded, decode):
 
 def warp_walk(src_off, n, gw, GW, U, decode, align, padded_of=lambda s: True, dst_off=None,
               mixed=True):
+    V = (4 if U >= 8 else 2) if decode else 1   # units a lane in a wide mixed round
     """Yields (string, unit j, bytes, start, uniform) for every unit the warp
     codes, in order, and checks the tile, staging and output-run bounds on
     the way (the run's flushed spans are checked against the units' outputs)."""
@@ -198,33 +202,47 @@ def warp_walk(src_off, n, gw, GW, U, decode, align, padded_of=lambda s: True, ds
                         run["len"] = RUN
                     R = Rq
             while R < Rq:
-                cnt = min(32, Rq - R)
+                # wide only where every string of the window has aligned output
+                wide = (V > 1 and Rq - R >= 32 * V and
+                        all(win.un[k] == 0 or seg_dst(k) % A == 0 for k in range(32)))
+                cnt = 32 * V if wide else min(32, Rq - R)
                 has = [win.un[k] > 0 and win.us[k] < R + cnt and win.us[k] + win.un[k] > R
                        for k in range(32)]
-                if mixed and all(win.un[k] == 0 or seg_dst(k) % A == 0
-                                 for k in range(32) if has[k]):
-                    # a mixed round: lane l codes unit R + l of whichever string
-                    # holds it, found from the strings starting inside the round
+                ok = mixed and all(win.un[k] == 0 or seg_dst(k) % A == 0
+                                   for k in range(32) if has[k])
+                NV = V if wide else 1
+                if ok:
+                    # a mixed round: lane l codes units R + 32 v + l (v < V) of
+                    # whichever strings hold them, found from the strings
+                    # starting inside the round (V block masks and a slot array)
                     ks0 = ballot_last(lambda kk: win.un[kk] > 0 and win.us[kk] <= R)
-                    slot, B = {}, 0
+                    slot, B = {}, [0] * NV
                     for k in range(32):
                         if has[k] and win.us[k] > R:
                             d = win.us[k] - R
+                            assert d < 32 * NV
                             slot[d] = k
-                            B |= 1 << d
-                    for lane in range(cnt):
-                        m = B & ((2 << lane) - 1)
-                        k = slot[m.bit_length() - 1] if m else ks0
-                        assert win.us[k] <= R + lane < win.us[k] + win.un[k]
-                        j = R + lane - win.us[k]
-                        part = j + 1 == win.un[k] and win.nbl[k] < G
-                        nbu = win.nbl[k] if part else G
-                        start = win.lo[k] + G * j
-                        assert p <= start < q and start + nbu <= b, (p, q, start, nbu, b)
-                        o = start - pbase
-                        assert 0 <= o and (o & ~7) + 24 <= SIN and o + 20 <= SIN
-                        assert (seg_dst(k) + O * j) % A == 0
-                        yield win.w0 + k, j, nbu, start, not part
+                            B[d >> 5] |= 1 << (d & 31)
+                    carry = ks0
+                    for v in range(NV):
+                        for lane in range(32):
+                            i = 32 * v + lane
+                            m = B[v] & ((2 << lane) - 1)
+                            k = slot[32 * v + m.bit_length() - 1] if m else carry
+                            if i >= cnt:
+                                continue        # idle: reads the buffer's start, stores nothing
+                            assert win.us[k] <= R + i < win.us[k] + win.un[k]
+                            j = R + i - win.us[k]
+                            part = j + 1 == win.un[k] and win.nbl[k] < G
+                            nbu = win.nbl[k] if part else G
+                            start = win.lo[k] + G * j
+                            assert p <= start < q and start + nbu <= b, (p, q, start, nbu, b)
+                            o = start - pbase
+                            assert 0 <= o and (o & ~7) + 24 <= SIN and o + 20 <= SIN
+                            assert (seg_dst(k) + O * j) % A == 0
+                            yield win.w0 + k, j, nbu, start, not part
+                        if B[v]:
+                            carry = slot[32 * v + B[v].bit_length() - 1]
                     R += cnt
                     continue
                 k = ballot_last(lambda kk: win.un[kk] > 0 and win.us[kk] <= R)

@@ -808,7 +808,8 @@ def batch_workload(args) -> dict:
                        "output_offsets": ("b64_batch_offsets with B64_OFFSETS_ALIGN16 (16-byte "
                                           "aligned string starts); packed offsets timed beside"
                                           if align16 else "b64_batch_offsets, packed"),
-                       "l2": "batch input and output (314 MB + 419 MB) larger than L2; no flush"},
+                       "l2": f"batch input and output ({total_in / 1e6:.0f} MB + "
+                             f"{int(texts[0].numel()) / 1e6:.0f} MB) larger than L2; no flush"},
             "encode": out["encode"], "decode": out["decode"], "clocks": clocks.summary(),
             # per step: encode results + tile kernel; decode tile + finalize kernel
             "gpu_launches": 4 * args.steps}
@@ -827,9 +828,10 @@ def run_batch(args):
 # ---------------------------------------------------------------- MIME workload
 
 # The kernels of one MIME decode call, and how many launches it makes.
-MIME_KERNELS = ("mime decode call (mime_count_kernel, mime_scan_kernel, mime_decode_kernel, "
-                "mime_finalize_kernel)")
-MIME_LAUNCHES_PER_CALL = 4
+MIME_KERNELS = ("mime decode call (mime_status_init_kernel, mime_onepass_kernel; "
+                "mime_count_kernel, mime_scan_kernel, mime_decode_kernel, which return at once "
+                "when the line layout holds; mime_finalize_kernel)")
+MIME_LAUNCHES_PER_CALL = 6
 
 def mime_workload(args) -> dict:
     """256 MiB of seed-3 random bytes, encoded with the standard table and
@@ -905,7 +907,8 @@ def mime_workload(args) -> dict:
             "config": {"workload": f"{n} random bytes (seed 3), standard table, 76-char lines "
                                    "+ CRLF, no trailing CRLF", "input_bytes": m,
                        "output_bytes": n,
-                       "l2": "input and output (367 MB + 268 MB) larger than L2; no flush"},
+                       "l2": f"input and output ({m / 1e6:.0f} MB + {n / 1e6:.0f} MB) larger "
+                             "than L2; no flush"},
             "memcpy_gbps": m / (mc / 1e3) / 1e9, "frac_of_memcpy": mc / ms,
             # the whole call (count, scan, decode and finalize kernels) against the
             # bytes it must move: the wrapped input read, the decoded bytes written

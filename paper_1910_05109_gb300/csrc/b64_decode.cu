@@ -119,12 +119,6 @@ __device__ void block_min_to_global(uint64_t first, unsigned long long* d_err) {
     if ((threadIdx.x & 31) == 0 && w != kNoError) atomicMin(d_err, (unsigned long long)w);
 }
 
-// Programmatic dependent launch: the body and tail kernels may start while
-// the kernel before them finishes; this waits until that kernel has
-// completed and its writes are visible (and makes this kernel's own
-// completion imply it).
-__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
 // One thread: *d_err = "no error" before the body kernel folds offsets into it.
 __global__ void result_init_kernel(unsigned long long* d_err) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *d_err = kNoError;
@@ -407,24 +401,6 @@ __global__ void __launch_bounds__(kSmallThreads)
         *d_result = tail_result(src, m, dst, tab, flags, err);
     }
     cluster.sync();  // no block leaves while block 0 may still read its shared memory
-}
-
-// Launches `kernel` as a programmatic dependent of the previous kernel on
-// the stream (it calls wait_prior_grid before using that kernel's results).
-template <class... KArgs, class... Args>
-cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
-                             cudaStream_t stream, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
 struct KernelSetup {

@@ -109,4 +109,29 @@ cudaError_t launch_mime_decode_batch(const BatchArgs& a, const BatchTables& tabs
                                      size_t workspace_bytes, cudaStream_t stream);
 uint32_t mime_fault_flag(bool clear);
 
+// ---- programmatic dependent launch (the decode and MIME launch chains)
+// A kernel launched by launch_dependent may start while the kernel before it
+// on the stream finishes; wait_prior_grid waits until that kernel has
+// completed and its writes are visible, and makes this kernel's own
+// completion imply it, so a dependent kernel calls it before it reads what
+// the kernel before wrote, and on every path before it exits. Launched
+// plainly, the wait returns at once.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                             cudaStream_t stream, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 }  // namespace b64

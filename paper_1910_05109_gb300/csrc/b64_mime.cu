@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(kCountThreads, 4)
                       unsigned long long* __restrict__ totals, uint64_t nseg,
                       const unsigned long long* __restrict__ status) {
     __shared__ uint32_t s_cnt[kSegsPerBlock], s_key[kSegsPerBlock];
+    wait_prior_grid();  // the one-pass kernel's status words
     if (status[7] == kNoSegment) return;  // the one-pass kernel decoded everything
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool aligned = (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
@@ -265,6 +266,7 @@ __global__ void __launch_bounds__(kScanThreads)
     __shared__ uint64_t warp_key[kScanThreads / 32];
     __shared__ uint32_t first_space;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    wait_prior_grid();  // the count kernel's totals and the status words
     if (status[7] == kNoSegment) return;  // the one-pass kernel decoded everything
     // the decode kernel recomputes the error and '=' words: what the one-pass
     // kernel left there came from counts that may be wrong past status[7]
@@ -498,7 +500,23 @@ __device__ __forceinline__ void decode_segment(uint8_t* buf, const uint8_t* lut,
 
 // Copies buf[skip .. skip + nout) to global q: 16-byte stores at aligned
 // addresses, each built from two aligned 16-byte shared loads; bytes at the
-// edges. Reads up to 32 bytes past skip + nout. Warp-collective.
+// edges. Reads up to 32 bytes past skip + nout. Warp-collective. The word
+// offset of the source within its 16 bytes is the same for every store, so
+// the loop has one copy per offset with the words picked at compile time.
+template <uint32_t SW>
+__device__ __forceinline__ void copy_out_body(const uint8_t* buf, uint32_t A0, uint32_t n16,
+                                              uint32_t sb, uint8_t* __restrict__ q, int lane) {
+    for (uint32_t i = lane; i < n16; i += 32) {
+        const uint32_t A = A0 + 16 * i;
+        const uint4 a = *reinterpret_cast<const uint4*>(buf + A);
+        const uint4 b = *reinterpret_cast<const uint4*>(buf + A + 16);
+        const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        *reinterpret_cast<uint4*>(q + 16 * i) =
+            make_uint4(__funnelshift_r(w[SW], w[SW + 1], sb), __funnelshift_r(w[SW + 1], w[SW + 2], sb),
+                       __funnelshift_r(w[SW + 2], w[SW + 3], sb),
+                       __funnelshift_r(w[SW + 3], w[SW + 4], sb));
+    }
+}
 __device__ __forceinline__ void copy_out(const uint8_t* buf, uint32_t skip, uint32_t nout,
                                          uint8_t* __restrict__ q, int lane) {
     const uint32_t head = uint32_t((16 - (reinterpret_cast<uintptr_t>(q) & 15)) & 15);
@@ -506,18 +524,12 @@ __device__ __forceinline__ void copy_out(const uint8_t* buf, uint32_t skip, uint
     if (lane < int(h)) q[lane] = buf[skip + lane];
     const uint32_t body = (nout - h) & ~15u;
     const uint32_t o0 = skip + h, sw = (o0 & 15) >> 2, sb = 8 * (o0 & 3);
-    for (uint32_t i = lane; i < body / 16; i += 32) {
-        const uint32_t A = (o0 & ~15u) + 16 * i;
-        const uint4 a = *reinterpret_cast<const uint4*>(buf + A);
-        const uint4 b = *reinterpret_cast<const uint4*>(buf + A + 16);
-        const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-        uint32_t v[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k)  // words sw .. sw + 4 (sw is the same in every lane)
-            v[k] = sw == 0 ? w[k] : sw == 1 ? w[k + 1] : sw == 2 ? w[k + 2] : w[(k + 3) & 7];
-        *reinterpret_cast<uint4*>(q + h + 16 * i) =
-            make_uint4(__funnelshift_r(v[0], v[1], sb), __funnelshift_r(v[1], v[2], sb),
-                       __funnelshift_r(v[2], v[3], sb), __funnelshift_r(v[3], v[4], sb));
+    const uint32_t A0 = o0 & ~15u;
+    switch (sw) {  // the same in every lane
+        case 0: copy_out_body<0>(buf, A0, body / 16, sb, q + h, lane); break;
+        case 1: copy_out_body<1>(buf, A0, body / 16, sb, q + h, lane); break;
+        case 2: copy_out_body<2>(buf, A0, body / 16, sb, q + h, lane); break;
+        default: copy_out_body<3>(buf, A0, body / 16, sb, q + h, lane); break;
     }
     for (uint32_t i = h + body + lane; i < nout; i += 32) q[i] = buf[skip + i];
 }
@@ -770,6 +782,7 @@ __global__ void __launch_bounds__(kThreads, 6)
         fence_mbar_init();
     }
     __syncthreads();  // the only block-wide barrier: tables and barriers ready
+    wait_prior_grid();  // the scan kernel's prefixes and the status words
     if (status[7] == kNoSegment) return;  // the one-pass kernel decoded everything
     const bool aligned = (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
     unsigned long long* timeout = status + 4;
@@ -924,6 +937,7 @@ __global__ void __launch_bounds__(kThreads, 6)
     }
     const uint32_t word = block_line_layout(src, m, &s_first, &s_word);  // synchronises
     if (tid == 0) lut['\r'] = lut['\n'] = lut[' '] = uint8_t(kSpace);
+    wait_prior_grid();  // the status words are initialised
     if (blockIdx.x == 0 && tid == 0) status[6] = word;
     if (!word) {  // no layout: the counting path decodes everything
         if (blockIdx.x == 0 && tid == 0) atomicMin(status + 7, 0ull);
@@ -1061,6 +1075,7 @@ __global__ void mime_finalize_kernel(const uint8_t* __restrict__ src, uint64_t m
                                      const __grid_constant__ DecodeTable tab,
                                      const unsigned long long* __restrict__ status,
                                      int64_t* __restrict__ d_result) {
+    wait_prior_grid();  // every kernel before it has completed
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (status[4]) {
         *d_result = B64_E_TIMEOUT;
@@ -1483,6 +1498,12 @@ size_t mime_workspace_bytes(uint64_t m) {
     return 64 + 8 * size_t(nseg + nblk);
 }
 
+// One warp: the single-document call's status words (see launch_mime_decode).
+__global__ void mime_status_init_kernel(unsigned long long* __restrict__ status) {
+    const int i = threadIdx.x;
+    if (i < 8) status[i] = (i < 3 || i == 7) ? ~0ull : 0ull;
+}
+
 cudaError_t launch_mime_decode(const uint8_t* src, uint64_t m, uint8_t* dst,
                                const DecodeTable& tab, int flags, int64_t* d_result,
                                void* workspace, uint64_t wait_limit_ns, cudaStream_t st) {
@@ -1491,13 +1512,17 @@ cudaError_t launch_mime_decode(const uint8_t* src, uint64_t m, uint8_t* dst,
     unsigned long long* status = static_cast<unsigned long long*>(workspace);
     unsigned long long* states = status + 8;
     unsigned long long* totals = states + nseg;
-    // status[0..2] (first bad byte, first '=' raw and compacted) start at
-    // "none"; status[3..6] (status[4]: the timeout word; status[5]: the whole
-    // input's state; status[6]: the line layout) at zero; status[7] (the
-    // first segment off the layout) at "none".
-    cudaError_t e = cudaMemsetAsync(status, 0xFF, 3 * sizeof(uint64_t), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(status + 3, 0, 4 * sizeof(uint64_t), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(status + 7, 0xFF, sizeof(uint64_t), st);
+    // The init kernel sets status[0..2] (first bad byte, first '=' raw and
+    // compacted) to "none"; status[3..6] (status[4]: the timeout word;
+    // status[5]: the whole input's state; status[6]: the line layout) to zero;
+    // status[7] (the first segment off the layout) to "none".
+    // Every kernel after the init kernel is a programmatic dependent of the
+    // one before it (it waits for that kernel before touching what it wrote),
+    // so each launch overlaps the end of the kernel before; the count, scan
+    // and decode kernels return at once when the one-pass kernel decoded
+    // everything.
+    mime_status_init_kernel<<<1, 32, 0, st>>>(status);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (nseg) {
         const DeviceInfo& di = device_info();
@@ -1505,26 +1530,22 @@ cudaError_t launch_mime_decode(const uint8_t* src, uint64_t m, uint8_t* dst,
                         occupancy(mime_onepass_kernel, kThreads, g_op_occ[di.device & 63]);
         const uint64_t need = (nseg + kWarps - 1) / kWarps;
         if (need < grid) grid = need;
-        mime_onepass_kernel<<<unsigned(grid), kThreads, 0, st>>>(src, m, dst, tab, flags, status,
-                                                                 nseg, wait_limit_ns);
-        e = cudaGetLastError();
+        e = launch_dependent(mime_onepass_kernel, unsigned(grid), kThreads, 0, st, src, m, dst, tab,
+                             flags, status, nseg, wait_limit_ns);
         if (e != cudaSuccess) return e;
-        mime_count_kernel<<<unsigned(nblk), kCountThreads, 0, st>>>(src, m, states, totals, nseg,
-                                                                    status);
-        e = cudaGetLastError();
+        e = launch_dependent(mime_count_kernel, unsigned(nblk), kCountThreads, 0, st, src, m,
+                             states, totals, nseg, status);
         if (e != cudaSuccess) return e;
-        mime_scan_kernel<<<1, kScanThreads, 0, st>>>(totals, nblk, status, src, m);
-        e = cudaGetLastError();
+        e = launch_dependent(mime_scan_kernel, 1, kScanThreads, 0, st, totals, nblk, status, src, m);
         if (e != cudaSuccess) return e;
         grid = uint64_t(di.sm_count) * occupancy(mime_decode_kernel, kThreads, g_occ[di.device & 63]);
         if (need < grid) grid = need;
-        mime_decode_kernel<<<unsigned(grid), kThreads, 0, st>>>(
-            src, m, dst, tab, flags, status, states, totals, nseg, wait_limit_ns);
-        e = cudaGetLastError();
+        e = launch_dependent(mime_decode_kernel, unsigned(grid), kThreads, 0, st, src, m, dst, tab,
+                             flags, status, states, totals, nseg, wait_limit_ns);
         if (e != cudaSuccess) return e;
     }
-    mime_finalize_kernel<<<1, 32, 0, st>>>(src, m, flags, tab, status, d_result);
-    return cudaGetLastError();
+    return launch_dependent(mime_finalize_kernel, 1, 32, 0, st, src, m, flags, tab, status,
+                            d_result);
 }
 
 cudaError_t launch_selftest_wait(int64_t* d_result, uint64_t wait_limit_ns, cudaStream_t st) {

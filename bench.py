@@ -598,7 +598,7 @@ def finish(args, v):
 # then a short sweep of higher rates for the engine's capacity.
 WORKLOAD_MIN_STEPS = 100
 SERVE_DURATION_S = 10.0
-SERVE_SWEEP = (40_000.0, 80_000.0, 160_000.0)
+SERVE_SWEEP = (40_000.0, 80_000.0, 120_000.0, 160_000.0)
 
 
 def other_workloads(args) -> dict:

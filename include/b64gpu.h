@@ -353,6 +353,16 @@ b64_server* b64_server_create(size_t budget_bytes, int n_streams, size_t max_bat
 int b64_server_submit(b64_server* s, uint64_t tag, int op, int alph_id, const uint8_t* in,
                       size_t len, uint8_t* out, size_t out_cap);
 
+/* Queues n requests in one call (fewer crossings for callers that collect
+ * arrivals): request i is (tags[i], ops[i], alph_ids[i], ins[i], lens[i],
+ * outs[i], out_caps[i]), each checked as b64_server_submit checks one, in
+ * order. Returns how many were queued: n, or the index of the first refused
+ * request (b64_last_error says why; none after it is queued); an error code
+ * < 0 for a NULL array with n > 0. */
+int b64_server_submit_many(b64_server* s, int n, const uint64_t* tags, const int32_t* ops,
+                           const int32_t* alph_ids, const uint8_t* const* ins,
+                           const uint64_t* lens, uint8_t* const* outs, const uint64_t* out_caps);
+
 /* Writes up to max_out completions; returns how many (or an error code < 0). */
 int b64_server_poll(b64_server* s, b64_completion* out, int max_out);
 

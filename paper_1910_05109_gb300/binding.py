@@ -52,6 +52,7 @@ SIGNATURES = {
     "b64_selftest_wait_timeout": (_I, [_P, ctypes.c_uint64, _P]),
     "b64_server_create": (_P, [_SZ, _I, _SZ, _P, _I]),
     "b64_server_submit": (_I, [_P, ctypes.c_uint64, _I, _I, _P, _SZ, _P, _SZ]),
+    "b64_server_submit_many": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P]),
     "b64_server_poll": (_I, [_P, _P, _I]),
     "b64_server_outstanding": (_I, [_P]),
     "b64_server_batches": (ctypes.c_uint64, [_P]),

@@ -316,6 +316,19 @@ int b64_server_submit(b64_server* s, uint64_t tag, int op, int alph_id, const ui
     return B64_SUCCESS;
 }
 
+int b64_server_submit_many(b64_server* s, int n, const uint64_t* tags, const int32_t* ops,
+                           const int32_t* alph_ids, const uint8_t* const* ins,
+                           const uint64_t* lens, uint8_t* const* outs, const uint64_t* out_caps) {
+    if (!s || n < 0 ||
+        (n > 0 && (!tags || !ops || !alph_ids || !ins || !lens || !outs || !out_caps)))
+        return set_error(B64_ERR_INVALID_ARGUMENT, "b64_server_submit_many: bad argument");
+    for (int i = 0; i < n; ++i)
+        if (b64_server_submit(s, tags[i], ops[i], alph_ids[i], ins[i], size_t(lens[i]), outs[i],
+                              size_t(out_caps[i])) != B64_SUCCESS)
+            return i;
+    return n;
+}
+
 int b64_server_poll(b64_server* s, b64_completion* out, int max_out) {
     if (!s || max_out < 0 || (max_out > 0 && !out))
         return set_error(B64_ERR_INVALID_ARGUMENT, "b64_server_poll: bad argument");

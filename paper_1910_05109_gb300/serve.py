@@ -43,6 +43,20 @@ class Server:
         if rc != b64.B64_SUCCESS:
             raise b64.B64Error(b64.last_error())
 
+    def submit_many(self, tags, ops, alph_ids, in_ptrs, lens, out_ptrs, out_caps) -> None:
+        """Queues len(tags) requests in one call (b64_server_submit_many);
+        pointers are host addresses as integers."""
+        arrs = [np.ascontiguousarray(a, dtype=t) for a, t in (
+            (tags, np.uint64), (ops, np.int32), (alph_ids, np.int32), (in_ptrs, np.uint64),
+            (lens, np.uint64), (out_ptrs, np.uint64), (out_caps, np.uint64))]
+        n = arrs[0].size
+        for a in arrs[1:]:
+            if a.size != n:
+                raise ValueError("submit_many: arrays of different lengths")
+        rc = b64.lib().b64_server_submit_many(self.handle, n, *[a.ctypes.data for a in arrs])
+        if rc != n:
+            raise b64.B64Error(b64.last_error())
+
     def poll(self) -> np.ndarray:
         n = b64.lib().b64_server_poll(self.handle, self._buf.ctypes.data, self._buf.size)
         if n < 0:
@@ -119,43 +133,82 @@ class HostRing:
 def run_open_loop(server: Server, arrivals, ops, sizes, pick, pools, out_bytes: int,
                   keep_outputs: bool = False):
     """Replays the request stream in real time. pools[op] = (host array, unit)
-    where payloads are cut at random multiples of `unit`. Returns per-request
-    latency (s, arrival -> hand-back), results, and wall time."""
+    where payloads are cut at random multiples of `unit`. Each pass hands every
+    request that has arrived to the engine in one call (as many as the host
+    output ring has room for, in one ring slot) and polls once. Returns
+    per-request latency (s, arrival -> hand-back), results, and wall time.
+    (Up to four arrivals go in one b64_server_submit call each, more in one
+    b64_server_submit_many call.)"""
     n = arrivals.size
     lat = np.full(n, np.nan)
     results = np.zeros(n, np.int64)
     outputs = {} if keep_outputs else None
     ring = HostRing(out_bytes)
-    base = [int(p.ctypes.data) for p, _ in pools]
-    span = [p.size for p, _ in pools]
-    caps = np.where(ops == 0, (sizes + 2) // 3 * 4, (sizes + 3) // 4 * 3)
+    ring_base = int(ring.buf.ctypes.data)
+    caps = np.where(ops == 0, (sizes + 2) // 3 * 4, (sizes + 3) // 4 * 3).astype(np.int64)
+    slots = (caps + 63) // 64 * 64                # each request's share of its group's slot
+    base = np.array([int(p.ctypes.data) for p, _ in pools], np.int64)
+    unit = np.array([u for _, u in pools], np.int64)
+    span = np.array([p.size for p, _ in pools], np.int64)
+    room = (span[ops] - sizes) // unit[ops]
+    in_ptr = base[ops] + (pick * room).astype(np.int64) * unit[ops]
+    out_at = np.zeros(n, np.int64)                # offset of each request's output in the ring
+    group = np.zeros(n, np.int64)
+    left = []                                     # per group: requests not yet handed back
+    tags_all = np.arange(n, dtype=np.int64)
+    zeros = np.zeros(n, np.int32)
     nxt = 0
     done = 0
     t0 = time.perf_counter()
     while done < n:
         now = time.perf_counter() - t0
-        while nxt < n and arrivals[nxt] <= now:
-            op, size = int(ops[nxt]), int(sizes[nxt])
-            unit = pools[op][1]
-            room = (span[op] - size) // unit
-            off = int(pick[nxt] * room) * unit
-            at = ring.take(nxt, int(caps[nxt]))
-            if at is None:
-                break                                # host output space full: poll first
-            server.submit(nxt, op, 0, base[op] + off, size, int(ring.buf.ctypes.data) + at,
-                          int(caps[nxt]))
-            nxt += 1
+        hi = nxt
+        if nxt < n and arrivals[nxt] <= now:
+            hi = nxt + 1
+            if hi < n and arrivals[hi] <= now:
+                hi = int(np.searchsorted(arrivals, now, side="right"))
+        if hi > nxt:
+            k = hi - nxt
+            if k <= 4:                                # a few: plain Python is cheaper
+                size = int(slots[nxt:hi].sum())
+                at = ring.take(len(left), size)
+                if at is not None:
+                    for i in range(nxt, hi):
+                        out_at[i] = at
+                        group[i] = len(left)
+                        server.submit(i, int(ops[i]), 0, int(in_ptr[i]), int(sizes[i]),
+                                      ring_base + at, int(caps[i]))
+                        at += int(slots[i])
+                    left.append(k)
+                    nxt = hi
+            else:
+                cum = np.cumsum(slots[nxt:hi])
+                at = ring.take(len(left), int(cum[k - 1]))
+                while at is None and k > 1:           # fewer, if the ring has less room
+                    k //= 2
+                    at = ring.take(len(left), int(cum[k - 1]))
+                if at is not None:                    # else: host output space full, poll first
+                    sl = slice(nxt, nxt + k)
+                    out_at[sl] = at + cum[:k] - slots[sl]
+                    group[sl] = len(left)
+                    left.append(k)
+                    server.submit_many(tags_all[sl], ops[sl], zeros[sl], in_ptr[sl], sizes[sl],
+                                       ring_base + out_at[sl], caps[sl])
+                    nxt += k
         comp = server.poll()
         if comp.size:
             t_now = time.perf_counter() - t0
             tags = comp["tag"].astype(np.int64)
             lat[tags] = t_now - arrivals[tags]
             results[tags] = comp["result"]
-            for tag, r in zip(tags.tolist(), comp["result"].tolist()):
-                if keep_outputs:
-                    at = ring.by_tag[tag][0]
+            if keep_outputs:
+                for tag, r in zip(tags.tolist(), comp["result"].tolist()):
+                    at = int(out_at[tag])
                     outputs[tag] = ring.buf[at:at + max(r, 0)].copy()
-                ring.release(tag)
+            for g in group[tags].tolist():
+                left[g] -= 1
+                if left[g] == 0:
+                    ring.release(g)
             done += comp.size
     wall = time.perf_counter() - t0
     return lat, results, wall, outputs

@@ -159,6 +159,14 @@ def test_new_entry_points_reject_bad_arguments_without_gpu(L):
     assert L.b64_host_decode(None, 16, 10, 16, std) == b.B64_E_INVAL
     assert L.b64_host_codec_device_bytes(None) == 0
     L.b64_host_codec_destroy(None)
+    # serving: a NULL server, a negative count, NULL arrays with n > 0
+    assert L.b64_server_submit_many(None, 0, None, None, None, None, None, None,
+                                    None) == b.B64_ERR_INVALID_ARGUMENT
+    assert L.b64_server_submit_many(16, -1, None, None, None, None, None, None,
+                                    None) == b.B64_ERR_INVALID_ARGUMENT
+    assert L.b64_server_submit_many(16, 2, 16, 16, 16, None, 16, 16,
+                                    16) == b.B64_ERR_INVALID_ARGUMENT
+    assert "submit_many" in b.last_error()
 
 
 def test_binding_rejects_host_and_mistyped_tensors(L):

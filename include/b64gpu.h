@@ -220,8 +220,12 @@ int b64_mime_decode_batch(const uint8_t* src, const int64_t* src_off, int64_t n,
  * string). tile_units: bytes per thread of a tile as 1, 2, 4 or 8 units of
  * 12 input bytes (encode) or 16 characters (decode), 0 picks 8; optionally
  * OR-ed with (b << 8), b resident blocks of 8 warps per SM (at most as many
- * as fit; 0: as many as fit), the number of warps the batch is spread over.
- * Both are the autotuner's choices; any value gives the same results. workspace:
+ * as fit; 0: as many as fit), the number of warps the batch is spread over,
+ * and with B64_TILE_PAIRS (encode with 8 units, at most 2 alphabets; ignored
+ * otherwise): tiles of one string's full units are encoded through 4096-entry
+ * tables of character pairs built per block (faster for long strings, slower
+ * where tiles are shared by many strings). All are the autotuner's choices;
+ * any value gives the same results. workspace:
  * device memory of at least b64_batch_workspace_size(n) bytes, 256-byte
  * aligned, owned by the caller and busy until the enqueued work completes.
  * Strings may start at any alignment; src and dst may be NULL only if every
@@ -230,6 +234,7 @@ int b64_mime_decode_batch(const uint8_t* src, const int64_t* src_off, int64_t n,
  * and output are then incomplete. Returns B64_SUCCESS or an error code;
  * nothing is enqueued on error. n == 0 enqueues nothing. */
 #define B64_BATCH_MAX_ALPHABETS 4
+#define B64_TILE_PAIRS (1 << 16)
 
 size_t b64_batch_workspace_size(int64_t n);
 

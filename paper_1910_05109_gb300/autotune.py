@@ -1,17 +1,21 @@
 """Autotuner for the batched kernels' tile shape.
 
-Two axes, both passed to the kernels in `tile_units`:
+Three axes, all passed to the kernels in `tile_units`:
 - bytes per thread: a tile is 32 threads x U units, a unit being 12 input
   bytes (encode) or 16 characters (decode), U in {2, 4, 8};
 - threads per batch: B resident blocks of 8 warps per SM (0 = as many as fit,
   1 or 2), i.e. how many warps the batch is spread over. Within a tile a
   string's units are coded 32 at a time, one a thread, so a string of L bytes
   meets up to min(32, ceil(L / 12)) threads at once and ceil(L / (32 * 12 * U))
-  tiles.
-The tuner times every (U, B) on the caller's own batch with CUDA events,
+  tiles;
+- for encode with U = 8 and at most two alphabets, whether whole tiles go
+  through 4096-entry character-pair tables (B64_TILE_PAIRS, bit 16): faster
+  for long strings, slower where many strings share tiles.
+The tuner times every choice on the caller's own batch with CUDA events,
 keeps the fastest, and caches it in a JSON file keyed by GPU name, SM count,
 operation and the batch's size buckets (log2 of the string count and of the
-mean string length). The value returned (and cached) is U | B << 8.
+mean string length). The value returned (and cached) is U | B << 8, with
+bit 16 for the pair tables.
 
 The cache lives in $B64GPU_CACHE, else $XDG_CACHE_HOME/b64gpu/autotune.json,
 else ~/.cache/b64gpu/autotune.json.
@@ -29,12 +33,21 @@ from . import binding as b64
 
 UNITS = (2, 4, 8)
 BLOCKS = (0, 1, 2)          # resident blocks an SM (0: as many as fit)
+TILE_PAIRS = 1 << 16        # B64_TILE_PAIRS: encode's whole tiles through pair tables
 CHOICES = tuple(u | (b << 8) for b in BLOCKS for u in UNITS)
+# encode with 8 units also tries the pair tables (batches of at most 2 alphabets)
+ENCODE_CHOICES = CHOICES + tuple(8 | (b << 8) | TILE_PAIRS for b in BLOCKS)
+
+
+def choices(op: str, n_alphabets: int) -> tuple:
+    """The tile_units values the tuner times for op."""
+    return ENCODE_CHOICES if op == "encode" and n_alphabets <= 2 else CHOICES
 
 
 def describe(tile: int) -> dict:
-    """The two axes of a tile_units value."""
-    return {"units": tile & 0xFF, "blocks_per_sm": (tile >> 8) & 0xFF}
+    """The axes of a tile_units value."""
+    return {"units": tile & 0xFF, "blocks_per_sm": (tile >> 8) & 0xFF,
+            "pairs": bool(tile & TILE_PAIRS)}
 _lock = threading.Lock()
 
 
@@ -104,7 +117,7 @@ def best_units(op: str, src, src_off, dst, dst_off, alphabets, alph_id=None,
             return int(table[k]["tile_units"]), {}
     ws = b64.batch_workspace(n, src.device)
     timings = {u: time_units(op, src, src_off, dst, dst_off, alphabets, alph_id, u, ws)
-               for u in CHOICES}
+               for u in choices(op, len(alphabets))}
     best = min(timings, key=timings.get)
     with _lock:
         table = _load(path)

@@ -137,6 +137,7 @@ int batch_tables(const char* fn, const b64_alphabet* const* alphabets, int n_alp
         t->padded[k] = a->padded;
         t->canonical[k] = a->canonical;
     }
+    t->n_alph = n_alphabets;
     return B64_SUCCESS;
 }
 
@@ -276,11 +277,11 @@ static int batch_common(bool decode, const uint8_t* src, const int64_t* src_off,
     int units = tile_units & 0xFF;
     if (units == 0) units = 8;
     if ((units != 1 && units != 2 && units != 4 && units != 8) || tile_units < 0 ||
-        tile_units > 0xFFFF)
+        (tile_units & ~(0xFFFF | B64_TILE_PAIRS)))
         return set_error(B64_ERR_INVALID_ARGUMENT,
                          "%s: tile_units must be 0, 1, 2, 4 or 8, optionally OR-ed with "
-                         "(blocks per SM << 8)", fn);
-    tile_units = units | (tile_units & 0xFF00);
+                         "(blocks per SM << 8) and B64_TILE_PAIRS", fn);
+    tile_units = units | (tile_units & (0xFF00 | B64_TILE_PAIRS));
     if (workspace_bytes < batch_workspace_bytes(n))
         return set_error(B64_ERR_INVALID_ARGUMENT, "%s: workspace holds %zu bytes, %zu needed", fn,
                          workspace_bytes, batch_workspace_bytes(n));

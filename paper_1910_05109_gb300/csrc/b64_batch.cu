@@ -421,7 +421,7 @@ __device__ __forceinline__ constexpr bool flag_value(std::integral_constant<bool
 
 // ------------------------------------------------------------------ tile kernels
 // One persistent kernel for both directions (see the file comment).
-template <int U, bool kDecode>
+template <int U, bool kDecode, bool kPairs = false>
 __global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
                                   TileShape<U, kDecode>::kMinBlocks)
     batch_tile_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
@@ -455,6 +455,28 @@ __global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
         fence_mbar_init();
     }
     __syncthreads();
+    // encode with pair tables (kPairs): per alphabet the 4096 character pairs
+    // of two adjacent 6-bit fields, after the staging and run buffers
+    uint16_t* const pairs = reinterpret_cast<uint16_t*>(smem + Sh::kSmem);
+    const uint32_t npair = kPairs ? uint32_t(tabs.n_alph) : 0u;
+    if constexpr (kPairs) {
+        for (uint32_t i = tid; i < npair * 4096u; i += kThreads) {
+            const uint8_t* l = luts[i >> 12];
+            pairs[i] = uint16_t(uint32_t(l[(i >> 6) & 63u]) | (uint32_t(l[i & 63u]) << 8));
+        }
+        __syncthreads();
+    }
+    // 12 bytes -> 16 characters with alphabet id (its byte table lut), in
+    // the whole-tile loop (pair tables made whole tiles faster, 144 -> 130 us
+    // on 300 strings of 1 MiB, but the kernel's mixed rounds slower even with
+    // their byte tables, 165 -> 174 us on 100,000 lognormal strings: the
+    // autotuner picks per batch shape)
+    auto enc12 = [&](const uint4& x, uint32_t id, const uint8_t* lut) -> uint4 {
+        if constexpr (kPairs)
+            return encode12_pairs(x.x, x.y, x.z, pairs + ((id < npair ? id : 0u) << 12));
+        else
+            return encode12(x.x, x.y, x.z, lut);
+    };
     uint8_t* const sin_base = smem + size_t(warp) * S * SIN;
     uint8_t* const sout = smem + size_t(kWarps) * S * SIN + size_t(warp) * SOUT;
     WinRec& rec = recs[warp];
@@ -590,7 +612,7 @@ __global__ void __launch_bounds__(TileShape<U, kDecode>::kThreads,
                                                      uint64_t(rec.rel[k0]) + 16ull * (j0 + i));
                             } else {
                                 const uint4 x = load16_shifted(sin, o, o & 3u);  // o mod 4 uniform
-                                const uint4 ch = encode12(x.x, x.y, x.z, lut);
+                                const uint4 ch = enc12(x, (fl0 >> 8) & 0xFFu, lut);
                                 if (dd) *reinterpret_cast<uint4*>(d0 + 16 * i) = ch;
                                 else *reinterpret_cast<uint4*>(sout + 16 * i) = ch;
                             }
@@ -908,23 +930,32 @@ int occupancy(K kernel, int threads, size_t smem, size_t max_smem, Occ& occ, cud
     return occ.ctas;
 }
 
-Occ g_enc_occ[4][64], g_dec_occ[4][64];
+Occ g_enc_occ[4][64], g_dec_occ[4][64], g_encp_occ[4][64];
+// Batches of up to this many alphabets may encode 8-unit tiles with pair
+// tables when the caller asks (B64_TILE_PAIRS; two 8 KiB tables still leave
+// room for two blocks an SM); 0 turns them off.
+#ifndef B64_BATCH_ENC_PAIRS
+#define B64_BATCH_ENC_PAIRS 2
+#endif
+constexpr int kPairAlphabets = B64_BATCH_ENC_PAIRS;
 
 int unit_slot(int units) { return units == 1 ? 0 : units == 2 ? 1 : units == 4 ? 2 : 3; }
 
-template <int U, bool kDecode>
+template <int U, bool kDecode, bool kPairs = false>
 cudaError_t launch_tiles(const BatchArgs& a, const BatchTables& t, unsigned long long* err,
                          int blocks_per_sm, cudaStream_t st) {
     using Sh = TileShape<U, kDecode>;
     const DeviceInfo& di = device_info();
     cudaError_t e = cudaSuccess;
-    Occ& slot = (kDecode ? g_dec_occ : g_enc_occ)[unit_slot(U)][di.device & 63];
-    const int occ = occupancy(batch_tile_kernel<U, kDecode>, Sh::kThreads, Sh::kSmem, Sh::kSmem,
+    // the pair tables' room is sized for kPairAlphabets, so the occupancy is one figure
+    const size_t smem = Sh::kSmem + (kPairs ? size_t(kPairAlphabets) * 8192 : 0);
+    Occ& slot = (kDecode ? g_dec_occ : kPairs ? g_encp_occ : g_enc_occ)[unit_slot(U)][di.device & 63];
+    const int occ = occupancy(batch_tile_kernel<U, kDecode, kPairs>, Sh::kThreads, smem, smem,
                               slot, &e);
     if (e != cudaSuccess) return e;
     // blocks_per_sm (the tuner's second axis): fewer resident warps than fit
     const int bps = blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ;
-    batch_tile_kernel<U, kDecode><<<unsigned(di.sm_count * bps), Sh::kThreads, Sh::kSmem, st>>>(
+    batch_tile_kernel<U, kDecode, kPairs><<<unsigned(di.sm_count * bps), Sh::kThreads, smem, st>>>(
         a.src, a.src_off, a.n, a.dst, a.dst_off, t, a.alph_id, err);
     return cudaGetLastError();
 }
@@ -1063,7 +1094,10 @@ cudaError_t launch_batch(bool decode, const BatchArgs& a, const BatchTables& tab
             case 1: return launch_tiles<1, false>(a, tabs, nullptr, bps, st);
             case 2: return launch_tiles<2, false>(a, tabs, nullptr, bps, st);
             case 4: return launch_tiles<4, false>(a, tabs, nullptr, bps, st);
-            default: return launch_tiles<8, false>(a, tabs, nullptr, bps, st);
+            default:
+                if ((tile & B64_TILE_PAIRS) && tabs.n_alph >= 1 && tabs.n_alph <= kPairAlphabets)
+                    return launch_tiles<8, false, true>(a, tabs, nullptr, bps, st);
+                return launch_tiles<8, false>(a, tabs, nullptr, bps, st);
         }
     }
     unsigned long long* err = static_cast<unsigned long long*>(workspace);

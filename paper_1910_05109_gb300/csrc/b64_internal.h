@@ -62,6 +62,7 @@ struct BatchTables {
     DecodeTable dec[kMaxAlphabets];
     int padded[kMaxAlphabets];
     int canonical[kMaxAlphabets];
+    int n_alph;  // distinct alphabets the caller gave (slots past them repeat alphabet 0)
 };
 
 struct BatchArgs {

@@ -90,6 +90,13 @@ def test_argument_errors_without_gpu(L):
     assert "overlap" in b.last_error()
     assert L.b64_decode_async(4096, 400, 4096 + 100, std, 8, None) == \
         b.B64_ERR_INVALID_ARGUMENT
+    # batch tile_units: units 1, 2, 4 or 8, blocks per SM in bits 8..15, the
+    # pair-table bit 16; anything else is refused before a launch
+    arr = (ctypes.c_void_p * 1)(std)
+    for bad in (3, 8 | (1 << 17), -1):
+        assert L.b64_encode_batch(256, 512, 4, 1024, 768, arr, 1, None, 2048, bad, 4096, 1 << 20,
+                                  None) == b.B64_ERR_INVALID_ARGUMENT
+        assert "tile_units" in b.last_error()
 
 
 def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):

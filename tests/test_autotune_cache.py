@@ -1,7 +1,8 @@
 """Host logic of the tile-shape autotuner (no GPU): every (units, blocks per
-SM) pair is timed, the fastest is chosen and stored with both axes, a second
-call is served from the cache file, retune measures again, and a damaged cache
-file is treated as empty."""
+SM) pair is timed (and, for encode with at most two alphabets, 8 units with
+the pair tables at each blocks-per-SM value), the fastest is chosen and stored
+with its axes, a second call is served from the cache file, retune measures
+again, and a damaged cache file is treated as empty."""
 import json
 
 import torch
@@ -14,7 +15,7 @@ def fake_env(monkeypatch, timings):
 
     def time_units(op, src, src_off, dst, dst_off, alphabets, alph_id, units, workspace, reps=5):
         calls.append(units)
-        return timings(units & 0xFF, units >> 8)
+        return timings(units & 0xFF, (units >> 8) & 0xFF) + (0.01 if units >> 16 else 0.0)
 
     monkeypatch.setattr(autotune, "time_units", time_units)
     monkeypatch.setattr(autotune, "key", lambda op, n, total, device=None: f"gpu|{op}|{n}|{total}")
@@ -36,14 +37,34 @@ def test_searches_both_axes_then_caches(monkeypatch, tmp_path):
     calls = fake_env(monkeypatch, grid(4, 2))
     path = str(tmp_path / "tune.json")
     tile, t = autotune.best_units(*args(), path=path)
-    assert tile == 4 | (2 << 8) and autotune.describe(tile) == {"units": 4, "blocks_per_sm": 2}
-    assert sorted(t) == sorted(autotune.CHOICES) and len(calls) == 9
-    assert {c & 0xFF for c in calls} == {2, 4, 8} and {c >> 8 for c in calls} == {0, 1, 2}
+    assert tile == 4 | (2 << 8)
+    assert autotune.describe(tile) == {"units": 4, "blocks_per_sm": 2, "pairs": False}
+    assert sorted(t) == sorted(autotune.ENCODE_CHOICES) and len(calls) == 12
+    assert {c & 0xFF for c in calls} == {2, 4, 8} and {(c >> 8) & 0xFF for c in calls} == {0, 1, 2}
+    assert sorted(c for c in calls if c >> 16) == [8 | (b << 8) | (1 << 16) for b in (0, 1, 2)]
     stored = json.load(open(path))["gpu|encode|8|800"]
     assert stored["tile_units"] == tile and stored["units"] == 4 and stored["blocks_per_sm"] == 2
-    assert len(stored["ms"]) == 9
+    assert len(stored["ms"]) == 12
     tile2, t2 = autotune.best_units(*args(), path=path)
-    assert tile2 == tile and t2 == {} and len(calls) == 9  # cache hit: nothing timed
+    assert tile2 == tile and t2 == {} and len(calls) == 12  # cache hit: nothing timed
+
+
+def test_pair_tables_chosen_when_fastest_and_only_for_encode(monkeypatch, tmp_path):
+    calls = fake_env(monkeypatch, lambda u, b: 1.0)
+    monkeypatch.setattr(autotune, "time_units",
+                        lambda *a, **k: calls.append(a[7]) or (0.5 if a[7] >> 16 and
+                                                               (a[7] >> 8) & 0xFF == 2 else 1.0))
+    path = str(tmp_path / "tune.json")
+    tile, _ = autotune.best_units(*args(), path=path)
+    assert tile == 8 | (2 << 8) | (1 << 16)
+    assert autotune.describe(tile) == {"units": 8, "blocks_per_sm": 2, "pairs": True}
+    assert json.load(open(path))["gpu|encode|8|800"]["pairs"] is True
+    calls.clear()
+    autotune.best_units("decode", *args()[1:], path=path)
+    assert len(calls) == 9 and not any(c >> 16 for c in calls)       # decode: no pair tables
+    calls.clear()
+    autotune.best_units("encode", *args(n=4)[1:5], [None, None, None], path=path)
+    assert len(calls) == 9 and not any(c >> 16 for c in calls)       # three alphabets: none
 
 
 def test_retune_and_other_keys(monkeypatch, tmp_path):
@@ -54,7 +75,7 @@ def test_retune_and_other_keys(monkeypatch, tmp_path):
     assert autotune.best_units(*args(), path=path)[0] == 2              # cached
     assert autotune.best_units(*args(), path=path, retune=True)[0] == 8 | (1 << 8)
     assert autotune.best_units(*args(n=16), path=path)[0] == 8 | (1 << 8)   # another batch size
-    assert len(json.load(open(path))) == 2 and len(calls) == 18
+    assert len(json.load(open(path))) == 2 and len(calls) == 24
 
 
 def test_damaged_cache_file(monkeypatch, tmp_path):

@@ -6,7 +6,7 @@ comparisons: the encode step without the 4096-entry pair table, the paper's
 (s2,s1,s3,s2) gather instead of the 24-bit form, the middle sextets taken on
 the FMA pipe, byte joins by multiply-add instead of byte permutes, other
 batch staging depths and register bounds, batch rounds that never mix
-strings or take one unit a lane, other unroll depths of the whole-tile loops, the MIME line path one group a lane, and other large-input
+strings or take one unit a lane, other unroll depths of the whole-tile loops, no pair-table encode tiles, the MIME line path one group a lane, and other large-input
 thresholds. This keeps them buildable so a
 comparison can be re-run with build(defines=...).
 """
@@ -26,6 +26,7 @@ VARIANTS = [
     ("b64_batch.cu", ("B64_BATCH_MIXED=0",)),
     ("b64_batch.cu", ("B64_BATCH_MIXED_UNITS=1",)),
     ("b64_batch.cu", ("B64_BATCH_DEC_WHOLE_UNROLL=8", "B64_BATCH_ENC_WHOLE_UNROLL=2")),
+    ("b64_batch.cu", ("B64_BATCH_ENC_PAIRS=0",)),
     ("b64_mime.cu", ("B64_MIME_UNITS=0",)),
 ]
 

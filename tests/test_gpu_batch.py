@@ -101,7 +101,10 @@ EDGE_LENGTHS = [0, 1, 2, 3, 4, 5, 0, 0, 383, 384, 385, 767, 768, 769, 1535, 1536
                 3071, 3072, 3073, 4096, 100_000, 0]
 
 
-@pytest.mark.parametrize("units", [1, 2, 4, 8])
+PAIRS = 1 << 16   # B64_TILE_PAIRS: encode's whole 8-unit tiles through pair tables
+
+
+@pytest.mark.parametrize("units", [1, 2, 4, 8, 8 | PAIRS])
 def test_batch_parity_all_tiles(b64, orc, tables, units):
     data, off, aid, padded = make_batch(orc, 1500, seed=20 + units, hi=1 << 17,
                                         extra_lengths=EDGE_LENGTHS)
@@ -117,7 +120,7 @@ def test_batch_parity_all_tiles(b64, orc, tables, units):
     check_decoded(dec, doff, dres, want_res, want_dec)
 
 
-@pytest.mark.parametrize("units", [1, 4])
+@pytest.mark.parametrize("units", [1, 4, 8 | PAIRS])
 def test_batch_parity_aligned_offsets(b64, orc, tables, units):
     """Output offsets with 16-byte aligned string starts (the kernels store
     such outputs straight from registers): every string equals the oracle's,
@@ -306,7 +309,8 @@ def test_batch_codec_graph_and_autotune_cache(b64, orc, tables, tmp_path):
     path = str(tmp_path / "autotune.json")
     args = (codec.src, codec.src_off, codec.dst, codec.dst_off, tables[0], codec.alph_id[:n])
     units, timings = autotune.best_units("encode", *args, path=path)
-    assert units in autotune.CHOICES and set(timings) == set(autotune.CHOICES)
+    choices = autotune.choices("encode", len(tables[0]))   # two alphabets: pair tables too
+    assert units in choices and set(timings) == set(choices) and len(choices) == 12
     again, t2 = autotune.best_units("encode", *args, path=path)
     assert again == units and t2 == {}          # served from the cache file
     codec.tile_units = units

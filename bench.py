@@ -50,7 +50,7 @@ def peaks() -> dict:
 # The source files each profiled kernel is built from.
 KERNEL_SOURCES = {
     "encode_tma_kernel": ("b64_encode.cu", "b64_device.cuh"),
-    "decode_body_kernel": ("b64_decode.cu", "b64_device.cuh"),
+    "decode_body_kernel": ("b64_decode.cu", "b64_device.cuh", "b64_internal.h"),
 }
 
 

@@ -145,7 +145,7 @@ def test_kernel_digest_ignores_comments_only(tmp_path, monkeypatch):
     src = os.path.join(ROOT, "paper_1910_05109_gb300", "csrc")
     dst = tmp_path / "paper_1910_05109_gb300" / "csrc"
     dst.mkdir(parents=True)
-    for name in ("b64_encode.cu", "b64_decode.cu", "b64_device.cuh"):
+    for name in ("b64_encode.cu", "b64_decode.cu", "b64_device.cuh", "b64_internal.h"):
         shutil.copy(os.path.join(src, name), dst / name)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     before = {k: bench.source_digest(k) for k in bench.KERNEL_SOURCES}

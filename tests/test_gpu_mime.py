@@ -282,3 +282,39 @@ def test_line_layout_whole_extra_line(b64, orc):
             assert check(b64, orc, t, std, chars, True) == data.size
         t = np.concatenate([good[:cut], good[cut + 78:]])       # one whole line less
         assert check(b64, orc, t, std, chars, True) == data.size - 57
+
+
+def test_call_recorded_in_a_cuda_graph(b64, orc):
+    """The call's launch chain (status kernel, then five programmatic
+    dependents) recorded once in a CUDA graph and replayed twice, on a
+    document whose line layout holds (the one-pass kernel decodes it) and on
+    one with a line a group longer part way (the counting kernels decode it
+    again), each replay against the oracle."""
+    std, chars = b64.Alphabet.standard(), orc.standard_alphabet()
+    good = wl.mime_wrap(orc.encode(wl.random_bytes(700_000, 780)))
+    lines = [good[k:k + 78] for k in range(0, good.size, 78)]
+    lines[2000] = np.concatenate([lines[2000][:76], np.frombuffer(b"QUJD", np.uint8),
+                                  lines[2000][76:]])
+    broken = np.concatenate(lines)
+    for text in (good, broken):
+        want_r, want = orc.decode(text, chars, True, mime=True)
+        src = torch.from_numpy(np.ascontiguousarray(text)).cuda()
+        cap = b64.decoded_max_length(text.size)
+        dst = torch.zeros(cap, dtype=torch.uint8, device="cuda")
+        res = torch.zeros(1, dtype=torch.int64, device="cuda")
+        ws = b64.mime_workspace(text.size)
+        s = torch.cuda.Stream()
+        b64.mime_decode_async(src, dst, res, std, ws, stream=s)   # first call sets up the kernels
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            b64.mime_decode_async(src, dst, res, std, ws, stream=s)
+        for _ in range(2):
+            dst.zero_()
+            res.fill_(-7)
+            torch.cuda.synchronize()
+            g.replay()
+            torch.cuda.synchronize()
+            assert int(res.item()) == want_r
+            if want_r >= 0:
+                assert np.array_equal(dst[:want_r].cpu().numpy(), want)

@@ -191,9 +191,12 @@ int b64_mime_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b6
  * b64_mime_batch_workspace_size(n, src_off[n] - src_off[0]) bytes, 8-byte
  * aligned; if the documents' total turns out larger than the size was
  * computed for, every results[i] becomes B64_E_INVAL and nothing else is
- * written. Five launches on `stream` (a memset, count, per-document scan,
- * decode, result), no waits between blocks. Returns B64_SUCCESS or an error
- * code; n == 0 enqueues nothing. */
+ * written. Seven launches on `stream`, no waits between blocks: a memset,
+ * per-document line layout, a one-pass decode of the documents laid out as
+ * lines (as b64_mime_decode_async decodes them, so the same note on bytes past
+ * the result holds), then count, per-document scan and decode for the others,
+ * and the results. Returns B64_SUCCESS or an error code; n == 0 enqueues
+ * nothing. */
 size_t b64_mime_batch_workspace_size(int64_t n, uint64_t total_bytes);
 
 int b64_mime_decode_batch(const uint8_t* src, const int64_t* src_off, int64_t n, uint8_t* dst,

@@ -1103,9 +1103,12 @@ __global__ void mime_finalize_kernel(const uint8_t* __restrict__ src, uint64_t m
 // slot ranges of consecutive documents never overlap (the next document's
 // first slot lies at least ceil(len / kSeg) further on), so no scan over the
 // documents is needed and a slot's document is found by a search. Launch
-// sequence: memset of the documents' status words, count (all segments), one
-// warp per document scanning its segments, decode (all segments), one thread
-// per document for the result. Documents start anywhere, so a segment is
+// sequence: memset of the documents' status words; one warp per document
+// detecting its line layout; the one-pass decode of the documents with one
+// (each segment with the count the layout gives it, a segment off the layout
+// marking its document); then, for the documents without a layout or marked,
+// count, one warp per document scanning its segments (and clearing its
+// status words), decode; one thread per document for the result. Documents start anywhere, so a segment is
 // staged by one bulk copy of the 16-byte aligned span around it (plain
 // aligned loads where that span would leave the batch's input) and read
 // through a funnel shift; the wait on each copy is bounded in time, and a
@@ -1178,10 +1181,22 @@ __device__ __forceinline__ uint64_t doc_slots(const int64_t* __restrict__ src_of
 // A warp's walk over its own contiguous range of slots [g0, g1): the
 // document of the last slot found is remembered, so the 32-way document
 // search runs once per document the range touches instead of once per slot.
+// status word 0 of a document whose bulk copy did not arrive (offsets are
+// below 2^62): its result becomes B64_E_TIMEOUT
+constexpr uint64_t kDocTimedOut = uint64_t(1) << 62;
+
+// Bit 32 of a document's line word (line_docs): its segments need the
+// counting passes (it has no line layout, or a segment broke it); bits 0..31:
+// the layout word.
+constexpr uint64_t kDocCounted = uint64_t(1) << 32;
+
 struct SlotWalk {
     uint64_t g, g1;
     int64_t d = -1;                  // the remembered document
     uint64_t first = 0, nseg = 0;    // its first slot and its segments
+    // with line_docs: only the documents whose kDocCounted bit equals counted
+    const unsigned long long* line_docs = nullptr;
+    bool counted = false;
     __device__ SlotWalk(uint64_t nslots, uint64_t warp, uint64_t warps) {
         const uint64_t per = (nslots + warps - 1) / warps;
         g = warp * per < nslots ? warp * per : nslots;
@@ -1198,6 +1213,8 @@ struct SlotWalk {
                 d = warp_find_doc(src_off, n, g, lane);
                 first = doc_slot(src_off, d);
                 nseg = (uint64_t(src_off[d + 1] - src_off[d]) + kSeg - 1) / kSeg;
+                if (line_docs && ((line_docs[d] & kDocCounted) != 0) != counted)
+                    nseg = 0;                     // not this pass's document: skip its slots
                 if (g >= first + nseg) continue;  // an unused slot
             }
             const uint64_t k = g - first;
@@ -1215,7 +1232,8 @@ struct SlotWalk {
 
 __global__ void __launch_bounds__(kCountThreads, 4)
     mime_count_docs_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
-                           int64_t n, unsigned long long* __restrict__ states, uint64_t slot_cap) {
+                           int64_t n, unsigned long long* __restrict__ states,
+                           const unsigned long long* __restrict__ line_docs, uint64_t slot_cap) {
     const int lane = threadIdx.x & 31;
     const uint64_t nslots = doc_slots(src_off, n);
     if (nslots > slot_cap) return;  // workspace too small: the results say so
@@ -1224,6 +1242,8 @@ __global__ void __launch_bounds__(kCountThreads, 4)
     const uint8_t* lo = src + src_off[0];
     const uint8_t* hi = src + src_off[n];
     SlotWalk walk(nslots, gw, GW);
+    walk.line_docs = line_docs;  // the documents the one-pass kernel left to this path
+    walk.counted = true;
     DocSeg ds;
     uint64_t g;
     while (walk.next(src, src_off, n, lane, &ds, &g)) {
@@ -1237,35 +1257,25 @@ __global__ void __launch_bounds__(kCountThreads, 4)
     }
 }
 
-// One warp per document: its segments' states become prefixes (data
-// characters and last data byte before the segment, within the document);
-// doc_state[d] = the whole document's.
+// One warp per document the counting passes decode (kDocCounted): its
+// segments' states become prefixes (data characters and last data byte before
+// the segment, within the document); doc_state[d] = the whole document's; its
+// status words, which the one-pass kernel may have set from layout counts,
+// return to "none" for the decode that follows.
 __global__ void __launch_bounds__(256)
     mime_scan_docs_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
                           int64_t n, unsigned long long* __restrict__ states,
                           unsigned long long* __restrict__ doc_state,
-                          unsigned long long* __restrict__ line_docs, uint64_t slot_cap) {
+                          const unsigned long long* __restrict__ line_docs,
+                          unsigned long long* __restrict__ status_docs, uint64_t slot_cap) {
     const int lane = threadIdx.x & 31;
     if (doc_slots(src_off, n) > slot_cap) return;
     const int64_t gw = (int64_t(blockIdx.x) * 256 + threadIdx.x) >> 5;
     const int64_t GW = (int64_t(gridDim.x) * 256) >> 5;
     for (int64_t d = gw; d < n; d += GW) {
-        {  // line_docs[d]: the line layout's L, as status[6] of the single-document call
-            const uint8_t* p = src + src_off[d];
-            const uint64_t len = uint64_t(src_off[d + 1] - src_off[d]);
-            uint32_t c[kScanThreads / 32];  // all loads issued before any is used
-#pragma unroll
-            for (int j = 0; j < kScanThreads / 32; ++j) {
-                const uint32_t i = uint32_t(lane) + 32 * j;
-                c[j] = i < len ? p[i] : 0u;
-            }
-            uint32_t f = kScanThreads;
-#pragma unroll
-            for (int j = kScanThreads / 32 - 1; j >= 0; --j)
-                if (c[j] == '\r' || c[j] == '\n' || c[j] == ' ') f = uint32_t(lane) + 32 * j;
-            f = __reduce_min_sync(0xffffffffu, f);
-            if (lane == 0) line_docs[d] = line_layout_word(p, len, f);
-        }
+        if (!(line_docs[d] & kDocCounted)) continue;
+        if (lane < 3 && status_docs[3 * d + lane] != kDocTimedOut)
+            status_docs[3 * d + lane] = ~0ull;
         const uint64_t first = doc_slot(src_off, d);
         const uint64_t segs = (uint64_t(src_off[d + 1] - src_off[d]) + kSeg - 1) / kSeg;
         uint64_t carry = 0, carry_key = 0;  // key: (segment + 1) << 8 | last byte
@@ -1296,11 +1306,51 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// One warp per document: its line layout (as the single-document call
+// detects it, from the first 1024 bytes) into line_docs[d], with kDocCounted
+// set when there is none; for a document with a layout, doc_state[d] = the
+// data characters and last data byte the layout gives (the finalize kernel's
+// figures if every segment keeps to it; the scan kernel replaces them
+// otherwise).
+__global__ void __launch_bounds__(256)
+    mime_layout_docs_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
+                            int64_t n, unsigned long long* __restrict__ line_docs,
+                            unsigned long long* __restrict__ doc_state, uint64_t slot_cap) {
+    const int lane = threadIdx.x & 31;
+    if (doc_slots(src_off, n) > slot_cap) return;
+    const int64_t gw = (int64_t(blockIdx.x) * 256 + threadIdx.x) >> 5;
+    const int64_t GW = (int64_t(gridDim.x) * 256) >> 5;
+    for (int64_t d = gw; d < n; d += GW) {
+        const uint8_t* p = src + src_off[d];
+        const uint64_t len = uint64_t(src_off[d + 1] - src_off[d]);
+        uint32_t c[kScanThreads / 32];  // all loads issued before any is used
+#pragma unroll
+        for (int j = 0; j < kScanThreads / 32; ++j) {
+            const uint32_t i = uint32_t(lane) + 32 * j;
+            c[j] = i < len ? p[i] : 0u;
+        }
+        uint32_t f = kScanThreads;
+#pragma unroll
+        for (int j = kScanThreads / 32 - 1; j >= 0; --j)
+            if (c[j] == '\r' || c[j] == '\n' || c[j] == ' ') f = uint32_t(lane) + 32 * j;
+        f = __reduce_min_sync(0xffffffffu, f);
+        if (lane == 0) {
+            const uint32_t word = line_layout_word(p, len, f);
+            line_docs[d] = word ? uint64_t(word) : kDocCounted;
+            if (word) {
+                const LineLayout ly{word};
+                const uint64_t k = len / ly.Q, r = len - k * ly.Q;
+                const uint64_t mc = k * ly.L + (r < ly.L ? r : ly.L);
+                const uint64_t j = mc - 1;
+                const uint32_t last = mc ? p[j / ly.L * ly.Q + j % ly.L] : 0u;
+                doc_state[d] = make_state(mc != 0, last, mc);
+            }
+        }
+    }
+}
+
 constexpr int kDocWarps = 4;
 constexpr uint32_t kStage = kSeg + 32;  // a segment's 16-byte aligned span
-// status word 0 of a document whose bulk copy did not arrive (offsets are
-// below 2^62): its result becomes B64_E_TIMEOUT
-constexpr uint64_t kDocTimedOut = uint64_t(1) << 62;
 
 // Starts the bulk copy of the 16-byte aligned span around a document
 // segment's bytes into stage (byte 0 of the segment lands at
@@ -1317,6 +1367,12 @@ __device__ __forceinline__ bool issue_doc_segment(uint8_t* stage, const DocSeg& 
     return true;
 }
 
+// kOnePass: the documents with a line layout (kDocCounted clear), every
+// segment decoded with the data count the layout gives it (as the
+// single-document one-pass kernel does); a segment off the layout sets its
+// document's kDocCounted. Otherwise: the kDocCounted documents, with the
+// counts of the count and scan kernels.
+template <bool kOnePass>
 __global__ void __launch_bounds__(32 * kDocWarps, 5)
     mime_decode_docs_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
                             int64_t n, uint8_t* __restrict__ dst,
@@ -1324,7 +1380,7 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
                             const __grid_constant__ BatchTables tabs,
                             const uint8_t* __restrict__ alph_id,
                             unsigned long long* __restrict__ status_docs,
-                            const unsigned long long* __restrict__ line_docs,
+                            unsigned long long* __restrict__ line_docs,
                             const unsigned long long* __restrict__ states, uint64_t slot_cap) {
     __shared__ __align__(256) uint8_t luts[kMaxAlphabets][256];  // 0..63, 0x80, kSpace
     __shared__ __align__(16) uint8_t bufs[kDocWarps][kBuf];
@@ -1348,6 +1404,8 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
     const uint64_t GW = uint64_t(gridDim.x) * kDocWarps;
 
     SlotWalk walk(nslots, uint64_t(blockIdx.x) * kDocWarps + warp, GW);
+    walk.line_docs = line_docs;
+    walk.counted = !kOnePass;
     // Slot g's segment arrives in the warp's stage buffer by a bulk copy
     // started while the slot before it is decoded, and is re-aligned into
     // buf; then the next slot's copy is started.
@@ -1357,6 +1415,37 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
     uint8_t* stg = stages[warp];
     if (have && lane == 0) by_copy = issue_doc_segment(stg, ds, lo, hi, &bars[warp]);
     by_copy = __shfl_sync(0xffffffffu, by_copy, 0);
+    // A slot's document metadata (alphabet, layout word, output offset; the
+    // one-pass kernel's data byte before the segment, the other's segment
+    // state), loaded with the slot's copy so the loads overlap the slot
+    // before it.
+    struct SegMeta {
+        uint64_t pre;
+        int64_t out;
+        uint32_t word, prev;
+        int a;
+    };
+    auto fetch = [&](const DocSeg& d, uint64_t slot) {
+        SegMeta m;
+        m.a = alph_id ? (alph_id[d.d] & (kMaxAlphabets - 1)) : 0;
+        m.word = uint32_t(line_docs[d.d]);
+        m.out = dst_off[d.d];
+        m.pre = 0;
+        m.prev = 0;
+        if constexpr (kOnePass) {
+            const LineLayout ly{m.word};
+            const uint64_t S = d.k * kSeg, lk = S / ly.Q;
+            const uint32_t lr = uint32_t(S - lk * ly.Q);
+            const uint64_t P = lk * ly.L + (lr < ly.L ? lr : ly.L);
+            const uint64_t j = P - 1;
+            if (P) m.prev = (d.p - S)[j / ly.L * ly.Q + j % ly.L];
+        } else {
+            m.pre = states[slot];
+        }
+        return m;
+    };
+    SegMeta meta{};
+    if (have) meta = fetch(ds, g);
     uint32_t phase = 0;
     while (have) {
         unsigned long long* st3 = status_docs + 3 * ds.d;
@@ -1410,27 +1499,50 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
         bool by_copy2 = false;
         if (have2 && lane == 0) by_copy2 = issue_doc_segment(stg, ds2, lo, hi, &bars[warp]);
         by_copy2 = __shfl_sync(0xffffffffu, by_copy2, 0);
-        const uint64_t pre = states[g];
-        const int a = alph_id ? (alph_id[ds.d] & (kMaxAlphabets - 1)) : 0;
+        SegMeta meta2{};
+        if (have2) meta2 = fetch(ds2, g2);
+        const int a = meta.a;
         const int flags = (tabs.padded[a] ? 1 : 0) | (tabs.canonical[a] ? 2 : 0);
-        const uint64_t P = st_count(pre);
-        const uint32_t prev_last = st_flag(pre) ? st_last(pre) : 0u;
-        const LineLayout ly{uint32_t(line_docs[ds.d])};
-        LinesResult fast = kLinesNo;
-        if (ly.L && ds.len == kSeg) {
-            const uint64_t S = ds.k * kSeg, lk = S / ly.Q;
-            fast = decode_segment_lines(buf, luts[a], lane, ly, lk, uint32_t(S - lk * ly.Q), P,
-                                        prev_last, dst + dst_off[ds.d]);
+        const LineLayout ly{meta.word};
+        const uint64_t S = ds.k * kSeg, lk = ly.L ? S / ly.Q : 0;
+        const uint32_t lr = uint32_t(S - lk * ly.Q);
+        uint8_t* const out_doc = dst + meta.out;
+        if constexpr (kOnePass) {
+            // the layout's count before the segment, and its last data byte
+            const uint64_t P = lk * ly.L + (lr < ly.L ? lr : ly.L);
+            const uint32_t prev_last = meta.prev;
+            bool irregular = false;
+            if (ds.len == kSeg) {
+                const LinesResult r = decode_segment_lines(buf, luts[a], lane, ly, lk, lr, P,
+                                                           prev_last, out_doc);
+                irregular = r == kLinesIrregular || r == kLinesNo;
+                if (r == kLinesSpoilt) {  // bad bytes or '=': the general path, same P
+                    stage_plain();
+                    decode_segment(buf, luts[a], flags, lane, P, prev_last, S, out_doc, st3);
+                }
+            } else {
+                irregular = !segment_fits_layout(buf + kLead, ds.len, ly, lr, lane);
+                if (!irregular)
+                    decode_segment(buf, luts[a], flags, lane, P, prev_last, S, out_doc, st3);
+            }
+            if (irregular && lane == 0) atomicOr(&line_docs[ds.d], (unsigned long long)kDocCounted);
+        } else {
+            const uint64_t pre = meta.pre;
+            const uint64_t P = st_count(pre);
+            const uint32_t prev_last = st_flag(pre) ? st_last(pre) : 0u;
+            LinesResult fast = kLinesNo;
+            if (ly.L && ds.len == kSeg)
+                fast = decode_segment_lines(buf, luts[a], lane, ly, lk, lr, P, prev_last, out_doc);
+            if (fast == kLinesSpoilt || fast == kLinesIrregular) stage_plain();
+            if (fast != kLinesDone)
+                decode_segment(buf, luts[a], flags, lane, P, prev_last, S, out_doc, st3);
         }
-        if (fast == kLinesSpoilt || fast == kLinesIrregular) stage_plain();
-        if (fast != kLinesDone)
-            decode_segment(buf, luts[a], flags, lane, P, prev_last, ds.k * kSeg,
-                           dst + dst_off[ds.d], st3);
         __syncwarp();  // the buffer is restaged for the next segment
         g = g2;
         ds = ds2;
         have = have2;
         by_copy = by_copy2;
+        meta = meta2;
     }
 }
 
@@ -1477,7 +1589,7 @@ struct Occ {
     std::once_flag once;
     int ctas = 1;
 };
-Occ g_occ[64], g_op_occ[64], g_cd_occ[64], g_dd_occ[64];
+Occ g_occ[64], g_op_occ[64], g_cd_occ[64], g_dd_occ[64], g_ddo_occ[64];
 
 template <class K>
 int occupancy(K kernel, int threads, Occ& occ) {
@@ -1571,19 +1683,31 @@ cudaError_t launch_mime_decode_batch(const BatchArgs& a, const BatchTables& tabs
     cudaError_t e = cudaMemsetAsync(status_docs, 0xFF, 3 * size_t(a.n) * sizeof(uint64_t), st);
     if (e != cudaSuccess) return e;
     const DeviceInfo& di = device_info();
-    const int cd = occupancy(mime_count_docs_kernel, kCountThreads, g_cd_occ[di.device & 63]);
-    mime_count_docs_kernel<<<unsigned(di.sm_count * cd), kCountThreads, 0, st>>>(
-        a.src, a.src_off, a.n, states, slot_cap);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     const uint64_t scan_blocks = (uint64_t(a.n) + 7) / 8;
     const unsigned sb = unsigned(scan_blocks < uint64_t(di.sm_count) * 8 ? scan_blocks : di.sm_count * 8);
-    mime_scan_docs_kernel<<<sb, 256, 0, st>>>(a.src, a.src_off, a.n, states, doc_state, line_docs,
-                                              slot_cap);
+    // one pass for the documents with a line layout, then the counting passes
+    // for the others (each kernel skips the documents it is not for)
+    mime_layout_docs_kernel<<<sb, 256, 0, st>>>(a.src, a.src_off, a.n, line_docs, doc_state,
+                                                slot_cap);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int dd = occupancy(mime_decode_docs_kernel, 32 * kDocWarps, g_dd_occ[di.device & 63]);
-    mime_decode_docs_kernel<<<unsigned(di.sm_count * dd), 32 * kDocWarps, 0, st>>>(
+    const int ddo = occupancy(mime_decode_docs_kernel<true>, 32 * kDocWarps, g_ddo_occ[di.device & 63]);
+    mime_decode_docs_kernel<true><<<unsigned(di.sm_count * ddo), 32 * kDocWarps, 0, st>>>(
+        a.src, a.src_off, a.n, a.dst, a.dst_off, tabs, a.alph_id, status_docs, line_docs, states,
+        slot_cap);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int cd = occupancy(mime_count_docs_kernel, kCountThreads, g_cd_occ[di.device & 63]);
+    mime_count_docs_kernel<<<unsigned(di.sm_count * cd), kCountThreads, 0, st>>>(
+        a.src, a.src_off, a.n, states, line_docs, slot_cap);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    mime_scan_docs_kernel<<<sb, 256, 0, st>>>(a.src, a.src_off, a.n, states, doc_state, line_docs,
+                                              status_docs, slot_cap);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int dd = occupancy(mime_decode_docs_kernel<false>, 32 * kDocWarps, g_dd_occ[di.device & 63]);
+    mime_decode_docs_kernel<false><<<unsigned(di.sm_count * dd), 32 * kDocWarps, 0, st>>>(
         a.src, a.src_off, a.n, a.dst, a.dst_off, tabs, a.alph_id, status_docs, line_docs, states,
         slot_cap);
     e = cudaGetLastError();

@@ -7,8 +7,10 @@ Each warp walks its own equal, contiguous range of slots, skipping slots no
 document uses and finding a slot's document by a search that it repeats only
 when the walk leaves the remembered document. Restated here in Python and
 run over batches with empty, tiny and multi-segment documents: the slot
-ranges of the documents never overlap and fit the workspace, and the walks
-of all warps visit every (document, segment) exactly once.
+ranges of the documents never overlap and fit the workspace, the walks of
+all warps visit every (document, segment) exactly once, and the one-pass and
+counting passes, each walking only its own documents, split them between
+them.
 """
 import bisect
 
@@ -36,7 +38,9 @@ def find_doc(src_off, n, g):
     return bisect.bisect_right(slots, g) - 1
 
 
-def walk(src_off, n, warp, warps):
+def walk(src_off, n, warp, warps, counted_of=None, counted=False):
+    """counted_of: a pass's filter (the kernel's kDocCounted bit per
+    document); only the documents whose bit equals `counted` are walked."""
     nslots = doc_slots(src_off, n)
     per = (nslots + warps - 1) // warps
     g = min(warp * per, nslots)
@@ -50,6 +54,8 @@ def walk(src_off, n, warp, warps):
                 continue
             d = find_doc(src_off, n, g)
             first, ns = doc_slot(src_off, d), nseg(src_off, d)
+            if counted_of is not None and counted_of[d] != counted:
+                ns = 0                  # not this pass's document: skip its slots
             if g >= first + ns:
                 g += 1
                 continue
@@ -102,4 +108,23 @@ def test_warp_walks_visit_every_segment_once(seed, count, origin):
             for d, k, g in walk(src_off, n, w, warps):
                 assert g == doc_slot(src_off, d) + k
                 seen.append((d, k))
+        assert len(seen) == len(set(seen)) and set(seen) == want, warps
+
+
+@pytest.mark.parametrize("seed,count,origin", [(2, 7, 5), (3, 200, 0), (5, 300, 1 << 20)])
+def test_the_two_passes_split_the_documents(seed, count, origin):
+    """The one-pass walk (documents with a line layout) and the counting
+    passes' walk (the others) together visit every segment exactly once, and
+    each only its own documents' segments."""
+    src_off = batch(seed, count, origin)
+    n = len(src_off) - 1
+    counted_of = [bool(b) for b in np.random.default_rng(seed + 9).random(n) < 0.3]
+    want = {(d, k) for d in range(n) for k in range(nseg(src_off, d))}
+    for warps in (1, 5, 32, 1216):
+        seen = []
+        for counted in (False, True):
+            for w in range(warps):
+                for d, k, g in walk(src_off, n, w, warps, counted_of, counted):
+                    assert counted_of[d] == counted and g == doc_slot(src_off, d) + k
+                    seen.append((d, k))
         assert len(seen) == len(set(seen)) and set(seen) == want, warps

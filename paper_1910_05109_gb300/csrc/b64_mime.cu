@@ -1008,19 +1008,21 @@ __global__ void __launch_bounds__(kThreads, 6)
         const uint64_t P = lk * ly.L + (lr < ly.L ? lr : ly.L);
         const uint32_t back = lr == 0 ? 1 + ly.eol : lr > ly.L ? lr - ly.L + 1 : 1u;
         const uint32_t prev_last = P ? buf[kLead - back] : 0u;
-        bool irregular = false;
+        bool irregular = false, general = false;
         if (len == kSeg) {
             const LinesResult r =
                 decode_segment_lines(buf, lut, lane, ly, lk, lr, P, prev_last, dst);
             irregular = r == kLinesIrregular || r == kLinesNo;
             if (r == kLinesSpoilt) {  // bad bytes or '=': the general path, same P
                 stage_plain(buf, base, len, false);
-                decode_segment(buf, lut, flags, lane, P, prev_last, base, dst, status);
+                general = true;
             }
         } else {
             irregular = !segment_fits_layout(buf + kLead, len, ly, lr, lane);
-            if (!irregular) decode_segment(buf, lut, flags, lane, P, prev_last, base, dst, status);
+            general = !irregular;
         }
+        // one call site, so the kernel holds one copy of the general path
+        if (general) decode_segment(buf, lut, flags, lane, P, prev_last, base, dst, status);
         if (irregular && lane == 0) atomicMin(status + 7, (unsigned long long)seg);
         lk += dk;
         lr += dr;
@@ -1511,20 +1513,21 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
             // the layout's count before the segment, and its last data byte
             const uint64_t P = lk * ly.L + (lr < ly.L ? lr : ly.L);
             const uint32_t prev_last = meta.prev;
-            bool irregular = false;
+            bool irregular = false, general = false;
             if (ds.len == kSeg) {
                 const LinesResult r = decode_segment_lines(buf, luts[a], lane, ly, lk, lr, P,
                                                            prev_last, out_doc);
                 irregular = r == kLinesIrregular || r == kLinesNo;
                 if (r == kLinesSpoilt) {  // bad bytes or '=': the general path, same P
                     stage_plain();
-                    decode_segment(buf, luts[a], flags, lane, P, prev_last, S, out_doc, st3);
+                    general = true;
                 }
             } else {
                 irregular = !segment_fits_layout(buf + kLead, ds.len, ly, lr, lane);
-                if (!irregular)
-                    decode_segment(buf, luts[a], flags, lane, P, prev_last, S, out_doc, st3);
+                general = !irregular;
             }
+            // one call site, so the kernel holds one copy of the general path
+            if (general) decode_segment(buf, luts[a], flags, lane, P, prev_last, S, out_doc, st3);
             if (irregular && lane == 0) atomicOr(&line_docs[ds.d], (unsigned long long)kDocCounted);
         } else {
             const uint64_t pre = meta.pre;

@@ -553,7 +553,10 @@ __device__ __forceinline__ void copy_out(const uint8_t* buf, uint32_t skip, uint
 // written to global memory, but the staged bytes are spoilt and the caller
 // stages the segment again for the general path (which also finds the
 // segment's errors). S: the segment's raw start in the document; P: the data
-// characters before it; prev_last: the last data byte before it.
+// characters before it; prev_last: the last data byte before it; delta: the
+// segment's first byte sits at buf + kLead + delta (0 to 15; nonzero only for
+// L >= 16, and even for CR LF breaks, so that a unit's three 8-byte loads
+// still hold its bytes and the break's).
 enum LinesResult { kLinesNo, kLinesDone, kLinesSpoilt, kLinesIrregular };
 
 // The line layout's constants (L = 0: the input does not start with it).
@@ -580,8 +583,10 @@ struct LineLayout {
 template <bool kCrLf>
 __device__ LinesResult decode_lines(uint8_t* buf, const uint8_t* lut, int lane,
                                     const LineLayout& ly, uint64_t k, uint32_t r, uint64_t P,
-                                    uint32_t prev_last, uint8_t* __restrict__ out_doc) {
+                                    uint32_t prev_last, uint8_t* __restrict__ out_doc,
+                                    uint32_t delta) {
     const uint32_t L = ly.L, Q = ly.Q, eol = kCrLf ? 2u : 1u;
+    if (delta && (L < 16 || (kCrLf && (delta & 1u)))) return kLinesNo;  // not for this path
     // data characters before S, and before the segment's end, in the layout
     if (k * L + (r < L ? r : L) != P) return kLinesNo;  // it does not hold up to here
     uint64_t k1 = k + ly.seg_q;
@@ -592,10 +597,10 @@ __device__ LinesResult decode_lines(uint8_t* buf, const uint8_t* lut, int lane,
     }
     const uint64_t P1 = k1 * L + (r1 < L ? r1 : L);
     const uint8_t* raw = buf + kLead;
-    // raw offset in the segment of data character P + d (d < 4096 + L): the
+    // raw offset from buf + kLead of data character P + d (d < 4096 + L): the
     // column of P in its line, and the raw offset of that line's start
     const uint32_t rP = r < L ? r : 0;
-    const int32_t off0 = r < L ? -int32_t(r) : int32_t(Q - r);
+    const int32_t off0 = (r < L ? -int32_t(r) : int32_t(Q - r)) + int32_t(delta);
     auto raw_of = [&](uint32_t d) -> uint32_t {
         const uint32_t t = rP + d, line = __umulhi(t, ly.inv);
         return uint32_t(off0) + line * eol + t;  // line Q + (t - line L)
@@ -605,10 +610,11 @@ __device__ LinesResult decode_lines(uint8_t* buf, const uint8_t* lut, int lane,
     uint32_t bad = 0, viol = 0;
     // the skipped bytes: break j at raw offsets L - r + j Q (and one more
     // for CR LF)
+    const uint8_t* seg = raw + delta;
     for (int32_t rel = int32_t(L) - int32_t(r) + lane * int32_t(Q); rel < int32_t(kSeg);
          rel += 32 * int32_t(Q)) {
-        if (rel >= 0 && lut[raw[rel]] != kSpace) viol = 1u;
-        if (kCrLf && rel + 1 >= 0 && rel + 1 < int32_t(kSeg) && lut[raw[rel + 1]] != kSpace)
+        if (rel >= 0 && lut[seg[rel]] != kSpace) viol = 1u;
+        if (kCrLf && rel + 1 >= 0 && rel + 1 < int32_t(kSeg) && lut[seg[rel + 1]] != kSpace)
             viol = 1u;
     }
     // groups: the one holding P (edge A: it started before the segment), the
@@ -757,9 +763,11 @@ __device__ __forceinline__ LinesResult decode_segment_lines(uint8_t* buf, const 
                                                             int lane, const LineLayout& ly,
                                                             uint64_t k, uint32_t r, uint64_t P,
                                                             uint32_t prev_last,
-                                                            uint8_t* __restrict__ out_doc) {
-    return ly.eol == 2 ? decode_lines<true>(buf, lut, lane, ly, k, r, P, prev_last, out_doc)
-                       : decode_lines<false>(buf, lut, lane, ly, k, r, P, prev_last, out_doc);
+                                                            uint8_t* __restrict__ out_doc,
+                                                            uint32_t delta = 0) {
+    return ly.eol == 2
+               ? decode_lines<true>(buf, lut, lane, ly, k, r, P, prev_last, out_doc, delta)
+               : decode_lines<false>(buf, lut, lane, ly, k, r, P, prev_last, out_doc, delta);
 }
 
 __global__ void __launch_bounds__(kThreads, 6)
@@ -1352,7 +1360,14 @@ __global__ void __launch_bounds__(256)
 }
 
 constexpr int kDocWarps = 4;
-constexpr uint32_t kStage = kSeg + 32;  // a segment's 16-byte aligned span
+// a segment's 16-byte aligned span (at most kSeg + 32 bytes) fits a buffer after its lead
+static_assert(kLead + kSeg + 32 <= kBuf, "document staging");
+
+// A segment's raw start S in its document's line layout as line * Q +
+// column: the line, by a 32-bit division where S < 2^32.
+__device__ __forceinline__ uint64_t line_of(uint64_t S, uint32_t Q) {
+    return (S >> 32) ? S / Q : uint64_t(uint32_t(S) / Q);
+}
 
 // Starts the bulk copy of the 16-byte aligned span around a document
 // segment's bytes into stage (byte 0 of the segment lands at
@@ -1385,8 +1400,7 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
                             unsigned long long* __restrict__ line_docs,
                             const unsigned long long* __restrict__ states, uint64_t slot_cap) {
     __shared__ __align__(256) uint8_t luts[kMaxAlphabets][256];  // 0..63, 0x80, kSpace
-    __shared__ __align__(16) uint8_t bufs[kDocWarps][kBuf];
-    __shared__ __align__(16) uint8_t stages[kDocWarps][kStage];
+    __shared__ __align__(16) uint8_t bufs[kDocWarps][2][kBuf];
     __shared__ uint64_t bars[kDocWarps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < kMaxAlphabets * 64; i += 32 * kDocWarps)
@@ -1402,20 +1416,21 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
     if (nslots > slot_cap) return;
     const uint8_t* lo = src + src_off[0];
     const uint8_t* hi = src + src_off[n];
-    uint8_t* buf = bufs[warp];
     const uint64_t GW = uint64_t(gridDim.x) * kDocWarps;
 
     SlotWalk walk(nslots, uint64_t(blockIdx.x) * kDocWarps + warp, GW);
     walk.line_docs = line_docs;
     walk.counted = !kOnePass;
-    // Slot g's segment arrives in the warp's stage buffer by a bulk copy
-    // started while the slot before it is decoded, and is re-aligned into
-    // buf; then the next slot's copy is started.
+    // Slot g's segment arrives in one of the warp's two buffers by a bulk copy
+    // of its aligned span (segment byte i at buf[kLead + (p & 15) + i]),
+    // started while the slot before it is decoded in the other buffer. The
+    // line path decodes it there; otherwise it is first moved down to
+    // buf + kLead.
     uint64_t g = 0;
     DocSeg ds;
     bool have = walk.next(src, src_off, n, lane, &ds, &g), by_copy = false;
-    uint8_t* stg = stages[warp];
-    if (have && lane == 0) by_copy = issue_doc_segment(stg, ds, lo, hi, &bars[warp]);
+    int kb = 0;  // the buffer of slot g
+    if (have && lane == 0) by_copy = issue_doc_segment(bufs[warp][0] + kLead, ds, lo, hi, &bars[warp]);
     by_copy = __shfl_sync(0xffffffffu, by_copy, 0);
     // A slot's document metadata (alphabet, layout word, output offset; the
     // one-pass kernel's data byte before the segment, the other's segment
@@ -1435,12 +1450,17 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
         m.pre = 0;
         m.prev = 0;
         if constexpr (kOnePass) {
-            const LineLayout ly{m.word};
-            const uint64_t S = d.k * kSeg, lk = S / ly.Q;
-            const uint32_t lr = uint32_t(S - lk * ly.Q);
-            const uint64_t P = lk * ly.L + (lr < ly.L ? lr : ly.L);
-            const uint64_t j = P - 1;
-            if (P) m.prev = (d.p - S)[j / ly.L * ly.Q + j % ly.L];
+            // the data byte before the segment (every segment but a
+            // document's first has one): the byte before it, or the last
+            // before the break where the segment starts a line or inside
+            // the break
+            const uint32_t L = m.word & 0xFFFFu, eol = m.word >> 16, Q = L + eol;
+            if (d.k && L) {
+                const uint64_t S = d.k * kSeg;
+                const uint32_t lr = uint32_t(S - line_of(S, Q) * Q);
+                const uint32_t back = lr == 0 ? 1 + eol : lr > L ? lr - L + 1 : 1u;
+                m.prev = d.p[-int64_t(back)];
+            }
         } else {
             m.pre = states[slot];
         }
@@ -1451,6 +1471,8 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
     uint32_t phase = 0;
     while (have) {
         unsigned long long* st3 = status_docs + 3 * ds.d;
+        uint8_t* const buf = bufs[warp][kb];
+        const LineLayout ly{meta.word};
         auto stage_plain = [&] {
 #pragma unroll
             for (int r = 0; r < kRows; ++r) {
@@ -1460,6 +1482,7 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
             }
             __syncwarp();
         };
+        uint32_t delta = 0;  // the segment's first byte is at buf[kLead + delta]
         if (by_copy) {
             const bool ok = __all_sync(0xffffffffu, wait_copy(&bars[warp], phase, kWaitLimitNs));
             phase ^= 1u;
@@ -1473,40 +1496,49 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
                 }
                 return;
             }
-            // re-align: segment byte i is at stg[(p & 15) + i]; bytes at or
-            // past len read as spaces
-            const uint32_t delta = uint32_t(reinterpret_cast<uintptr_t>(ds.p) & 15);
+            const uint32_t pd = uint32_t(reinterpret_cast<uintptr_t>(ds.p) & 15);
+            if (ds.len == kSeg && ly.L >= 16 && (ly.eol == 1 || (pd & 1u) == 0)) {
+                delta = pd;  // the line path reads the segment where it landed
+            } else if (pd || ds.len < kSeg) {
+                // moved down by pd, a row at a time (a row's reads reach 16
+                // bytes into the next lane's row part, so all come before its
+                // writes; the next row's reads start past them); bytes at or
+                // past len read as spaces
+                uint8_t* const raw = buf + kLead;
 #pragma unroll
-            for (int r = 0; r < kRows; ++r) {
-                const uint32_t off = kRow * r + 16 * lane;
-                uint4 v;
-                if (off + 16 <= ds.len) {
-                    v = load16_shifted_u(stg, delta + off);
-                } else {
-                    uint8_t* bv = reinterpret_cast<uint8_t*>(&v);
-                    for (int j = 0; j < 16; ++j)
-                        bv[j] = off + j < ds.len ? stg[delta + off + j] : uint8_t(' ');
+                for (int r = 0; r < kRows; ++r) {
+                    const uint32_t off = kRow * r + 16 * lane;
+                    uint4 v;
+                    if (off + 16 <= ds.len) {
+                        v = load16_shifted_u(raw, pd + off);
+                    } else {
+                        uint8_t* bv = reinterpret_cast<uint8_t*>(&v);
+                        for (int j = 0; j < 16; ++j)
+                            bv[j] = off + j < ds.len ? raw[pd + off + j] : uint8_t(' ');
+                    }
+                    __syncwarp();
+                    *reinterpret_cast<uint4*>(raw + off) = v;
                 }
-                *reinterpret_cast<uint4*>(buf + kLead + off) = v;
             }
         } else {
             stage_plain();
         }
-        // the stage buffer is read; the next slot's copy may overwrite it
+        // this lane's accesses to the other buffer (the slot before) come
+        // before the next slot's copy into it
         fence_proxy_async_smem();
         __syncwarp();
         uint64_t g2 = 0;
         DocSeg ds2;
         const bool have2 = walk.next(src, src_off, n, lane, &ds2, &g2);
         bool by_copy2 = false;
-        if (have2 && lane == 0) by_copy2 = issue_doc_segment(stg, ds2, lo, hi, &bars[warp]);
+        if (have2 && lane == 0)
+            by_copy2 = issue_doc_segment(bufs[warp][kb ^ 1] + kLead, ds2, lo, hi, &bars[warp]);
         by_copy2 = __shfl_sync(0xffffffffu, by_copy2, 0);
         SegMeta meta2{};
         if (have2) meta2 = fetch(ds2, g2);
         const int a = meta.a;
         const int flags = (tabs.padded[a] ? 1 : 0) | (tabs.canonical[a] ? 2 : 0);
-        const LineLayout ly{meta.word};
-        const uint64_t S = ds.k * kSeg, lk = ly.L ? S / ly.Q : 0;
+        const uint64_t S = ds.k * kSeg, lk = ly.L ? line_of(S, ly.Q) : 0;
         const uint32_t lr = uint32_t(S - lk * ly.Q);
         uint8_t* const out_doc = dst + meta.out;
         if constexpr (kOnePass) {
@@ -1516,7 +1548,7 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
             bool irregular = false, general = false;
             if (ds.len == kSeg) {
                 const LinesResult r = decode_segment_lines(buf, luts[a], lane, ly, lk, lr, P,
-                                                           prev_last, out_doc);
+                                                           prev_last, out_doc, delta);
                 irregular = r == kLinesIrregular || r == kLinesNo;
                 if (r == kLinesSpoilt) {  // bad bytes or '=': the general path, same P
                     stage_plain();
@@ -1535,12 +1567,16 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
             const uint32_t prev_last = st_flag(pre) ? st_last(pre) : 0u;
             LinesResult fast = kLinesNo;
             if (ly.L && ds.len == kSeg)
-                fast = decode_segment_lines(buf, luts[a], lane, ly, lk, lr, P, prev_last, out_doc);
-            if (fast == kLinesSpoilt || fast == kLinesIrregular) stage_plain();
+                fast = decode_segment_lines(buf, luts[a], lane, ly, lk, lr, P, prev_last, out_doc,
+                                            delta);
+            // the general path reads the segment at buf + kLead
+            if (fast == kLinesSpoilt || fast == kLinesIrregular || (fast == kLinesNo && delta))
+                stage_plain();
             if (fast != kLinesDone)
                 decode_segment(buf, luts[a], flags, lane, P, prev_last, S, out_doc, st3);
         }
-        __syncwarp();  // the buffer is restaged for the next segment
+        __syncwarp();
+        kb ^= 1;
         g = g2;
         ds = ds2;
         have = have2;

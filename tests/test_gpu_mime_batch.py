@@ -153,14 +153,17 @@ def test_small_workspace_and_empty_batch(b64, orc):
 
 
 def test_line_layout_documents(b64, orc):
-    """Documents in the line layout (L = 64 or 76, CR LF) over several
+    """Documents in the line layout (L from 4 to 1020, CR LF) over several
     segments, next to broken ones (a CR turned into data, a bad byte, a line
-    one group longer, LF-only breaks), at odd offsets in the batch."""
+    one group longer, LF-only breaks), at odd and even offsets in the batch
+    (the line path reads a segment where its copy put it for L >= 16 and, with
+    CR LF, an even offset; other segments are moved first)."""
     std, chars = b64.Alphabet.standard(), orc.standard_alphabet()
     g = wl.rng(31)
     docs = []
+    widths = (76, 64, 16, 20, 8, 1020, 76, 64, 36, 4)
     for i in range(60):
-        L = 64 if i % 2 else 76
+        L = widths[i // 6]
         n = int(g.integers(3 * TILE, 40_000))
         t = wl.mime_wrap(orc.encode(wl.random_bytes(n, 9000 + i)), line=L)
         kind = i % 6

@@ -14,9 +14,15 @@ lane decodes a unit of four whole groups (16 data characters) from three
 8-byte loads at its raw offset rounded down to 8, taking each word either at
 that offset or, past the one line break the unit can cross, e bytes further
 on (that word shifted by e bytes into the next one, the next one past the 16
-bytes being the low bytes of the last loaded word). These are restated here with numpy and compared with the layout's
-definition over many segments of every accepted layout. The GPU tests run
-the kernel itself on L = 4, 64, 76 and 1020.
+bytes being the low bytes of the last loaded word). A segment of a batched
+document may sit delta bytes (0 to 15) past the staging buffer's start, where
+its bulk copy put it: the unit path then reads it there (L >= 16, delta even
+for CR LF) with delta added to the line start's offset. The data byte before
+a segment is found by stepping back over the break from its start. These are
+restated here with numpy and compared with the layout's definition over many
+segments of every accepted layout. The GPU tests run the kernel itself on
+L = 4, 64, 76 and 1020, and batched documents of several line lengths at
+arbitrary starts.
 """
 import numpy as np
 
@@ -88,9 +94,9 @@ def test_units_of_four_groups_take_their_characters_from_the_loaded_words():
     bytes are exactly the raw positions of its data characters. Each round of
     32 units writes its 12 output bytes a unit (at 12 i) below every load of
     the next round, and no load leaves the staging buffer."""
-    for L, e in LAYOUTS:
-        if L < 16:
-            continue
+    for n, (L, e) in enumerate(le for le in LAYOUTS if le[0] >= 16):
+        # a batched document's segment: delta bytes into the buffer, even for CR LF
+        delta = n % 16 if e == 1 else 2 * (n % 8)
         Q = L + e
         inv = 0xFFFFFFFF // L + 1
         for s in range(0, 24 * K_SEG, K_SEG):
@@ -99,7 +105,7 @@ def test_units_of_four_groups_take_their_characters_from_the_loaded_words():
             k1, r1 = divmod(s + K_SEG, Q)
             P1 = k1 * L + min(r1, L)
             rP = r if r < L else 0
-            off0 = -r if r < L else Q - r
+            off0 = (-r if r < L else Q - r) + delta
             cA = (4 - P % 4) % 4
             nfull = (P1 - P - cA) // 4
             nunits = (nfull + 3) // 4
@@ -113,15 +119,33 @@ def test_units_of_four_groups_take_their_characters_from_the_loaded_words():
             A, sh = ro & ~7, ro & 7
             assert np.all(sh + e <= 8)          # the shifted words' bytes stay in the 24 loaded
             assert np.all((sh & 3) + e <= 4)    # and the word past the 16 needs only its low word
-            assert np.all(A + 24 <= K_SEG + 48)  # the staging buffer's slack
+            assert np.all(A >= 0) and np.all(A + 24 <= K_SEG + 48)  # inside the buffer
             tb = L - col
             b = np.arange(16, dtype=np.int64)
             got = ro[:, None] + b[None, :] + np.where(b[None, :] >= tb[:, None], e, 0)
             j = P + cA + 16 * i[:, None] + b[None, :]
-            want = Q * (j // L) + j % L - s
+            want = Q * (j // L) + j % L - s + delta
             used = b[None, :] < 4 * ng[:, None]
-            assert np.array_equal(got[used], want[used]), (L, e, s)
-            assert np.all(want[used] < K_SEG)   # whole groups inside the segment
+            assert np.array_equal(got[used], want[used]), (L, e, s, delta)
+            assert np.all(want[used] < K_SEG + delta)  # whole groups inside the segment
             for r0 in range(0, nunits - 32, 32):
                 wr_end = 12 * (r0 + 32)
                 assert wr_end <= A[r0 + 32:r0 + 64].min(), (L, e, s, r0)
+
+
+def test_data_byte_before_a_segment_by_stepping_back():
+    """The data byte before a document's segment k > 0 (raw start S = 4096 k
+    = line Q + column): one byte back, or 1 + e back where S starts a line,
+    or column - L + 1 back where S lies inside the break. It is the raw
+    position of data character P - 1, and no line division of P - 1 is
+    needed."""
+    for L, e in LAYOUTS:
+        Q = L + e
+        for k in range(1, 40):
+            S = k * K_SEG
+            line, col = divmod(S, Q)
+            P = line * L + min(col, L)
+            assert P > 0
+            back = 1 + e if col == 0 else (col - L + 1 if col > L else 1)
+            j = P - 1
+            assert S - back == Q * (j // L) + j % L, (L, e, k)

@@ -194,9 +194,12 @@ int b64_mime_decode_async(const uint8_t* src, size_t len, uint8_t* dst, const b6
  * written. Seven launches on `stream`, no waits between blocks: a memset,
  * per-document line layout, a one-pass decode of the documents laid out as
  * lines (as b64_mime_decode_async decodes them, so the same note on bytes past
- * the result holds), then count, per-document scan and decode for the others,
- * and the results. Returns B64_SUCCESS or an error code; n == 0 enqueues
- * nothing. */
+ * the result holds), then count, per-document scan and decode for the others
+ * (each returning at once when every document kept its line layout), and the
+ * results; each kernel after the layout kernel is a programmatic dependent
+ * of the one before (it may start while that one finishes, and waits for it
+ * before reading its results). Returns B64_SUCCESS or an error code; n == 0
+ * enqueues nothing. */
 size_t b64_mime_batch_workspace_size(int64_t n, uint64_t total_bytes);
 
 int b64_mime_decode_batch(const uint8_t* src, const int64_t* src_off, int64_t n, uint8_t* dst,

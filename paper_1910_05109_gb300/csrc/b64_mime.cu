@@ -1243,8 +1243,12 @@ struct SlotWalk {
 __global__ void __launch_bounds__(kCountThreads, 4)
     mime_count_docs_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
                            int64_t n, unsigned long long* __restrict__ states,
-                           const unsigned long long* __restrict__ line_docs, uint64_t slot_cap) {
+                           const unsigned long long* __restrict__ line_docs,
+                           const unsigned long long* __restrict__ none_counted,
+                           uint64_t slot_cap) {
     const int lane = threadIdx.x & 31;
+    wait_prior_grid();  // line_docs and none_counted are written by the kernels before
+    if (*none_counted) return;  // every document kept its line layout
     const uint64_t nslots = doc_slots(src_off, n);
     if (nslots > slot_cap) return;  // workspace too small: the results say so
     const uint64_t gw = (uint64_t(blockIdx.x) * kCountThreads + threadIdx.x) >> 5;
@@ -1277,8 +1281,12 @@ __global__ void __launch_bounds__(256)
                           int64_t n, unsigned long long* __restrict__ states,
                           unsigned long long* __restrict__ doc_state,
                           const unsigned long long* __restrict__ line_docs,
-                          unsigned long long* __restrict__ status_docs, uint64_t slot_cap) {
+                          unsigned long long* __restrict__ status_docs,
+                          const unsigned long long* __restrict__ none_counted,
+                          uint64_t slot_cap) {
     const int lane = threadIdx.x & 31;
+    wait_prior_grid();
+    if (*none_counted) return;
     if (doc_slots(src_off, n) > slot_cap) return;
     const int64_t gw = (int64_t(blockIdx.x) * 256 + threadIdx.x) >> 5;
     const int64_t GW = (int64_t(gridDim.x) * 256) >> 5;
@@ -1325,7 +1333,8 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     mime_layout_docs_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
                             int64_t n, unsigned long long* __restrict__ line_docs,
-                            unsigned long long* __restrict__ doc_state, uint64_t slot_cap) {
+                            unsigned long long* __restrict__ doc_state,
+                            unsigned long long* __restrict__ none_counted, uint64_t slot_cap) {
     const int lane = threadIdx.x & 31;
     if (doc_slots(src_off, n) > slot_cap) return;
     const int64_t gw = (int64_t(blockIdx.x) * 256 + threadIdx.x) >> 5;
@@ -1347,6 +1356,7 @@ __global__ void __launch_bounds__(256)
         if (lane == 0) {
             const uint32_t word = line_layout_word(p, len, f);
             line_docs[d] = word ? uint64_t(word) : kDocCounted;
+            if (!word) *none_counted = 0;
             if (word) {
                 const LineLayout ly{word};
                 const uint64_t k = len / ly.Q, r = len - k * ly.Q;
@@ -1398,7 +1408,8 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
                             const uint8_t* __restrict__ alph_id,
                             unsigned long long* __restrict__ status_docs,
                             unsigned long long* __restrict__ line_docs,
-                            const unsigned long long* __restrict__ states, uint64_t slot_cap) {
+                            const unsigned long long* __restrict__ states,
+                            unsigned long long* __restrict__ none_counted, uint64_t slot_cap) {
     __shared__ __align__(256) uint8_t luts[kMaxAlphabets][256];  // 0..63, 0x80, kSpace
     __shared__ __align__(16) uint8_t bufs[kDocWarps][2][kBuf];
     __shared__ uint64_t bars[kDocWarps];
@@ -1412,6 +1423,10 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
         fence_mbar_init();
     }
     __syncthreads();
+    wait_prior_grid();  // the layout words, states and status words of the kernels before
+    if constexpr (!kOnePass) {
+        if (*none_counted) return;  // every document kept its line layout
+    }
     const uint64_t nslots = doc_slots(src_off, n);
     if (nslots > slot_cap) return;
     const uint8_t* lo = src + src_off[0];
@@ -1560,7 +1575,10 @@ __global__ void __launch_bounds__(32 * kDocWarps, 5)
             }
             // one call site, so the kernel holds one copy of the general path
             if (general) decode_segment(buf, luts[a], flags, lane, P, prev_last, S, out_doc, st3);
-            if (irregular && lane == 0) atomicOr(&line_docs[ds.d], (unsigned long long)kDocCounted);
+            if (irregular && lane == 0) {
+                atomicOr(&line_docs[ds.d], (unsigned long long)kDocCounted);
+                *none_counted = 0;
+            }
         } else {
             const uint64_t pre = meta.pre;
             const uint64_t P = st_count(pre);
@@ -1592,6 +1610,7 @@ __global__ void mime_finalize_docs_kernel(const uint8_t* __restrict__ src,
                                           const unsigned long long* __restrict__ status_docs,
                                           const unsigned long long* __restrict__ doc_state,
                                           uint64_t slot_cap, int64_t* __restrict__ results) {
+    wait_prior_grid();
     const int64_t d = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (d >= n) return;
     if (doc_slots(src_off, n) > slot_cap) {
@@ -1706,54 +1725,57 @@ cudaError_t launch_selftest_wait(int64_t* d_result, uint64_t wait_limit_ns, cuda
 
 size_t mime_batch_workspace_bytes(int64_t n, uint64_t total_bytes) {
     const uint64_t slots = total_bytes / kSeg + uint64_t(n) + 1;
-    return 8 * (5 * size_t(n) + size_t(slots));
+    return 8 * (5 * size_t(n) + 1 + size_t(slots));
 }
 
 cudaError_t launch_mime_decode_batch(const BatchArgs& a, const BatchTables& tabs, void* workspace,
                                      size_t workspace_bytes, cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
-    // [status: 3 words per document][document states: n][line layouts: n][segment slots]
+    // [status: 3 words per document][none_counted][document states: n]
+    // [line layouts: n][segment slots]; none_counted stays all ones while
+    // every document keeps its line layout, and the counting passes then
+    // return at once
     unsigned long long* status_docs = static_cast<unsigned long long*>(workspace);
-    unsigned long long* doc_state = status_docs + 3 * a.n;
+    unsigned long long* none_counted = status_docs + 3 * a.n;
+    unsigned long long* doc_state = none_counted + 1;
     unsigned long long* line_docs = doc_state + a.n;
     unsigned long long* states = line_docs + a.n;
-    const uint64_t words = workspace_bytes / 8;
-    const uint64_t slot_cap = words > 5 * uint64_t(a.n) ? words - 5 * uint64_t(a.n) : 0;
-    cudaError_t e = cudaMemsetAsync(status_docs, 0xFF, 3 * size_t(a.n) * sizeof(uint64_t), st);
+    const uint64_t words = workspace_bytes / 8, fixed = 5 * uint64_t(a.n) + 1;
+    const uint64_t slot_cap = words > fixed ? words - fixed : 0;
+    cudaError_t e =
+        cudaMemsetAsync(status_docs, 0xFF, (3 * size_t(a.n) + 1) * sizeof(uint64_t), st);
     if (e != cudaSuccess) return e;
     const DeviceInfo& di = device_info();
     const uint64_t scan_blocks = (uint64_t(a.n) + 7) / 8;
     const unsigned sb = unsigned(scan_blocks < uint64_t(di.sm_count) * 8 ? scan_blocks : di.sm_count * 8);
     // one pass for the documents with a line layout, then the counting passes
-    // for the others (each kernel skips the documents it is not for)
+    // for the others (each kernel skips the documents it is not for); every
+    // kernel after the layout kernel is a programmatic dependent of the one
+    // before
     mime_layout_docs_kernel<<<sb, 256, 0, st>>>(a.src, a.src_off, a.n, line_docs, doc_state,
-                                                slot_cap);
+                                                none_counted, slot_cap);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int ddo = occupancy(mime_decode_docs_kernel<true>, 32 * kDocWarps, g_ddo_occ[di.device & 63]);
-    mime_decode_docs_kernel<true><<<unsigned(di.sm_count * ddo), 32 * kDocWarps, 0, st>>>(
-        a.src, a.src_off, a.n, a.dst, a.dst_off, tabs, a.alph_id, status_docs, line_docs, states,
-        slot_cap);
-    e = cudaGetLastError();
+    e = launch_dependent(mime_decode_docs_kernel<true>, unsigned(di.sm_count * ddo), 32 * kDocWarps,
+                         0, st, a.src, a.src_off, a.n, a.dst, a.dst_off, tabs, a.alph_id,
+                         status_docs, line_docs, states, none_counted, slot_cap);
     if (e != cudaSuccess) return e;
     const int cd = occupancy(mime_count_docs_kernel, kCountThreads, g_cd_occ[di.device & 63]);
-    mime_count_docs_kernel<<<unsigned(di.sm_count * cd), kCountThreads, 0, st>>>(
-        a.src, a.src_off, a.n, states, line_docs, slot_cap);
-    e = cudaGetLastError();
+    e = launch_dependent(mime_count_docs_kernel, unsigned(di.sm_count * cd), kCountThreads, 0, st,
+                         a.src, a.src_off, a.n, states, line_docs, none_counted, slot_cap);
     if (e != cudaSuccess) return e;
-    mime_scan_docs_kernel<<<sb, 256, 0, st>>>(a.src, a.src_off, a.n, states, doc_state, line_docs,
-                                              status_docs, slot_cap);
-    e = cudaGetLastError();
+    e = launch_dependent(mime_scan_docs_kernel, sb, 256, 0, st, a.src, a.src_off, a.n, states,
+                         doc_state, line_docs, status_docs, none_counted, slot_cap);
     if (e != cudaSuccess) return e;
     const int dd = occupancy(mime_decode_docs_kernel<false>, 32 * kDocWarps, g_dd_occ[di.device & 63]);
-    mime_decode_docs_kernel<false><<<unsigned(di.sm_count * dd), 32 * kDocWarps, 0, st>>>(
-        a.src, a.src_off, a.n, a.dst, a.dst_off, tabs, a.alph_id, status_docs, line_docs, states,
-        slot_cap);
-    e = cudaGetLastError();
+    e = launch_dependent(mime_decode_docs_kernel<false>, unsigned(di.sm_count * dd), 32 * kDocWarps,
+                         0, st, a.src, a.src_off, a.n, a.dst, a.dst_off, tabs, a.alph_id,
+                         status_docs, line_docs, states, none_counted, slot_cap);
     if (e != cudaSuccess) return e;
-    mime_finalize_docs_kernel<<<unsigned((a.n + 255) / 256), 256, 0, st>>>(
-        a.src, a.src_off, a.n, tabs, a.alph_id, status_docs, doc_state, slot_cap, a.results);
-    return cudaGetLastError();
+    return launch_dependent(mime_finalize_docs_kernel, unsigned((a.n + 255) / 256), 256, 0, st,
+                            a.src, a.src_off, a.n, tabs, a.alph_id, status_docs, doc_state,
+                            slot_cap, a.results);
 }
 
 uint32_t mime_fault_flag(bool clear) {

@@ -155,7 +155,7 @@ def test_new_entry_points_reject_bad_arguments_without_gpu(L):
                                    None) == b.B64_ERR_INVALID_ARGUMENT
     assert "workspace" in b.last_error()
     assert L.b64_mime_batch_workspace_size(0, 1000) == 0
-    assert L.b64_mime_batch_workspace_size(4, 4096 * 10) == 8 * (5 * 4 + 10 + 4 + 1)
+    assert L.b64_mime_batch_workspace_size(4, 4096 * 10) == 8 * (5 * 4 + 1 + 10 + 4 + 1)
     # bounded-wait self-test: NULL or misaligned result, limit out of range
     assert L.b64_selftest_wait_timeout(None, 1000, None) == b.B64_ERR_INVALID_ARGUMENT
     assert L.b64_selftest_wait_timeout(12, 1000, None) == b.B64_ERR_INVALID_ARGUMENT

@@ -191,3 +191,49 @@ def test_line_layout_documents(b64, orc):
             assert res[i] == want_r, (origin, i, res[i], want_r)
             if want_r >= 0:
                 assert np.array_equal(outs[i][:want_r], want), i
+
+
+def test_layout_broken_past_the_start_and_recorded_in_a_cuda_graph(b64, orc):
+    """Every document shows its line layout in its first bytes; in the second
+    batch one of them has a line a group longer in its third segment, which
+    only the one-pass kernel can find (it then clears the word that lets the
+    counting kernels return at once). The launch chain (a memset, then the
+    layout kernel and five programmatic dependents) is recorded once in a CUDA
+    graph per batch and replayed twice, each replay against the oracle."""
+    std, chars = b64.Alphabet.standard(), orc.standard_alphabet()
+    docs = [wl.mime_wrap(orc.encode(wl.random_bytes(12_000 + 997 * i, 7100 + i)))
+            for i in range(8)]
+    lines = [docs[5][k:k + 78] for k in range(0, docs[5].size, 78)]
+    j = 9000 // 78  # a line of the third segment
+    lines[j] = np.concatenate([lines[j][:76], np.frombuffer(b"QUJD", np.uint8), lines[j][76:]])
+    broken = docs[:5] + [np.concatenate(lines)] + docs[6:]
+    for batch in (docs, broken):
+        # odd offsets: origin 3 and the documents' own lengths
+        off = np.concatenate([[0], np.cumsum([d.size for d in batch])]).astype(np.int64) + 3
+        buf = np.concatenate([np.full(3, ord("*"), np.uint8)] + batch)
+        src = torch.from_numpy(buf).cuda()
+        d_off = torch.from_numpy(off).cuda()
+        dst_off = b64.batch_offsets(d_off, [std], None, decode=True)
+        dst = torch.zeros(int(dst_off[-1]), dtype=torch.uint8, device="cuda")
+        res = torch.zeros(len(batch), dtype=torch.int64, device="cuda")
+        ws = torch.empty(b64.lib().b64_mime_batch_workspace_size(len(batch), int(off[-1] - off[0])),
+                         dtype=torch.uint8, device="cuda")
+        s = torch.cuda.Stream()
+        b64.mime_decode_batch(src, d_off, dst, dst_off, [std], None, res, ws, stream=s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            b64.mime_decode_batch(src, d_off, dst, dst_off, [std], None, res, ws, stream=s)
+        ho = dst_off.cpu().numpy()
+        for _ in range(2):
+            dst.zero_()
+            res.fill_(-7)
+            torch.cuda.synchronize()
+            g.replay()
+            torch.cuda.synchronize()
+            got, out = res.cpu().numpy(), dst.cpu().numpy()
+            for i, text in enumerate(batch):
+                want_r, want = orc.decode(text, chars, True, mime=True)
+                assert got[i] == want_r, (i, got[i], want_r)
+                if want_r >= 0:
+                    assert np.array_equal(out[ho[i]:ho[i] + want_r], want), i

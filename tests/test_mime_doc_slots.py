@@ -88,12 +88,13 @@ def test_slot_ranges_are_disjoint_and_fit_the_workspace(seed, count, origin):
         if nseg(src_off, d):
             end = first + nseg(src_off, d) - 1
     assert end < cap
-    # the library's workspace size: 3 status words, a state and a layout word
-    # a document, then the slots
+    # the library's workspace size: 3 status words a document, one word that
+    # says whether any document needs the counting passes, a state and a
+    # layout word a document, then the slots
     from paper_1910_05109_gb300 import binding, build
     build.build()
     total = src_off[n] - src_off[0]
-    assert binding.lib().b64_mime_batch_workspace_size(n, total) == 8 * (5 * n + cap)
+    assert binding.lib().b64_mime_batch_workspace_size(n, total) == 8 * (5 * n + 1 + cap)
 
 
 @pytest.mark.parametrize("seed,count,origin", [(1, 1, 0), (2, 7, 5), (3, 200, 0),

@@ -1370,6 +1370,10 @@ __global__ void __launch_bounds__(256)
 }
 
 constexpr int kDocWarps = 4;
+// Blocks an SM the register bound of the one-pass documents kernel aims at
+#ifndef B64_MIME_DOCS_ONEPASS_BLOCKS
+#define B64_MIME_DOCS_ONEPASS_BLOCKS 5
+#endif
 // a segment's 16-byte aligned span (at most kSeg + 32 bytes) fits a buffer after its lead
 static_assert(kLead + kSeg + 32 <= kBuf, "document staging");
 
@@ -1400,7 +1404,7 @@ __device__ __forceinline__ bool issue_doc_segment(uint8_t* stage, const DocSeg& 
 // document's kDocCounted. Otherwise: the kDocCounted documents, with the
 // counts of the count and scan kernels.
 template <bool kOnePass>
-__global__ void __launch_bounds__(32 * kDocWarps, 5)
+__global__ void __launch_bounds__(32 * kDocWarps, kOnePass ? B64_MIME_DOCS_ONEPASS_BLOCKS : 5)
     mime_decode_docs_kernel(const uint8_t* __restrict__ src, const int64_t* __restrict__ src_off,
                             int64_t n, uint8_t* __restrict__ dst,
                             const int64_t* __restrict__ dst_off,

@@ -28,6 +28,7 @@ VARIANTS = [
     ("b64_batch.cu", ("B64_BATCH_DEC_WHOLE_UNROLL=8", "B64_BATCH_ENC_WHOLE_UNROLL=2")),
     ("b64_batch.cu", ("B64_BATCH_ENC_PAIRS=0",)),
     ("b64_mime.cu", ("B64_MIME_UNITS=0",)),
+    ("b64_mime.cu", ("B64_MIME_DOCS_ONEPASS_BLOCKS=6",)),
 ]
 
 

@@ -358,9 +358,10 @@ typedef struct {
 b64_server* b64_server_create(size_t budget_bytes, int n_streams, size_t max_batch_bytes,
                               const b64_alphabet* const* alphabets, int n_alphabets);
 
-/* op: 0 = encode, 1 = strict decode; alph_id indexes the server's alphabets.
- * out_cap: at least b64_encoded_length (encode) or b64_decoded_max_length
- * (decode) of len. A request that could never fit the budget is refused. */
+/* op: 0 = encode, 1 = strict decode; alph_id indexes the server's alphabets
+ * (0 .. n_alphabets - 1; others are refused). out_cap: at least
+ * b64_encoded_length (encode) or b64_decoded_max_length (decode) of len. A
+ * request that could never fit the budget is refused. */
 int b64_server_submit(b64_server* s, uint64_t tag, int op, int alph_id, const uint8_t* in,
                       size_t len, uint8_t* out, size_t out_cap);
 

@@ -302,7 +302,7 @@ b64_server* b64_server_create(size_t budget_bytes, int n_streams, size_t max_bat
 
 int b64_server_submit(b64_server* s, uint64_t tag, int op, int alph_id, const uint8_t* in,
                       size_t len, uint8_t* out, size_t out_cap) {
-    if (!s || (op != 0 && op != 1) || alph_id < 0 || alph_id >= kMaxAlphabets ||
+    if (!s || (op != 0 && op != 1) || alph_id < 0 || alph_id >= s->tabs.n_alph ||
         (len && (!in || !out)))
         return set_error(B64_ERR_INVALID_ARGUMENT, "b64_server_submit: bad argument");
     b64_server_req r{tag, op, alph_id, in, len, out, out_cap, 0, Clock::now()};

@@ -143,6 +143,9 @@ def test_small_budget_waits_and_refuses(env, orc):
     out = np.zeros((8 << 20) // 3 * 4 + 4, np.uint8)
     with pytest.raises(b64.B64Error, match="budget"):
         srv.submit(1, 0, 0, big.ctypes.data, big.size, out.ctypes.data, out.size)
+    # the server holds one alphabet: id 1 is refused, not coded with another
+    with pytest.raises(b64.B64Error, match="bad argument"):
+        srv.submit(2, 0, 1, big.ctypes.data, 12, out.ctypes.data, 16)
     srv.close()
 
 
